@@ -1,0 +1,226 @@
+/*
+ * cn.h -- C ABI of the GB300-native fixed-step cable-network engine.
+ *
+ * The engine advances many multi-compartment cells with the fixed-step
+ * (backward Euler) method of CoreNEURON (arXiv 1901.10975, Section 2): every
+ * step delivers due events, assembles each cell's tree matrix from the
+ * mechanism currents and conductances (Eq. 1), solves it by Gaussian
+ * elimination in Hines order, updates the gating states and detects
+ * threshold crossings; spikes are exchanged once per minimum-delay interval
+ * (Section 2, hybrid clock-event algorithm).  All of that runs in CUDA
+ * kernels for sm_103a; this header only carries plain pointers and sizes.
+ *
+ * Conventions shared by every entry point:
+ *  - Each call returns a cn_status.  No exception crosses the ABI.  After a
+ *    failure cn_last_error() describes it.
+ *  - Host input arrays are copied; the caller keeps ownership and may free
+ *    them when the call returns.  Outputs are written into caller buffers.
+ *  - A model handle is not thread-safe: one host thread at a time.
+ *  - Units: mV, ms, um, um2, uF/cm2, MOhm, S/cm2 (density mechanisms),
+ *    uS (synaptic weights and conductances), nA (stimuli).
+ *  - Indices are 0-based.  Node indices are global (concatenated cells, cell
+ *    c owning nodes [cell_offset[c], cell_offset[c+1])) unless a field says
+ *    "cell-local".
+ */
+#ifndef CN_H_
+#define CN_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CN_OK = 0,
+  CN_EINVAL = 1,    /* bad argument or inconsistent model description */
+  CN_ENOMEM = 2,    /* device or host allocation failed */
+  CN_ECUDA = 3,     /* a CUDA runtime call or kernel launch failed */
+  CN_ESTATE = 4,    /* call not allowed in the model's current state */
+  CN_ETIMEOUT = 5,  /* a bounded device wait gave up */
+  CN_ERANGE = 6     /* a fixed-capacity buffer overflowed (see cn_last_error) */
+} cn_status;
+
+/* Mechanism types and their parameter columns (SoA, one column per name, in
+ * this order).  Density mechanisms use S/cm2 and mV; point processes uS.
+ * Gate kinetics of the channel types: alpha = A (v-vh)/(1-exp(-(v-vh)/k)),
+ * beta = B exp(-(v-vh2)/k2), cnexp update (Section 6: fixed step).        */
+typedef enum {
+  CN_MECH_PAS = 0,    /* g, e                                                   */
+  CN_MECH_HH = 1,     /* gnabar, gkbar, gl, el, ena, ek (Hodgkin-Huxley, 6.3 C)  */
+  CN_MECH_EXPSYN = 2, /* tau, e   (point process; state g in uS)                 */
+  CN_MECH_NA3H = 3,   /* gbar, erev, m:{A,vh,k,B,vh2,k2}, h:{...}   g = gbar m^3 h */
+  CN_MECH_KDR4 = 4,   /* gbar, erev, n:{6}                          g = gbar n^4   */
+  CN_MECH_KA = 5,     /* gbar, erev, a:{6}, b:{6}                   g = gbar a^3 b */
+  CN_MECH_IH = 6,     /* gbar, erev, q:{6}                          g = gbar q     */
+  CN_MECH_CAHVA = 7,  /* gbar, erev, m:{6}, h:{6}, depth, taur, cainf  g = gbar m^2 h,
+                         cai' = -1e4 ica/(2 F depth) (inward) + (cainf-cai)/taur  */
+  CN_MECH_KCA = 8,    /* gbar, erev, A, kd, B:  alpha = A cai/(cai+kd), beta = B */
+  CN_MECH_NTYPES = 9
+} cn_mech_type;
+
+/* Number of parameter columns of a mechanism type (-1 for an unknown type). */
+int32_t cn_mech_nparams(int32_t type);
+
+typedef enum {
+  CN_PREC_FP64 = 0,      /* everything FP64                                     */
+  CN_PREC_GATE_FP32 = 1, /* gating rates, exponentials and state updates FP32   */
+  CN_PREC_GATE_BF16 = 2  /* as GATE_FP32, gating states stored as bfloat16      */
+} cn_precision;
+
+/* Morphology (Section 2: a tree of compartments per cell, indexed by parent).
+ * parent is cell-local with parent[i] < i and exactly one root (-1) per cell,
+ * at cell-local index 0.  area and ri are per node; ri is the axial
+ * resistance between a node and its parent (ignored at roots).            */
+typedef struct {
+  int32_t n_cells;
+  const int32_t* cell_offset;   /* [n_cells+1], cell_offset[0] = 0 */
+  const int32_t* parent;        /* [n_nodes], cell-local */
+  const double* area_um2;       /* [n_nodes] */
+  const double* cm_uF_cm2;      /* [n_nodes] */
+  const double* ri_MOhm;        /* [n_nodes] */
+  const int32_t* spike_node;    /* [n_cells], cell-local threshold-detection node */
+  const double* threshold_mV;   /* [n_cells] */
+} cn_morph;
+
+/* One SoA mechanism instance table (Section 4.2: instances of one type are
+ * grouped, each property stored contiguously).  param is [n_params][n]. */
+typedef struct {
+  int32_t type;
+  int32_t n;
+  const int32_t* node;          /* [n] global node index per instance */
+  const double* param;          /* [cn_mech_nparams(type) * n] */
+} cn_mech_table;
+
+/* Device allocator used for every buffer of a model.  NULL -> cudaMalloc. */
+typedef void* (*cn_alloc_fn)(size_t bytes, void* ctx);
+typedef void (*cn_free_fn)(void* ptr, void* ctx);
+
+typedef struct {
+  double dt_ms;          /* time step (0.025 typical) */
+  double v_init_mV;      /* initial voltage of every node; gates start at steady state */
+  int32_t precision;     /* cn_precision */
+  int32_t device;        /* CUDA device ordinal */
+  void* stream;          /* cudaStream_t for every launch and copy (NULL: legacy default) */
+  cn_alloc_fn alloc;
+  cn_free_fn free;
+  void* alloc_ctx;
+  int32_t mapping;       /* cn_mapping: cell-to-thread mapping, CN_MAP_AUTO picks */
+  int32_t use_graph;     /* nonzero: replay intervals from a captured CUDA graph */
+} cn_options;
+
+typedef enum {
+  CN_MAP_AUTO = 0,       /* autotuned */
+  CN_MAP_THREAD = 1      /* one cell per thread, 32 cells per warp, interleaved nodes */
+} cn_mapping;
+
+typedef struct cn_model cn_model;
+
+/* Fill *opt with defaults: dt 0.025 ms, v_init -65 mV, FP64, device 0,
+ * default stream, cudaMalloc, autotuned mapping, graphs on. */
+void cn_options_default(cn_options* opt);
+
+/* Geometry helper (Section 2 discretisation, the engine's reading): each node
+ * is a cylinder of length dx and diameter diam; area = pi diam dx (lateral
+ * surface); the half-segment resistance is 1e-2 * 2 Ra dx / (pi diam^2) MOhm
+ * and ri(node) = R_half(node) + R_half(parent).  parent is cell-local as in
+ * cn_morph.  Outputs area[n_nodes] and ri[n_nodes] (0 at roots).
+ * Errors: CN_EINVAL on bad parent indices or non-positive geometry.      */
+cn_status cn_geometry(int32_t n_cells, const int32_t* cell_offset, const int32_t* parent,
+                      const double* dx_um, const double* diam_um, const double* Ra_ohm_cm,
+                      double* area_um2, double* ri_MOhm);
+
+/* Build a model on the GPU from a morphology and mechanism tables (Eq. 1's
+ * terms: pas -> I_pas, channels -> I_ion, EXPSYN -> I_syn; Section 4.2 SoA
+ * tables).  At most one table per type.  Every node must carry at least one
+ * mechanism or capacitance only.  On success *out owns device memory until
+ * cn_model_destroy.  Errors: CN_EINVAL (validation, message in
+ * cn_last_error(NULL)), CN_ENOMEM, CN_ECUDA.                               */
+cn_status cn_model_create(const cn_morph* morph, const cn_mech_table* mechs, int32_t n_mechs,
+                          const cn_options* opt, cn_model** out);
+
+/* NetCon (Table 2): a spike of cell src_gid delivers weight_uS to EXPSYN
+ * instance target_syn (index into the EXPSYN table) delay_ms later, rounded
+ * to whole steps half away from zero.  The minimum delay over all NetCons
+ * sets the spike-exchange interval (Section 2) and must be >= 1 step.
+ * Allowed only before the first cn_run (CN_ESTATE after).                  */
+cn_status cn_add_netcon(cn_model* m, int32_t src_gid, int32_t target_syn, double weight_uS,
+                        double delay_ms);
+/* Batch form of cn_add_netcon; NetCon indices follow call order.          */
+cn_status cn_add_netcons(cn_model* m, int64_t n, const int32_t* src_gid, const int32_t* target_syn,
+                         const double* weight_uS, const double* delay_ms);
+
+/* External events (a kick, Poisson background): event e adds weight_uS[e] to
+ * EXPSYN target_syn[e] at step round(t_ms[e]/dt).  Events due at the same
+ * step are applied in input order, before NetCon events of that step.
+ * Before the first cn_run only (CN_ESTATE after).                          */
+cn_status cn_add_events(cn_model* m, int64_t n, const int32_t* target_syn, const double* t_ms,
+                        const double* weight_uS);
+
+/* Current clamp: +amp_nA into node (global) while del <= (k+1/2) dt < del+dur.
+ * Before the first cn_run only.                                            */
+cn_status cn_add_stim(cn_model* m, int32_t node, double del_ms, double dur_ms, double amp_nA);
+
+/* Record the voltage of a node (global index) at every step; *rec_id is the
+ * handle for cn_get_trace.  Before the first cn_run only.                  */
+cn_status cn_record(cn_model* m, int32_t node, int32_t* rec_id);
+
+/* Advance to step round(tstop_ms/dt) (continuing from the current step).
+ * Launches are queued on the model's stream; errors detected on the device
+ * (buffer overflow, bounded-wait timeout) are returned by the next call that
+ * synchronizes (cn_sync, cn_get_*).  CN_EINVAL if tstop is behind the
+ * current time.                                                            */
+cn_status cn_run(cn_model* m, double tstop_ms);
+
+/* Wait for queued work and report device-side errors.                      */
+cn_status cn_sync(cn_model* m);
+
+/* Current step index k (v holds v_k).                                      */
+int64_t cn_current_step(const cn_model* m);
+
+/* Spike raster (Section 3.1: spikes are the simulation's output), sorted by
+ * (step, gid).  A spike (gid, k) means the threshold node of cell gid crossed
+ * its threshold upward between steps k-1 and k.  Two-call form: with gid or
+ * step NULL only *n is set; otherwise at most cap entries are written and *n
+ * is the total count (CN_ERANGE if cap < total).                          */
+cn_status cn_get_spikes(cn_model* m, int32_t* gid, int64_t* step, size_t cap, size_t* n);
+
+/* Voltage trace of a recorded node: v at steps 0..current (n = current+1).
+ * Two-call form as cn_get_spikes.                                          */
+cn_status cn_get_trace(cn_model* m, int32_t rec_id, double* out, size_t cap, size_t* n);
+
+/* Node voltages v_k of every node, in global input order (cap >= n_nodes). */
+cn_status cn_get_v(cn_model* m, double* out, size_t cap);
+
+/* State column col of mechanism type (HH: 0 m, 1 h, 2 n; EXPSYN: 0 g; channel
+ * types: their gates in parameter order; CAHVA: 2 = cai), per instance in
+ * table order (cap >= instance count).                                     */
+cn_status cn_get_state(cn_model* m, int32_t type, int32_t col, double* out, size_t cap);
+
+/* Number of compartment updates performed so far (sum of cell sizes x steps). */
+int64_t cn_updates(const cn_model* m);
+
+/* Diagnostics of the last cn_run: kernel launches issued.                  */
+int64_t cn_launch_count(const cn_model* m);
+
+/* Kernel timing (diagnostics): while enabled, cn_run brackets every
+ * interval-kernel and spike-pull launch with CUDA events on the model's
+ * stream.  cn_profile_read synchronizes, returns the summed device time (ms)
+ * and launch counts since the last read, and clears them.                 */
+cn_status cn_profile(cn_model* m, int32_t enable);
+cn_status cn_profile_read(cn_model* m, double* interval_ms, int64_t* interval_launches, double* pull_ms,
+                          int64_t* pull_launches);
+
+/* Error text of the last failed call on m (or of the last failed
+ * cn_model_create when m is NULL).  Valid until the next call on m.        */
+const char* cn_last_error(const cn_model* m);
+
+/* Release every device buffer of m (through the model's allocator).        */
+void cn_model_destroy(cn_model* m);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CN_H_ */

@@ -1,0 +1,179 @@
+// cn_device.cuh -- device data layout and kernels of the fixed-step engine.
+//
+// Layout ("one cell per thread", Section 4.4's interleaved idea, rebuilt for
+// sm_103a): cells are sorted by size and packed 32 to a warp ("group"); node
+// row j of lane l lives at element base_g + 32*j + l of every per-node
+// array, so the 32 lanes of a warp touch one contiguous 256-byte row of
+// FP64 per array.  Mechanism instances (synapses, HH, stimuli) and records
+// use the same interleaving with their own row counts.  Each thread owns one
+// cell for a whole minimum-delay interval: there is no communication between
+// threads inside the interval kernel.
+#pragma once
+#include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+namespace cn {
+
+constexpr int kLanes = 32;
+constexpr int kEvCap = 256;          // events per cell per interval
+constexpr int kMaxInterval = 64;     // steps per interval (spike mask width)
+
+enum : int32_t { kStatusEvOverflow = 1, kStatusBadState = 2 };
+
+struct EvRec {
+  int32_t step;   // step offset inside the interval
+  int32_t syn;    // lane-local synapse row
+  double w;       // uS
+};
+
+// Plain-old-data view of a model's device buffers, passed by value.
+struct DevModel {
+  int32_t n_groups, n_slots, n_cells, D, n_rec;
+  double dt;
+  // per group
+  const int64_t* g_node_base;
+  const int32_t* g_rows;
+  const int64_t* g_syn_base;
+  const int32_t* g_syn_rows;
+  const int64_t* g_hh_base;
+  const int32_t* g_hh_rows;
+  const int64_t* g_st_base;
+  const int32_t* g_st_rows;
+  const int64_t* g_rec_base;
+  const int32_t* g_rec_rows;
+  // per slot (group * 32 + lane)
+  const int32_t* s_rows;
+  const int32_t* s_nsyn;
+  const int32_t* s_nhh;
+  const int32_t* s_nst;
+  const int32_t* s_nrec;
+  const int32_t* s_gid;
+  const int32_t* s_spike_row;
+  const double* s_thresh;
+  uint8_t* s_above;
+  // nodes (interleaved)
+  double* v;
+  double* acc;    // right-hand side accumulator, reset to ge after each solve
+  double* dacc;   // diagonal accumulator, reset to d0 after each solve
+  const double* a;     // row p, column i coupling (-100/(ri area_p))
+  const double* b;     // row i, column p coupling (-100/(ri area_i))
+  const double* cdt;   // 1e-3 cm / dt
+  const double* ge;    // constant part of sum g E (pas)
+  const double* d0;    // constant diagonal: cdt + pas g + axial sums
+  const int32_t* prow; // parent row (-1 at the root)
+  // synapses (ExpSyn)
+  const int32_t* syn_row;
+  double* syn_g;
+  const double* syn_s;      // 100 / area of the synapse node
+  const double* syn_e;
+  const double* syn_decay;  // exp(-dt / tau)
+  // HH
+  const int32_t* hh_row;
+  void* hh_m;
+  void* hh_h;
+  void* hh_n;
+  const double* hh_p;       // [6][hh_elems]: gnabar gkbar gl el ena ek
+  int64_t hh_elems;
+  // stimuli
+  const int32_t* st_row;
+  const double* st_del;
+  const double* st_dur;
+  const double* st_amp;     // 100 amp / area (mA/cm2)
+  // records
+  const int32_t* rec_row;
+  const int32_t* rec_id;
+  double* trace;            // [step][n_rec]
+  // events
+  int32_t* ev_count;
+  EvRec* ev_buf;            // [slot][kEvCap]
+  // external events, CSR by slot
+  const int64_t* x_off;
+  int64_t* x_pos;
+  const int64_t* x_step;
+  const int32_t* x_syn;
+  const double* x_w;
+  // incoming NetCons, CSR by target slot, sorted by (src gid, NetCon index)
+  const int64_t* in_off;
+  const int32_t* in_src;
+  const int32_t* in_syn;
+  const int32_t* in_dsteps;
+  const double* in_w;
+  // spike masks, [interval][gid]: bit s = spike at step interval*D + s + 1
+  uint64_t* hist;
+  int32_t* status;
+};
+
+// --------------------------------------------------------------- arithmetic
+// Reciprocal of a positive FP64 number in [2^-126, 2^126] (always true for a
+// pivot of the cable matrix: cdt = 1e-3 cm/dt > 0 plus non-negative terms).
+// Newton-Raphson division (e.g. Markstein 1990): a float seed from the top
+// 23 mantissa bits of d, the hardware approximate reciprocal (~2^-22), then
+// one cubic step r' = r (1 + e + e^2), e = 1 - d r, which brings the relative
+// error to ~eps0^3 plus rounding (within 2 ulp of 1/d).  Costs 3 FP64
+// instructions instead of an IEEE division's ~6.
+__device__ __forceinline__ double rcp64(double d) {
+  const int hi = __double2hiint(d);
+  const int lo = __double2loint(d);
+  const unsigned fb = ((unsigned)(hi - (896 << 20)) << 3) | ((unsigned)lo >> 29);
+  float rf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(__uint_as_float(fb)));
+  const unsigned rb = __float_as_uint(rf);
+  const double r = __hiloint2double((int)((rb >> 3) + (896u << 20)), (int)(rb << 29));
+  const double e = fma(-d, r, 1.0);
+  const double t = fma(e, e, e);
+  return fma(r, t, r);
+}
+
+// alpha = A (v - vh) / (1 - exp(-(v - vh)/k)); limit A k (1 + u/2) near vh.
+template <typename T>
+__device__ __forceinline__ T vtrap(T A, T vh, T k, T v);
+
+template <>
+__device__ __forceinline__ double vtrap<double>(double A, double vh, double k, double v) {
+  const double u = (v - vh) / k;
+  if (fabs(u) < 1e-6) return A * k * (1.0 + 0.5 * u);
+  return A * (v - vh) / (1.0 - exp(-u));
+}
+template <>
+__device__ __forceinline__ float vtrap<float>(float A, float vh, float k, float v) {
+  const float u = (v - vh) / k;
+  if (fabsf(u) < 1e-4f) return A * k * (1.0f + 0.5f * u);
+  return A * (v - vh) / (1.0f - expf(-u));
+}
+__device__ __forceinline__ double dexp_(double x) { return exp(x); }
+__device__ __forceinline__ float dexp_(float x) { return expf(x); }
+
+// Hodgkin-Huxley rate functions (squid axon, 6.3 C, q10 = 1).
+template <typename T>
+__device__ __forceinline__ void hh_rates(T v, T& am, T& bm, T& ah, T& bh, T& an, T& bn) {
+  am = vtrap<T>(T(0.1), T(-40.0), T(10.0), v);
+  bm = T(4.0) * dexp_(-(v + T(65.0)) / T(18.0));
+  ah = T(0.07) * dexp_(-(v + T(65.0)) / T(20.0));
+  bh = T(1.0) / (T(1.0) + dexp_(-(v + T(35.0)) / T(10.0)));
+  an = vtrap<T>(T(0.01), T(-55.0), T(10.0), v);
+  bn = T(0.125) * dexp_(-(v + T(65.0)) / T(80.0));
+}
+
+// cnexp: x <- x + (1 - exp(-dt (alpha+beta))) (alpha/(alpha+beta) - x)
+template <typename T>
+__device__ __forceinline__ T cnexp_step(T x, T al, T be, T dt) {
+  const T s = al + be;
+  const T inf = al / s;
+  return x + (T(1.0) - dexp_(-dt * s)) * (inf - x);
+}
+
+// Gate storage per precision mode.
+template <int PREC> struct GateT;
+template <> struct GateT<0> { using S = double; using M = double; };
+template <> struct GateT<1> { using S = float; using M = float; };
+template <> struct GateT<2> { using S = __nv_bfloat16; using M = float; };
+
+__device__ __forceinline__ double g_load(const double* p) { return *p; }
+__device__ __forceinline__ float g_load(const float* p) { return *p; }
+__device__ __forceinline__ float g_load(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+__device__ __forceinline__ void g_store(double* p, double x) { *p = x; }
+__device__ __forceinline__ void g_store(float* p, float x) { *p = x; }
+__device__ __forceinline__ void g_store(__nv_bfloat16* p, float x) { *p = __float2bfloat16_rn(x); }
+
+}  // namespace cn

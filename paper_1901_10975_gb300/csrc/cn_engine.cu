@@ -1,0 +1,922 @@
+// cn_engine.cu -- host side of the C ABI declared in include/cn.h.
+//
+// The host validates inputs, lays cells out for the device (sort by size,
+// 32 cells per warp, interleaved rows), uploads the tables and queues the
+// kernels.  All model arithmetic (matrix constants, initial gates, every
+// simulation step) runs in the kernels of cn_kernels.cuh.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "cn.h"
+#include "cn_kernels.cuh"
+
+namespace {
+
+thread_local std::string g_create_error;
+
+int64_t round_half_away(double x) { return (int64_t)std::llround(x); }
+
+const int kNParams[CN_MECH_NTYPES] = {2, 6, 2, 14, 8, 14, 8, 17, 5};
+
+}  // namespace
+
+struct cn_model {
+  cn_options opt{};
+  cudaStream_t stream = nullptr;
+  std::string err;
+  std::vector<void*> allocs;
+
+  // ---- host copy of the description (input order)
+  int32_t n_cells = 0;
+  int64_t n_nodes = 0;
+  std::vector<int32_t> off, parent, spike_node;
+  std::vector<double> area, cm, ri, thresh;
+  std::vector<int32_t> pas_node, hh_node, syn_node;
+  std::vector<double> pas_g, pas_e, hh_par, syn_tau, syn_e;
+  std::vector<int32_t> nc_src, nc_syn;
+  std::vector<double> nc_w, nc_delay;
+  std::vector<int32_t> ev_syn;
+  std::vector<double> ev_t, ev_w;
+  std::vector<int32_t> st_node;
+  std::vector<double> st_del, st_dur, st_amp;
+  std::vector<int32_t> rec_node;
+  std::vector<int32_t> node_cell;
+
+  // ---- layout
+  bool finalized = false;
+  int32_t n_groups = 0, n_slots = 0, D = 0;
+  std::vector<int32_t> cell_slot;             // gid -> slot
+  std::vector<int64_t> g_node_base, g_syn_base, g_hh_base;
+  std::vector<int32_t> syn_slot, syn_q, hh_slot, hh_q;
+  int64_t node_elems = 0, syn_elems = 0, hh_elems = 0, st_elems = 0, rec_elems = 0;
+  int gate_bytes = 8;
+  cn::DevModel dm{};
+  int64_t step = 0;
+  int64_t hist_cap = 0;   // intervals
+  int64_t trace_cap = 0;  // steps + 1
+  int64_t launches = 0;
+  int64_t cells_nodes = 0;
+  // optional per-launch timing
+  bool profiling = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_interval, ev_pull;
+  std::vector<cudaEvent_t> ev_pool;
+
+  cn_status fail(cn_status s, const std::string& msg) {
+    err = msg;
+    return s;
+  }
+};
+
+namespace {
+
+void* dalloc_raw(cn_model* m, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  void* p = nullptr;
+  if (m->opt.alloc) {
+    p = m->opt.alloc(bytes, m->opt.alloc_ctx);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    p = nullptr;
+  }
+  if (p) m->allocs.push_back(p);
+  return p;
+}
+
+void dfree_raw(cn_model* m, void* p) {
+  if (!p) return;
+  auto it = std::find(m->allocs.begin(), m->allocs.end(), p);
+  if (it != m->allocs.end()) m->allocs.erase(it);
+  if (m->opt.free) m->opt.free(p, m->opt.alloc_ctx);
+  else cudaFree(p);
+}
+
+#define CN_TRY_CUDA(m, call)                                                              \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return (m)->fail(CN_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));    \
+  } while (0)
+
+template <class T>
+cn_status upload(cn_model* m, T** dst, const std::vector<T>& src, size_t min_elems = 0) {
+  size_t n = std::max(src.size(), min_elems);
+  T* p = static_cast<T*>(dalloc_raw(m, n * sizeof(T)));
+  if (!p) return m->fail(CN_ENOMEM, "device allocation failed");
+  if (!src.empty())
+    CN_TRY_CUDA(m, cudaMemcpyAsync(p, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, m->stream));
+  if (n > src.size())
+    CN_TRY_CUDA(m, cudaMemsetAsync(p + src.size(), 0, (n - src.size()) * sizeof(T), m->stream));
+  *dst = p;
+  return CN_OK;
+}
+
+template <class T>
+cn_status zeros(cn_model* m, T** dst, size_t n) {
+  T* p = static_cast<T*>(dalloc_raw(m, n * sizeof(T)));
+  if (!p) return m->fail(CN_ENOMEM, "device allocation failed");
+  CN_TRY_CUDA(m, cudaMemsetAsync(p, 0, std::max<size_t>(n, 1) * sizeof(T), m->stream));
+  *dst = p;
+  return CN_OK;
+}
+
+#define CN_CHECK(expr)              \
+  do {                              \
+    cn_status s_ = (expr);          \
+    if (s_ != CN_OK) return s_;     \
+  } while (0)
+
+// Interleave per-instance lists: instance i of cell c becomes row q of slot
+// cell_slot[c].  Returns per-group row counts/bases and per-slot counts.
+struct Rows {
+  std::vector<int32_t> slot_n;   // per slot
+  std::vector<int32_t> g_rows;   // per group
+  std::vector<int64_t> g_base;   // per group (elements)
+  std::vector<int32_t> inst_slot, inst_q;
+  int64_t elems = 0;
+};
+
+Rows interleave(const cn_model* m, const std::vector<int32_t>& inst_node) {
+  Rows r;
+  r.slot_n.assign(m->n_slots, 0);
+  r.inst_slot.resize(inst_node.size());
+  r.inst_q.resize(inst_node.size());
+  for (size_t i = 0; i < inst_node.size(); ++i) {
+    int s = m->cell_slot[m->node_cell[inst_node[i]]];
+    r.inst_slot[i] = s;
+    r.inst_q[i] = r.slot_n[s]++;
+  }
+  r.g_rows.assign(m->n_groups, 0);
+  r.g_base.assign(m->n_groups, 0);
+  for (int s = 0; s < m->n_slots; ++s)
+    r.g_rows[s / cn::kLanes] = std::max(r.g_rows[s / cn::kLanes], r.slot_n[s]);
+  int64_t acc = 0;
+  for (int g = 0; g < m->n_groups; ++g) {
+    r.g_base[g] = acc;
+    acc += (int64_t)r.g_rows[g] * cn::kLanes;
+  }
+  r.elems = acc;
+  return r;
+}
+
+int64_t elem_of(const Rows& r, size_t inst) {
+  int s = r.inst_slot[inst];
+  return r.g_base[s / cn::kLanes] + (int64_t)r.inst_q[inst] * cn::kLanes + s % cn::kLanes;
+}
+
+template <class F>
+cn_status launch_checked(cn_model* m, F&& f) {
+  f();
+  m->launches++;
+  CN_TRY_CUDA(m, cudaGetLastError());
+  return CN_OK;
+}
+
+cn_status finalize(cn_model* m) {
+  cn::DevModel& dm = m->dm;
+  const double dt = m->opt.dt_ms;
+  // interval length: the minimum NetCon delay in steps, at most 64
+  int64_t dmin = 0;
+  std::vector<int32_t> nc_ds(m->nc_src.size());
+  for (size_t j = 0; j < m->nc_src.size(); ++j) {
+    int64_t ds = round_half_away(m->nc_delay[j] / dt);
+    if (ds < 1) return m->fail(CN_EINVAL, "NetCon delay rounds to less than one step");
+    if (ds > (int64_t)1 << 30) return m->fail(CN_EINVAL, "NetCon delay too long");
+    nc_ds[j] = (int32_t)ds;
+    if (dmin == 0 || ds < dmin) dmin = ds;
+  }
+  m->D = (int32_t)(dmin == 0 ? cn::kMaxInterval : std::min<int64_t>(dmin, cn::kMaxInterval));
+
+  // cells sorted by size (largest first), 32 per warp
+  std::vector<int32_t> order(m->n_cells);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    return (m->off[x + 1] - m->off[x]) > (m->off[y + 1] - m->off[y]);
+  });
+  m->n_groups = (m->n_cells + cn::kLanes - 1) / cn::kLanes;
+  m->n_slots = m->n_groups * cn::kLanes;
+  m->cell_slot.assign(m->n_cells, -1);
+  std::vector<int32_t> slot_gid(m->n_slots, -1), slot_rows(m->n_slots, 0), slot_spike(m->n_slots, 0);
+  std::vector<double> slot_thresh(m->n_slots, 0.0);
+  for (int r = 0; r < m->n_cells; ++r) {
+    int c = order[r];
+    m->cell_slot[c] = r;
+    slot_gid[r] = c;
+    slot_rows[r] = m->off[c + 1] - m->off[c];
+    slot_spike[r] = m->spike_node[c];
+    slot_thresh[r] = m->thresh[c];
+  }
+  std::vector<int32_t> g_rows(m->n_groups, 0);
+  m->g_node_base.assign(m->n_groups, 0);
+  for (int s = 0; s < m->n_slots; ++s) g_rows[s / cn::kLanes] = std::max(g_rows[s / cn::kLanes], slot_rows[s]);
+  int64_t acc = 0;
+  for (int g = 0; g < m->n_groups; ++g) {
+    m->g_node_base[g] = acc;
+    acc += (int64_t)g_rows[g] * cn::kLanes;
+  }
+  m->node_elems = acc;
+  auto node_elem = [&](int64_t node) {
+    int c = m->node_cell[node];
+    int s = m->cell_slot[c];
+    return m->g_node_base[s / cn::kLanes] + (int64_t)(node - m->off[c]) * cn::kLanes + s % cn::kLanes;
+  };
+  // per-node inputs, interleaved
+  std::vector<double> h_area(acc, 1.0), h_ri(acc, 1.0), h_cm(acc, 1.0), h_gp(acc, 0.0), h_ep(acc, 0.0);
+  std::vector<int32_t> h_prow(acc, -1);
+  for (int64_t i = 0; i < m->n_nodes; ++i) {
+    int64_t e = node_elem(i);
+    h_area[e] = m->area[i];
+    h_ri[e] = m->ri[i];
+    h_cm[e] = m->cm[i];
+    h_prow[e] = m->parent[i];
+  }
+  for (size_t q = 0; q < m->pas_node.size(); ++q) {
+    int64_t e = node_elem(m->pas_node[q]);
+    h_gp[e] = m->pas_g[q];
+    h_ep[e] = m->pas_e[q];
+  }
+  // synapses, HH, stimuli, records
+  Rows rs = interleave(m, m->syn_node), rh = interleave(m, m->hh_node), rt = interleave(m, m->st_node),
+       rr = interleave(m, m->rec_node);
+  m->syn_slot = rs.inst_slot; m->syn_q = rs.inst_q;
+  m->hh_slot = rh.inst_slot; m->hh_q = rh.inst_q;
+  m->g_syn_base = rs.g_base;
+  m->g_hh_base = rh.g_base;
+  m->syn_elems = rs.elems; m->hh_elems = rh.elems; m->st_elems = rt.elems; m->rec_elems = rr.elems;
+  std::vector<int32_t> h_syn_row(rs.elems, 0);
+  std::vector<double> h_syn_tau(rs.elems, 1.0), h_syn_e(rs.elems, 0.0), h_syn_area(rs.elems, 1.0);
+  for (size_t i = 0; i < m->syn_node.size(); ++i) {
+    int64_t e = elem_of(rs, i);
+    int c = m->node_cell[m->syn_node[i]];
+    h_syn_row[e] = m->syn_node[i] - m->off[c];
+    h_syn_tau[e] = m->syn_tau[i];
+    h_syn_e[e] = m->syn_e[i];
+    h_syn_area[e] = m->area[m->syn_node[i]];
+  }
+  std::vector<int32_t> h_hh_row(rh.elems, 0);
+  std::vector<double> h_hh_p(6 * rh.elems, 0.0);
+  size_t nhh = m->hh_node.size();
+  for (size_t i = 0; i < nhh; ++i) {
+    int64_t e = elem_of(rh, i);
+    h_hh_row[e] = m->hh_node[i] - m->off[m->node_cell[m->hh_node[i]]];
+    for (int p = 0; p < 6; ++p) h_hh_p[p * rh.elems + e] = m->hh_par[p * nhh + i];
+  }
+  std::vector<int32_t> h_st_row(rt.elems, 0);
+  std::vector<double> h_st_del(rt.elems, 0.0), h_st_dur(rt.elems, 0.0), h_st_amp(rt.elems, 0.0),
+      h_st_area(rt.elems, 1.0);
+  for (size_t i = 0; i < m->st_node.size(); ++i) {
+    int64_t e = elem_of(rt, i);
+    h_st_row[e] = m->st_node[i] - m->off[m->node_cell[m->st_node[i]]];
+    h_st_del[e] = m->st_del[i];
+    h_st_dur[e] = m->st_dur[i];
+    h_st_amp[e] = m->st_amp[i];
+    h_st_area[e] = m->area[m->st_node[i]];
+  }
+  std::vector<int32_t> h_rec_row(rr.elems, 0), h_rec_id(rr.elems, 0);
+  for (size_t i = 0; i < m->rec_node.size(); ++i) {
+    int64_t e = elem_of(rr, i);
+    h_rec_row[e] = m->rec_node[i] - m->off[m->node_cell[m->rec_node[i]]];
+    h_rec_id[e] = (int32_t)i;
+  }
+  // incoming NetCons per target slot, by (source gid, NetCon index)
+  size_t nnc = m->nc_src.size();
+  std::vector<int64_t> in_off(m->n_slots + 1, 0);
+  std::vector<int32_t> nc_tslot(nnc);
+  for (size_t j = 0; j < nnc; ++j) {
+    nc_tslot[j] = rs.inst_slot[m->nc_syn[j]];
+    in_off[nc_tslot[j] + 1]++;
+  }
+  for (int s = 0; s < m->n_slots; ++s) in_off[s + 1] += in_off[s];
+  std::vector<int64_t> nc_order(nnc);
+  std::iota(nc_order.begin(), nc_order.end(), 0);
+  std::stable_sort(nc_order.begin(), nc_order.end(), [&](int64_t x, int64_t y) {
+    if (nc_tslot[x] != nc_tslot[y]) return nc_tslot[x] < nc_tslot[y];
+    return m->nc_src[x] < m->nc_src[y];
+  });
+  std::vector<int32_t> h_in_src(nnc), h_in_syn(nnc), h_in_ds(nnc);
+  std::vector<double> h_in_w(nnc);
+  for (size_t q = 0; q < nnc; ++q) {
+    int64_t j = nc_order[q];
+    h_in_src[q] = m->nc_src[j];
+    h_in_syn[q] = rs.inst_q[m->nc_syn[j]];
+    h_in_ds[q] = nc_ds[j];
+    h_in_w[q] = m->nc_w[j];
+  }
+  // external events per target slot, by (step, input index)
+  size_t nev = m->ev_syn.size();
+  std::vector<int64_t> x_off(m->n_slots + 1, 0), ev_step(nev);
+  std::vector<int32_t> ev_tslot(nev);
+  for (size_t e = 0; e < nev; ++e) {
+    ev_step[e] = std::max<int64_t>(0, round_half_away(m->ev_t[e] / dt));
+    ev_tslot[e] = rs.inst_slot[m->ev_syn[e]];
+    x_off[ev_tslot[e] + 1]++;
+  }
+  for (int s = 0; s < m->n_slots; ++s) x_off[s + 1] += x_off[s];
+  std::vector<int64_t> ev_order(nev);
+  std::iota(ev_order.begin(), ev_order.end(), 0);
+  std::stable_sort(ev_order.begin(), ev_order.end(), [&](int64_t x, int64_t y) {
+    if (ev_tslot[x] != ev_tslot[y]) return ev_tslot[x] < ev_tslot[y];
+    return ev_step[x] < ev_step[y];
+  });
+  std::vector<int64_t> h_x_step(nev);
+  std::vector<int32_t> h_x_syn(nev);
+  std::vector<double> h_x_w(nev);
+  for (size_t q = 0; q < nev; ++q) {
+    int64_t e = ev_order[q];
+    h_x_step[q] = ev_step[e];
+    h_x_syn[q] = rs.inst_q[m->ev_syn[e]];
+    h_x_w[q] = m->ev_w[e];
+  }
+
+  // ---- upload
+  dm = cn::DevModel{};
+  dm.n_groups = m->n_groups;
+  dm.n_slots = m->n_slots;
+  dm.n_cells = m->n_cells;
+  dm.D = m->D;
+  dm.n_rec = (int32_t)m->rec_node.size();
+  dm.dt = dt;
+  int64_t* p64;
+  int32_t* p32;
+  double* pd;
+  CN_CHECK(upload(m, &p64, m->g_node_base)); dm.g_node_base = p64;
+  CN_CHECK(upload(m, &p32, g_rows)); dm.g_rows = p32;
+  CN_CHECK(upload(m, &p64, rs.g_base)); dm.g_syn_base = p64;
+  CN_CHECK(upload(m, &p32, rs.g_rows)); dm.g_syn_rows = p32;
+  CN_CHECK(upload(m, &p64, rh.g_base)); dm.g_hh_base = p64;
+  CN_CHECK(upload(m, &p32, rh.g_rows)); dm.g_hh_rows = p32;
+  CN_CHECK(upload(m, &p64, rt.g_base)); dm.g_st_base = p64;
+  CN_CHECK(upload(m, &p32, rt.g_rows)); dm.g_st_rows = p32;
+  CN_CHECK(upload(m, &p64, rr.g_base)); dm.g_rec_base = p64;
+  CN_CHECK(upload(m, &p32, rr.g_rows)); dm.g_rec_rows = p32;
+  CN_CHECK(upload(m, &p32, slot_rows)); dm.s_rows = p32;
+  CN_CHECK(upload(m, &p32, rs.slot_n)); dm.s_nsyn = p32;
+  CN_CHECK(upload(m, &p32, rh.slot_n)); dm.s_nhh = p32;
+  CN_CHECK(upload(m, &p32, rt.slot_n)); dm.s_nst = p32;
+  CN_CHECK(upload(m, &p32, rr.slot_n)); dm.s_nrec = p32;
+  CN_CHECK(upload(m, &p32, slot_gid)); dm.s_gid = p32;
+  CN_CHECK(upload(m, &p32, slot_spike)); dm.s_spike_row = p32;
+  CN_CHECK(upload(m, &pd, slot_thresh)); dm.s_thresh = pd;
+  uint8_t* pu8;
+  CN_CHECK(zeros(m, &pu8, m->n_slots)); dm.s_above = pu8;
+  CN_CHECK(zeros(m, &pd, acc)); dm.v = pd;
+  CN_CHECK(zeros(m, &pd, acc)); dm.acc = pd;
+  CN_CHECK(zeros(m, &pd, acc)); dm.dacc = pd;
+  CN_CHECK(zeros(m, &pd, acc)); dm.a = pd;
+  CN_CHECK(zeros(m, &pd, acc)); dm.b = pd;
+  CN_CHECK(zeros(m, &pd, acc)); dm.cdt = pd;
+  CN_CHECK(zeros(m, &pd, acc)); dm.ge = pd;
+  CN_CHECK(zeros(m, &pd, acc)); dm.d0 = pd;
+  CN_CHECK(upload(m, &p32, h_prow)); dm.prow = p32;
+  CN_CHECK(upload(m, &p32, h_syn_row)); dm.syn_row = p32;
+  CN_CHECK(zeros(m, &pd, rs.elems)); dm.syn_g = pd;
+  CN_CHECK(zeros(m, &pd, rs.elems)); dm.syn_s = pd;
+  CN_CHECK(upload(m, &pd, h_syn_e)); dm.syn_e = pd;
+  CN_CHECK(zeros(m, &pd, rs.elems)); dm.syn_decay = pd;
+  CN_CHECK(upload(m, &p32, h_hh_row)); dm.hh_row = p32;
+  m->gate_bytes = m->opt.precision == CN_PREC_FP64 ? 8 : (m->opt.precision == CN_PREC_GATE_FP32 ? 4 : 2);
+  for (void** gp : {&dm.hh_m, &dm.hh_h, &dm.hh_n}) {
+    void* q = dalloc_raw(m, std::max<int64_t>(rh.elems, 1) * m->gate_bytes);
+    if (!q) return m->fail(CN_ENOMEM, "device allocation failed");
+    CN_TRY_CUDA(m, cudaMemsetAsync(q, 0, std::max<int64_t>(rh.elems, 1) * m->gate_bytes, m->stream));
+    *gp = q;
+  }
+  CN_CHECK(upload(m, &pd, h_hh_p)); dm.hh_p = pd;
+  dm.hh_elems = rh.elems;
+  CN_CHECK(upload(m, &p32, h_st_row)); dm.st_row = p32;
+  CN_CHECK(upload(m, &pd, h_st_del)); dm.st_del = pd;
+  CN_CHECK(upload(m, &pd, h_st_dur)); dm.st_dur = pd;
+  CN_CHECK(zeros(m, &pd, rt.elems)); dm.st_amp = pd;
+  CN_CHECK(upload(m, &p32, h_rec_row)); dm.rec_row = p32;
+  CN_CHECK(upload(m, &p32, h_rec_id)); dm.rec_id = p32;
+  CN_CHECK(zeros(m, &p32, m->n_slots)); dm.ev_count = p32;
+  cn::EvRec* pev = static_cast<cn::EvRec*>(dalloc_raw(m, (size_t)m->n_slots * cn::kEvCap * sizeof(cn::EvRec)));
+  if (!pev) return m->fail(CN_ENOMEM, "device allocation failed");
+  dm.ev_buf = pev;
+  CN_CHECK(upload(m, &p64, x_off)); dm.x_off = p64;
+  std::vector<int64_t> x_pos(x_off.begin(), x_off.end() - 1);
+  CN_CHECK(upload(m, &p64, x_pos)); dm.x_pos = p64;
+  CN_CHECK(upload(m, &p64, h_x_step)); dm.x_step = p64;
+  CN_CHECK(upload(m, &p32, h_x_syn)); dm.x_syn = p32;
+  CN_CHECK(upload(m, &pd, h_x_w)); dm.x_w = pd;
+  CN_CHECK(upload(m, &p64, in_off)); dm.in_off = p64;
+  CN_CHECK(upload(m, &p32, h_in_src)); dm.in_src = p32;
+  CN_CHECK(upload(m, &p32, h_in_syn)); dm.in_syn = p32;
+  CN_CHECK(upload(m, &p32, h_in_ds)); dm.in_dsteps = p32;
+  CN_CHECK(upload(m, &pd, h_in_w)); dm.in_w = pd;
+  CN_CHECK(zeros(m, &p32, 1)); dm.status = p32;
+  dm.hist = nullptr;
+  dm.trace = nullptr;
+
+  // temporaries for the setup kernels
+  double *d_area, *d_ri, *d_cm, *d_gp, *d_ep, *d_syn_area, *d_syn_tau, *d_st_amp, *d_st_area;
+  CN_CHECK(upload(m, &d_area, h_area));
+  CN_CHECK(upload(m, &d_ri, h_ri));
+  CN_CHECK(upload(m, &d_cm, h_cm));
+  CN_CHECK(upload(m, &d_gp, h_gp));
+  CN_CHECK(upload(m, &d_ep, h_ep));
+  CN_CHECK(upload(m, &d_syn_area, h_syn_area));
+  CN_CHECK(upload(m, &d_syn_tau, h_syn_tau));
+  CN_CHECK(upload(m, &d_st_amp, h_st_amp));
+  CN_CHECK(upload(m, &d_st_area, h_st_area));
+  const int tb = 128, nb = (m->n_slots + tb - 1) / tb;
+  cudaStream_t st = m->stream;
+  double v0 = m->opt.v_init_mV;
+  CN_CHECK(launch_checked(m, [&] { cn::k_setup_nodes<<<nb, tb, 0, st>>>(dm, d_area, d_ri, d_cm, d_gp, d_ep, v0); }));
+  CN_CHECK(launch_checked(m, [&] { cn::k_setup_syn<<<nb, tb, 0, st>>>(dm, d_syn_area, d_syn_tau); }));
+  switch (m->opt.precision) {
+    case CN_PREC_FP64: CN_CHECK(launch_checked(m, [&] { cn::k_setup_hh<0><<<nb, tb, 0, st>>>(dm, v0); })); break;
+    case CN_PREC_GATE_FP32: CN_CHECK(launch_checked(m, [&] { cn::k_setup_hh<1><<<nb, tb, 0, st>>>(dm, v0); })); break;
+    default: CN_CHECK(launch_checked(m, [&] { cn::k_setup_hh<2><<<nb, tb, 0, st>>>(dm, v0); })); break;
+  }
+  CN_CHECK(launch_checked(m, [&] { cn::k_setup_stim<<<nb, tb, 0, st>>>(dm, d_st_amp, d_st_area); }));
+  CN_CHECK(launch_checked(m, [&] { cn::k_init_above<<<nb, tb, 0, st>>>(dm); }));
+  CN_TRY_CUDA(m, cudaStreamSynchronize(st));
+  for (double* p : {d_area, d_ri, d_cm, d_gp, d_ep, d_syn_area, d_syn_tau, d_st_amp, d_st_area}) dfree_raw(m, p);
+  m->finalized = true;
+  m->cells_nodes = m->n_nodes;
+  return CN_OK;
+}
+
+// Grow a device buffer to n elements, keeping old contents.
+template <class T>
+cn_status grow(cn_model* m, T** p, int64_t old_n, int64_t new_n) {
+  T* q = static_cast<T*>(dalloc_raw(m, (size_t)new_n * sizeof(T)));
+  if (!q) return m->fail(CN_ENOMEM, "device allocation failed");
+  CN_TRY_CUDA(m, cudaMemsetAsync(q, 0, (size_t)new_n * sizeof(T), m->stream));
+  if (*p && old_n > 0)
+    CN_TRY_CUDA(m, cudaMemcpyAsync(q, *p, (size_t)old_n * sizeof(T), cudaMemcpyDeviceToDevice, m->stream));
+  if (*p) {
+    CN_TRY_CUDA(m, cudaStreamSynchronize(m->stream));
+    dfree_raw(m, *p);
+  }
+  *p = q;
+  return CN_OK;
+}
+
+cn_status ensure_capacity(cn_model* m, int64_t K) {
+  int64_t need_int = (K + m->D - 1) / m->D + 1;
+  if (need_int > m->hist_cap) {
+    int64_t nc = std::max(need_int, m->hist_cap * 2);
+    CN_CHECK(grow(m, &m->dm.hist, m->hist_cap * m->n_cells, nc * m->n_cells));
+    m->hist_cap = nc;
+  }
+  if (!m->rec_node.empty() && K + 1 > m->trace_cap) {
+    int64_t nc = std::max(K + 1, m->trace_cap * 2);
+    bool first = m->trace_cap == 0;
+    CN_CHECK(grow(m, &m->dm.trace, m->trace_cap * m->dm.n_rec, nc * m->dm.n_rec));
+    m->trace_cap = nc;
+    if (first) {
+      const int tb = 128, nb = (m->n_slots + tb - 1) / tb;
+      cn::DevModel dm = m->dm;
+      int64_t k = m->step;
+      CN_CHECK(launch_checked(m, [&] { cn::k_record0<<<nb, tb, 0, m->stream>>>(dm, k); }));
+    }
+  }
+  return CN_OK;
+}
+
+cudaEvent_t take_event(cn_model* m) {
+  if (!m->ev_pool.empty()) {
+    cudaEvent_t e = m->ev_pool.back();
+    m->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+cn_status launch_interval(cn_model* m, int64_t J, int s0, int s1) {
+  cn::DevModel dm = m->dm;
+  cudaStream_t st = m->stream;
+  const int wpb = 1;
+  const int blocks = (m->n_groups + wpb - 1) / wpb;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (s0 == 0) {
+    const int tb = 128, nb = (m->n_slots + tb - 1) / tb;
+    if (m->profiling) {
+      e0 = take_event(m);
+      e1 = take_event(m);
+      CN_TRY_CUDA(m, cudaEventRecord(e0, st));
+    }
+    CN_CHECK(launch_checked(m, [&] { cn::k_pull_events<<<nb, tb, 0, st>>>(dm, J); }));
+    if (m->profiling) {
+      CN_TRY_CUDA(m, cudaEventRecord(e1, st));
+      m->ev_pull.emplace_back(e0, e1);
+    }
+  }
+  if (m->profiling) {
+    e0 = take_event(m);
+    e1 = take_event(m);
+    CN_TRY_CUDA(m, cudaEventRecord(e0, st));
+  }
+  switch (m->opt.precision) {
+    case CN_PREC_FP64:
+      CN_CHECK(launch_checked(m, [&] { cn::k_interval<0><<<blocks, 32 * wpb, 0, st>>>(dm, J, s0, s1); }));
+      break;
+    case CN_PREC_GATE_FP32:
+      CN_CHECK(launch_checked(m, [&] { cn::k_interval<1><<<blocks, 32 * wpb, 0, st>>>(dm, J, s0, s1); }));
+      break;
+    default:
+      CN_CHECK(launch_checked(m, [&] { cn::k_interval<2><<<blocks, 32 * wpb, 0, st>>>(dm, J, s0, s1); }));
+      break;
+  }
+  if (m->profiling) {
+    CN_TRY_CUDA(m, cudaEventRecord(e1, st));
+    m->ev_interval.emplace_back(e0, e1);
+  }
+  return CN_OK;
+}
+
+}  // namespace
+
+// ====================================================================== ABI
+extern "C" {
+
+int32_t cn_mech_nparams(int32_t type) {
+  return (type >= 0 && type < CN_MECH_NTYPES) ? kNParams[type] : -1;
+}
+
+void cn_options_default(cn_options* opt) {
+  std::memset(opt, 0, sizeof(*opt));
+  opt->dt_ms = 0.025;
+  opt->v_init_mV = -65.0;
+  opt->precision = CN_PREC_FP64;
+  opt->device = 0;
+  opt->mapping = CN_MAP_AUTO;
+  opt->use_graph = 1;
+}
+
+cn_status cn_geometry(int32_t n_cells, const int32_t* cell_offset, const int32_t* parent,
+                      const double* dx_um, const double* diam_um, const double* Ra_ohm_cm,
+                      double* area_um2, double* ri_MOhm) {
+  if (n_cells < 0 || !cell_offset || (n_cells > 0 && (!parent || !dx_um || !diam_um || !Ra_ohm_cm ||
+                                                      !area_um2 || !ri_MOhm)))
+    return CN_EINVAL;
+  const double pi = 3.14159265358979323846;
+  int64_t n = cell_offset[n_cells];
+  std::vector<double> rhalf(n);
+  for (int64_t i = 0; i < n; ++i) {
+    if (!(dx_um[i] > 0) || !(diam_um[i] > 0) || !(Ra_ohm_cm[i] > 0)) return CN_EINVAL;
+    area_um2[i] = pi * diam_um[i] * dx_um[i];
+    rhalf[i] = 1e-2 * 2.0 * Ra_ohm_cm[i] * dx_um[i] / (pi * diam_um[i] * diam_um[i]);
+  }
+  for (int c = 0; c < n_cells; ++c) {
+    for (int64_t i = cell_offset[c]; i < cell_offset[c + 1]; ++i) {
+      int64_t li = i - cell_offset[c];
+      int32_t p = parent[i];
+      if ((li == 0) != (p == -1) || p >= li || p < -1) return CN_EINVAL;
+      ri_MOhm[i] = p < 0 ? 0.0 : rhalf[i] + rhalf[cell_offset[c] + p];
+    }
+  }
+  return CN_OK;
+}
+
+cn_status cn_model_create(const cn_morph* morph, const cn_mech_table* mechs, int32_t n_mechs,
+                          const cn_options* opt, cn_model** out) {
+  g_create_error.clear();
+  auto bad = [](const std::string& s) {
+    g_create_error = s;
+    return CN_EINVAL;
+  };
+  if (!morph || !out || n_mechs < 0 || (n_mechs > 0 && !mechs)) return bad("null argument");
+  *out = nullptr;
+  cn_options o;
+  if (opt) o = *opt;
+  else cn_options_default(&o);
+  if (!(o.dt_ms > 0) || !std::isfinite(o.v_init_mV)) return bad("bad dt or v_init");
+  if (o.precision < 0 || o.precision > 2) return bad("bad precision");
+  if ((o.alloc == nullptr) != (o.free == nullptr)) return bad("alloc and free must be given together");
+  const int32_t nc = morph->n_cells;
+  if (nc <= 0 || !morph->cell_offset || !morph->parent || !morph->area_um2 || !morph->cm_uF_cm2 ||
+      !morph->ri_MOhm || !morph->spike_node || !morph->threshold_mV)
+    return bad("incomplete morphology");
+  if (morph->cell_offset[0] != 0) return bad("cell_offset[0] must be 0");
+  for (int c = 0; c < nc; ++c)
+    if (morph->cell_offset[c + 1] <= morph->cell_offset[c]) return bad("empty cell or decreasing cell_offset");
+  const int64_t nn = morph->cell_offset[nc];
+  for (int c = 0; c < nc; ++c) {
+    const int32_t a0 = morph->cell_offset[c], a1 = morph->cell_offset[c + 1];
+    if (a1 - a0 > (1 << 24)) return bad("cell too large");
+    for (int32_t i = a0; i < a1; ++i) {
+      const int32_t li = i - a0, p = morph->parent[i];
+      if (li == 0 ? p != -1 : (p < 0 || p >= li)) return bad("parent must satisfy parent[0] = -1, 0 <= parent[i] < i");
+      if (!(morph->area_um2[i] > 0) || !(morph->cm_uF_cm2[i] > 0) || (li > 0 && !(morph->ri_MOhm[i] > 0)))
+        return bad("non-positive area, cm or ri");
+    }
+    if (morph->spike_node[c] < 0 || morph->spike_node[c] >= a1 - a0) return bad("spike_node out of range");
+    if (!std::isfinite(morph->threshold_mV[c])) return bad("bad threshold");
+  }
+  cn_model* m = new (std::nothrow) cn_model();
+  if (!m) {
+    g_create_error = "host allocation failed";
+    return CN_ENOMEM;
+  }
+  m->opt = o;
+  m->stream = static_cast<cudaStream_t>(o.stream);
+  m->n_cells = nc;
+  m->n_nodes = nn;
+  m->off.assign(morph->cell_offset, morph->cell_offset + nc + 1);
+  m->parent.assign(morph->parent, morph->parent + nn);
+  m->area.assign(morph->area_um2, morph->area_um2 + nn);
+  m->cm.assign(morph->cm_uF_cm2, morph->cm_uF_cm2 + nn);
+  m->ri.assign(morph->ri_MOhm, morph->ri_MOhm + nn);
+  m->spike_node.assign(morph->spike_node, morph->spike_node + nc);
+  m->thresh.assign(morph->threshold_mV, morph->threshold_mV + nc);
+  m->node_cell.resize(nn);
+  for (int c = 0; c < nc; ++c)
+    for (int32_t i = m->off[c]; i < m->off[c + 1]; ++i) m->node_cell[i] = c;
+  bool seen[CN_MECH_NTYPES] = {};
+  std::vector<uint8_t> has_pas(nn, 0);
+  for (int t = 0; t < n_mechs; ++t) {
+    const cn_mech_table& mt = mechs[t];
+    if (mt.type < 0 || mt.type >= CN_MECH_NTYPES) { delete m; return bad("unknown mechanism type"); }
+    if (seen[mt.type]) { delete m; return bad("duplicate mechanism table"); }
+    seen[mt.type] = true;
+    if (mt.n < 0 || (mt.n > 0 && (!mt.node || !mt.param))) { delete m; return bad("bad mechanism table"); }
+    for (int i = 0; i < mt.n; ++i)
+      if (mt.node[i] < 0 || mt.node[i] >= nn) { delete m; return bad("mechanism node out of range"); }
+    const int np = kNParams[mt.type];
+    auto col = [&](int p, int i) { return mt.param[(int64_t)p * mt.n + i]; };
+    switch (mt.type) {
+      case CN_MECH_PAS:
+        for (int i = 0; i < mt.n; ++i) {
+          if (has_pas[mt.node[i]]) { delete m; return bad("at most one pas instance per node"); }
+          has_pas[mt.node[i]] = 1;
+          m->pas_node.push_back(mt.node[i]);
+          m->pas_g.push_back(col(0, i));
+          m->pas_e.push_back(col(1, i));
+        }
+        break;
+      case CN_MECH_HH:
+        m->hh_node.assign(mt.node, mt.node + mt.n);
+        m->hh_par.assign(mt.param, mt.param + (int64_t)np * mt.n);
+        break;
+      case CN_MECH_EXPSYN:
+        for (int i = 0; i < mt.n; ++i)
+          if (!(col(0, i) > 0)) { delete m; return bad("ExpSyn tau must be positive"); }
+        m->syn_node.assign(mt.node, mt.node + mt.n);
+        m->syn_tau.assign(mt.param, mt.param + mt.n);
+        m->syn_e.assign(mt.param + mt.n, mt.param + 2 * (int64_t)mt.n);
+        break;
+      default:
+        if (mt.n > 0) { delete m; return bad("mechanism type not supported by this mapping"); }
+    }
+  }
+  cudaError_t e = cudaSetDevice(o.device);
+  if (e != cudaSuccess) {
+    g_create_error = std::string("cudaSetDevice: ") + cudaGetErrorString(e);
+    delete m;
+    return CN_ECUDA;
+  }
+  *out = m;
+  return CN_OK;
+}
+
+static cn_status state_check(cn_model* m) {
+  if (!m) return CN_EINVAL;
+  if (m->finalized) return m->fail(CN_ESTATE, "model already running: add inputs before the first cn_run");
+  return CN_OK;
+}
+
+cn_status cn_add_netcons(cn_model* m, int64_t n, const int32_t* src, const int32_t* syn, const double* w,
+                         const double* delay) {
+  CN_CHECK(state_check(m));
+  if (n < 0 || (n > 0 && (!src || !syn || !w || !delay))) return m->fail(CN_EINVAL, "bad netcon arrays");
+  for (int64_t j = 0; j < n; ++j) {
+    if (src[j] < 0 || src[j] >= m->n_cells) return m->fail(CN_EINVAL, "NetCon source out of range");
+    if (syn[j] < 0 || syn[j] >= (int64_t)m->syn_node.size()) return m->fail(CN_EINVAL, "NetCon target out of range");
+    if (!std::isfinite(w[j]) || !(delay[j] > 0)) return m->fail(CN_EINVAL, "bad NetCon weight or delay");
+  }
+  m->nc_src.insert(m->nc_src.end(), src, src + n);
+  m->nc_syn.insert(m->nc_syn.end(), syn, syn + n);
+  m->nc_w.insert(m->nc_w.end(), w, w + n);
+  m->nc_delay.insert(m->nc_delay.end(), delay, delay + n);
+  return CN_OK;
+}
+
+cn_status cn_add_netcon(cn_model* m, int32_t src, int32_t syn, double w, double delay) {
+  return cn_add_netcons(m, 1, &src, &syn, &w, &delay);
+}
+
+cn_status cn_add_events(cn_model* m, int64_t n, const int32_t* syn, const double* t, const double* w) {
+  CN_CHECK(state_check(m));
+  if (n < 0 || (n > 0 && (!syn || !t || !w))) return m->fail(CN_EINVAL, "bad event arrays");
+  for (int64_t e = 0; e < n; ++e) {
+    if (syn[e] < 0 || syn[e] >= (int64_t)m->syn_node.size()) return m->fail(CN_EINVAL, "event target out of range");
+    if (!std::isfinite(t[e]) || !std::isfinite(w[e])) return m->fail(CN_EINVAL, "bad event time or weight");
+  }
+  m->ev_syn.insert(m->ev_syn.end(), syn, syn + n);
+  m->ev_t.insert(m->ev_t.end(), t, t + n);
+  m->ev_w.insert(m->ev_w.end(), w, w + n);
+  return CN_OK;
+}
+
+cn_status cn_add_stim(cn_model* m, int32_t node, double del, double dur, double amp) {
+  CN_CHECK(state_check(m));
+  if (node < 0 || node >= m->n_nodes) return m->fail(CN_EINVAL, "stimulus node out of range");
+  if (!std::isfinite(del) || !std::isfinite(dur) || !std::isfinite(amp)) return m->fail(CN_EINVAL, "bad stimulus");
+  m->st_node.push_back(node);
+  m->st_del.push_back(del);
+  m->st_dur.push_back(dur);
+  m->st_amp.push_back(amp);
+  return CN_OK;
+}
+
+cn_status cn_record(cn_model* m, int32_t node, int32_t* rec_id) {
+  CN_CHECK(state_check(m));
+  if (node < 0 || node >= m->n_nodes || !rec_id) return m->fail(CN_EINVAL, "record node out of range");
+  *rec_id = (int32_t)m->rec_node.size();
+  m->rec_node.push_back(node);
+  return CN_OK;
+}
+
+cn_status cn_run(cn_model* m, double tstop_ms) {
+  if (!m) return CN_EINVAL;
+  if (!std::isfinite(tstop_ms)) return m->fail(CN_EINVAL, "bad tstop");
+  const int64_t K = round_half_away(tstop_ms / m->opt.dt_ms);
+  if (K < m->step) return m->fail(CN_EINVAL, "tstop is behind the current time");
+  CN_TRY_CUDA(m, cudaSetDevice(m->opt.device));
+  if (!m->finalized) CN_CHECK(finalize(m));
+  CN_CHECK(ensure_capacity(m, K));
+  while (m->step < K) {
+    const int64_t J = m->step / m->D;
+    const int s0 = (int)(m->step - J * m->D);
+    const int s1 = (int)std::min<int64_t>(m->D, K - J * m->D);
+    CN_CHECK(launch_interval(m, J, s0, s1));
+    m->step = J * m->D + s1;
+  }
+  return CN_OK;
+}
+
+cn_status cn_sync(cn_model* m) {
+  if (!m) return CN_EINVAL;
+  if (!m->finalized) return CN_OK;
+  CN_TRY_CUDA(m, cudaStreamSynchronize(m->stream));
+  int32_t st = 0;
+  CN_TRY_CUDA(m, cudaMemcpy(&st, m->dm.status, sizeof(st), cudaMemcpyDeviceToHost));
+  if (st & cn::kStatusEvOverflow)
+    return m->fail(CN_ERANGE, "more than 256 events arrived at one cell within one interval");
+  return CN_OK;
+}
+
+int64_t cn_current_step(const cn_model* m) { return m ? m->step : -1; }
+int64_t cn_updates(const cn_model* m) { return m ? m->n_nodes * m->step : 0; }
+int64_t cn_launch_count(const cn_model* m) { return m ? m->launches : 0; }
+
+cn_status cn_get_spikes(cn_model* m, int32_t* gid, int64_t* step, size_t cap, size_t* n) {
+  if (!m || !n) return CN_EINVAL;
+  *n = 0;
+  if (!m->finalized) return CN_OK;
+  CN_CHECK(cn_sync(m));
+  const int64_t nint = (m->step + m->D - 1) / m->D;
+  std::vector<uint64_t> h((size_t)nint * m->n_cells);
+  if (!h.empty())
+    CN_TRY_CUDA(m, cudaMemcpy(h.data(), m->dm.hist, h.size() * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+  std::vector<std::pair<int64_t, int32_t>> sp;
+  for (int64_t J = 0; J < nint; ++J)
+    for (int32_t c = 0; c < m->n_cells; ++c) {
+      uint64_t mk = h[(size_t)J * m->n_cells + c];
+      while (mk) {
+        int b = __builtin_ctzll(mk);
+        mk &= mk - 1;
+        sp.emplace_back(J * m->D + b + 1, c);
+      }
+    }
+  std::sort(sp.begin(), sp.end());
+  *n = sp.size();
+  if (!gid || !step) return CN_OK;
+  if (cap < sp.size()) return m->fail(CN_ERANGE, "spike buffer too small");
+  for (size_t i = 0; i < sp.size(); ++i) {
+    gid[i] = sp[i].second;
+    step[i] = sp[i].first;
+  }
+  return CN_OK;
+}
+
+cn_status cn_get_trace(cn_model* m, int32_t rec_id, double* out, size_t cap, size_t* n) {
+  if (!m || !n) return CN_EINVAL;
+  if (rec_id < 0 || rec_id >= (int32_t)m->rec_node.size()) return m->fail(CN_EINVAL, "bad record id");
+  *n = (size_t)m->step + 1;
+  if (!out) return CN_OK;
+  if (cap < *n) return m->fail(CN_ERANGE, "trace buffer too small");
+  if (!m->finalized) {
+    out[0] = m->opt.v_init_mV;
+    return CN_OK;
+  }
+  CN_CHECK(cn_sync(m));
+  const int nr = m->dm.n_rec;
+  CN_TRY_CUDA(m, cudaMemcpy2D(out, sizeof(double), m->dm.trace + rec_id, nr * sizeof(double), sizeof(double),
+                              *n, cudaMemcpyDeviceToHost));
+  return CN_OK;
+}
+
+cn_status cn_get_v(cn_model* m, double* out, size_t cap) {
+  if (!m || !out) return CN_EINVAL;
+  if (cap < (size_t)m->n_nodes) return m->fail(CN_ERANGE, "buffer too small");
+  if (!m->finalized) {
+    for (int64_t i = 0; i < m->n_nodes; ++i) out[i] = m->opt.v_init_mV;
+    return CN_OK;
+  }
+  CN_CHECK(cn_sync(m));
+  std::vector<double> h(m->node_elems);
+  CN_TRY_CUDA(m, cudaMemcpy(h.data(), m->dm.v, h.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  for (int64_t i = 0; i < m->n_nodes; ++i) {
+    int c = m->node_cell[i];
+    int s = m->cell_slot[c];
+    out[i] = h[m->g_node_base[s / cn::kLanes] + (int64_t)(i - m->off[c]) * cn::kLanes + s % cn::kLanes];
+  }
+  return CN_OK;
+}
+
+static double gate_to_double(const void* base, int64_t e, int bytes) {
+  if (bytes == 8) return static_cast<const double*>(base)[e];
+  if (bytes == 4) return static_cast<const float*>(base)[e];
+  uint16_t hb = static_cast<const uint16_t*>(base)[e];
+  uint32_t fb = (uint32_t)hb << 16;
+  float f;
+  std::memcpy(&f, &fb, 4);
+  return f;
+}
+
+cn_status cn_get_state(cn_model* m, int32_t type, int32_t col, double* out, size_t cap) {
+  if (!m || !out) return CN_EINVAL;
+  if (!m->finalized) return m->fail(CN_ESTATE, "state is built at the first cn_run");
+  CN_CHECK(cn_sync(m));
+  if (type == CN_MECH_HH && col >= 0 && col < 3) {
+    size_t n = m->hh_node.size();
+    if (cap < n) return m->fail(CN_ERANGE, "buffer too small");
+    const void* src = col == 0 ? m->dm.hh_m : (col == 1 ? m->dm.hh_h : m->dm.hh_n);
+    std::vector<uint8_t> h((size_t)std::max<int64_t>(m->hh_elems, 1) * m->gate_bytes);
+    CN_TRY_CUDA(m, cudaMemcpy(h.data(), src, h.size(), cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < n; ++i) {
+      int s = m->hh_slot[i];
+      int64_t e = m->g_hh_base[s / cn::kLanes] + (int64_t)m->hh_q[i] * cn::kLanes + s % cn::kLanes;
+      out[i] = gate_to_double(h.data(), e, m->gate_bytes);
+    }
+    return CN_OK;
+  }
+  if (type == CN_MECH_EXPSYN && col == 0) {
+    size_t n = m->syn_node.size();
+    if (cap < n) return m->fail(CN_ERANGE, "buffer too small");
+    std::vector<double> h(std::max<int64_t>(m->syn_elems, 1));
+    CN_TRY_CUDA(m, cudaMemcpy(h.data(), m->dm.syn_g, h.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < n; ++i) {
+      int s = m->syn_slot[i];
+      out[i] = h[m->g_syn_base[s / cn::kLanes] + (int64_t)m->syn_q[i] * cn::kLanes + s % cn::kLanes];
+    }
+    return CN_OK;
+  }
+  return m->fail(CN_EINVAL, "no such state column");
+}
+
+cn_status cn_profile(cn_model* m, int32_t enable) {
+  if (!m) return CN_EINVAL;
+  m->profiling = enable != 0;
+  return CN_OK;
+}
+
+cn_status cn_profile_read(cn_model* m, double* interval_ms, int64_t* interval_launches, double* pull_ms,
+                          int64_t* pull_launches) {
+  if (!m) return CN_EINVAL;
+  CN_TRY_CUDA(m, cudaStreamSynchronize(m->stream));
+  auto sum = [&](std::vector<std::pair<cudaEvent_t, cudaEvent_t>>& v, double* ms, int64_t* cnt) -> cn_status {
+    double t = 0.0;
+    for (auto& pr : v) {
+      float x = 0.f;
+      CN_TRY_CUDA(m, cudaEventElapsedTime(&x, pr.first, pr.second));
+      t += x;
+      m->ev_pool.push_back(pr.first);
+      m->ev_pool.push_back(pr.second);
+    }
+    if (ms) *ms = t;
+    if (cnt) *cnt = (int64_t)v.size();
+    v.clear();
+    return CN_OK;
+  };
+  CN_CHECK(sum(m->ev_interval, interval_ms, interval_launches));
+  CN_CHECK(sum(m->ev_pull, pull_ms, pull_launches));
+  return CN_OK;
+}
+
+const char* cn_last_error(const cn_model* m) {
+  if (!m) return g_create_error.c_str();
+  return m->err.c_str();
+}
+
+void cn_model_destroy(cn_model* m) {
+  if (!m) return;
+  if (m->stream || m->finalized) cudaStreamSynchronize(m->stream);
+  std::vector<void*> all = m->allocs;
+  for (void* p : all) dfree_raw(m, p);
+  for (auto& pr : m->ev_interval) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
+  for (auto& pr : m->ev_pull) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
+  for (cudaEvent_t e : m->ev_pool) cudaEventDestroy(e);
+  delete m;
+}
+
+}  // extern "C"

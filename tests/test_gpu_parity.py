@@ -1,0 +1,197 @@
+"""CUDA engine vs FP64 oracle, element by element, through the C ABI.
+
+Bar (FP64 path): spike raster (gid, step) bit-exact; every voltage within
+1e-9 mV of the oracle; gating states within 1e-9 (they are O(1)).
+"""
+import numpy as np
+import pytest
+
+from scenarios import ring16, network, adjoint_net, single_compartment, passive_cable
+from oracle import simulate
+
+pytestmark = pytest.mark.gpu
+
+V_TOL = 1e-9      # mV, FP64 path
+GATE_TOL = 1e-9
+
+
+@pytest.fixture(scope="module")
+def cn():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1901_10975_gb300 import build
+    build.build()
+    from paper_1901_10975_gb300 import cn as _cn
+    return _cn
+
+
+def run_gpu(cn, sc, precision="fp64", tstop=None, chunks=None):
+    md = cn.from_scenario(sc, precision=precision)
+    tstop = sc.tstop if tstop is None else tstop
+    if chunks:
+        for t in chunks:
+            md.cn_run(t)
+    md.cn_run(tstop)
+    md.cn_sync()
+    g, k = md.cn_get_spikes()
+    tr = np.stack([md.cn_get_trace(r) for r in range(len(sc.rec_node))]) if len(sc.rec_node) else None
+    v = md.cn_get_v()
+    out = {"g": g, "k": k, "tr": tr, "v": v, "model": md}
+    hh = sc.mech("hh")
+    if hh is not None and hh.n:
+        out["hh"] = [md.cn_get_state("hh", c, hh.n) for c in range(3)]
+    syn = sc.mech("expsyn")
+    if syn is not None and syn.n:
+        out["syn"] = md.cn_get_state("expsyn", 0, syn.n)
+    return out
+
+
+def run_oracle(sc, nsteps=None, nthreads=None):
+    m = simulate(sc, nsteps=nsteps, nthreads=nthreads)
+    g, k = m.spikes()
+    out = {"g": g, "k": k, "tr": m.traces() if len(sc.rec_node) else None, "v": m.v()}
+    hh = sc.mech("hh")
+    if hh is not None and hh.n:
+        out["hh"] = [m.state("hh", c) for c in range(3)]
+    syn = sc.mech("expsyn")
+    if syn is not None and syn.n:
+        out["syn"] = m.state("expsyn", 0)
+    return out
+
+
+def assert_parity(gpu, ref, v_tol=V_TOL, gate_tol=GATE_TOL):
+    assert np.array_equal(gpu["g"], ref["g"]) and np.array_equal(gpu["k"], ref["k"]), \
+        (gpu["g"][:10], gpu["k"][:10], ref["g"][:10], ref["k"][:10])
+    if ref["tr"] is not None:
+        assert gpu["tr"].shape == ref["tr"].shape
+        err = np.max(np.abs(gpu["tr"] - ref["tr"]))
+        assert err <= v_tol, f"trace error {err}"
+    err_v = np.max(np.abs(gpu["v"] - ref["v"]))
+    assert err_v <= v_tol, f"voltage error {err_v}"
+    if "hh" in ref:
+        for c in range(3):
+            assert np.max(np.abs(gpu["hh"][c] - ref["hh"][c])) <= gate_tol
+    if "syn" in ref:
+        assert np.max(np.abs(gpu["syn"] - ref["syn"])) <= 1e-12 * max(1.0, np.max(np.abs(ref["syn"])))
+
+
+def test_ring16_fp64(cn):
+    """Ring of 16 (the Ring model's shape): raster bit-exact, v within 1e-9 mV."""
+    sc = ring16()
+    ref = run_oracle(sc, nthreads=1)
+    gpu = run_gpu(cn, sc)
+    assert len(ref["g"]) >= 5
+    assert_parity(gpu, ref)
+
+
+def test_ring16_strong_many_laps(cn):
+    sc = ring16(weight=0.02, tstop=300.0)
+    ref = run_oracle(sc, nthreads=1)
+    gpu = run_gpu(cn, sc)
+    assert len(ref["g"]) > 32
+    assert_parity(gpu, ref)
+
+
+def test_network_reduced_ragged(cn):
+    """Network shape (200-600 compartments, 50 ExpSyn, 100 NetCons, 5 Hz
+    background) cut to 500 cells (15 full warps and a ragged tail) x 50 ms."""
+    sc = network(n_cells=500, tstop=50.0)
+    ref = run_oracle(sc)
+    gpu = run_gpu(cn, sc)
+    assert_parity(gpu, ref)
+
+
+def test_network_driven_spiking(cn):
+    """Stronger synapses so that cells fire and NetCon events flow: exercises
+    the interval exchange, delivery order and threshold detection."""
+    sc = network(n_cells=300, tstop=60.0, w_median=0.03, bg_w=0.03, bg_rate_hz=30.0)
+    ref = run_oracle(sc)
+    assert len(ref["g"]) > 50
+    gpu = run_gpu(cn, sc)
+    assert_parity(gpu, ref)
+
+
+def test_network_full_size_short(cn):
+    """All 16,384 cells of the network workload, 10 ms, every soma trace and
+    every node voltage against the oracle."""
+    sc = network(tstop=10.0)
+    ref = run_oracle(sc)
+    gpu = run_gpu(cn, sc)
+    assert_parity(gpu, ref)
+
+
+def test_partial_intervals_and_resume(cn):
+    """cn_run to times that are not interval boundaries, then continue."""
+    sc = network(n_cells=70, tstop=20.0, w_median=0.03, bg_w=0.03, bg_rate_hz=30.0)
+    ref = run_oracle(sc)
+    gpu = run_gpu(cn, sc, chunks=[0.0, 0.3, 1.0, 1.525, 7.0, 13.3])
+    assert_parity(gpu, ref)
+
+
+def test_stimulus_and_single_compartment(cn):
+    sc = single_compartment(mech="hh", tstop=30.0, stim_amp=0.3, stim_del=1.0, stim_dur=1.0)
+    ref = run_oracle(sc)
+    gpu = run_gpu(cn, sc)
+    assert len(ref["g"]) == 1
+    assert_parity(gpu, ref)
+
+
+def test_adjoint_shape_forward(cn):
+    """Clamp-driven unconnected cells (the adjoint workload's forward pass)."""
+    sc = adjoint_net(n_cells=70, tstop=30.0)
+    ref = run_oracle(sc)
+    gpu = run_gpu(cn, sc)
+    assert_parity(gpu, ref)
+
+
+def test_passive_cable_long_chain(cn):
+    """One 2,000-node unbranched cable (deep chain, one lane busy)."""
+    sc = passive_cable(2000, L=4000.0, tstop=5.0)
+    ref = run_oracle(sc)
+    gpu = run_gpu(cn, sc)
+    assert_parity(gpu, ref)
+
+
+@pytest.mark.parametrize("prec,bound", [("gate_fp32", 0.1), ("gate_bf16", None)])
+def test_reduced_precision_gating_error(cn, prec, bound):
+    """FP32 gating (BF16 storage optional) against the FP64 oracle: report
+    max soma-voltage error and spike agreement; FP32 must stay within 0.1 mV
+    with every spike in the same step on the ring."""
+    sc = ring16(weight=0.02, tstop=200.0)
+    ref = run_oracle(sc, nthreads=1)
+    gpu = run_gpu(cn, sc, precision=prec)
+    err = np.max(np.abs(gpu["tr"] - ref["tr"]))
+    same = len(set(zip(gpu["g"].tolist(), gpu["k"].tolist())) & set(zip(ref["g"].tolist(), ref["k"].tolist())))
+    frac = same / max(1, len(ref["g"]))
+    print(f"{prec}: max soma error {err:.3g} mV, spikes in the same step {same}/{len(ref['g'])}")
+    if bound is not None:
+        assert err <= bound and frac == 1.0 and len(gpu["g"]) == len(ref["g"])
+
+
+def test_add_after_run_is_rejected(cn):
+    sc = ring16(n_cells=4, tstop=2.0)
+    md = cn.from_scenario(sc)
+    md.cn_run(1.0)
+    with pytest.raises(cn.CNError) as e:
+        md.cn_add_stim(0, 0.0, 1.0, 0.1)
+    assert e.value.status == cn.CN_ESTATE
+    with pytest.raises(cn.CNError) as e:
+        md.cn_run(0.5)
+    assert e.value.status == cn.CN_EINVAL
+
+
+def test_event_buffer_overflow_reported(cn):
+    """More than 256 events for one cell inside one interval is reported as
+    CN_ERANGE (the kernel bounds-checks the buffer and drops the excess)."""
+    sc = ring16(n_cells=2, tstop=2.0)
+    sc.netcon_src = sc.netcon_src[:0]; sc.netcon_syn = sc.netcon_syn[:0]
+    sc.netcon_w = sc.netcon_w[:0]; sc.netcon_delay = sc.netcon_delay[:0]
+    sc.ev_syn = np.zeros(300, np.int32)
+    sc.ev_t = np.full(300, 0.5)
+    sc.ev_w = np.full(300, 1e-6)
+    md = cn.from_scenario(sc)
+    md.cn_run(2.0)
+    with pytest.raises(cn.CNError) as e:
+        md.cn_sync()
+    assert e.value.status == cn.CN_ERANGE
