@@ -212,6 +212,21 @@ cn_status cn_profile(cn_model* m, int32_t enable);
 cn_status cn_profile_read(cn_model* m, double* interval_ms, int64_t* interval_launches, double* pull_ms,
                           int64_t* pull_launches);
 
+/* Batched tree solve (Section 2: Gaussian elimination in Hines order, as in
+ * the per-step matrix resolution).  All arrays are DEVICE pointers of the
+ * current device; trees are concatenated: tree t owns rows
+ * [offset[t], offset[t+1]) with cell-local parent (parent[first] = -1,
+ * 0 <= parent[i] < i - first otherwise).  Row i has diagonal d[i] and
+ * coupling b[i] to its parent p; row p has coupling a[i] to i.  Writes the
+ * solution to x (which may not alias the inputs); inputs are not modified.
+ * Allocates n_nodes doubles of scratch (stream-ordered) per call and
+ * synchronizes the stream before returning.  Errors: CN_EINVAL (bad sizes,
+ * NULL pointers or a bad parent index, detected on the device; that tree is
+ * left unsolved), CN_ERANGE (a zero pivot), CN_ENOMEM, CN_ECUDA.           */
+cn_status cn_solve_trees(int32_t n_trees, int64_t n_nodes, const int32_t* offset, const int32_t* parent,
+                         const double* a, const double* b, const double* d, const double* rhs, double* x,
+                         void* stream);
+
 /* Error text of the last failed call on m (or of the last failed
  * cn_model_create when m is NULL).  Valid until the next call on m.        */
 const char* cn_last_error(const cn_model* m);

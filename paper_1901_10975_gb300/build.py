@@ -6,14 +6,14 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libcn.so")
-SOURCES = [os.path.join(HERE, "csrc", "cn_engine.cu")]
+SOURCES = [os.path.join(HERE, "csrc", f) for f in ("cn_engine.cu", "cn_solve.cu")]
 DEPS = SOURCES + [os.path.join(HERE, "csrc", f) for f in ("cn_device.cuh", "cn_kernels.cuh")] + \
     [os.path.join(ROOT, "include", "cn.h")]
 
 
 def nvcc_cmd(out, extra=()):
     return ["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
-            "-Xcompiler", "-fPIC", "-shared", "-I", os.path.join(ROOT, "include"), *extra,
+            "-Xcompiler", "-fPIC", "-shared", "--threads", "4", "-I", os.path.join(ROOT, "include"), *extra,
             "-o", out, *SOURCES]
 
 

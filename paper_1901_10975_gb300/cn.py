@@ -101,6 +101,9 @@ def lib():
         L.cn_profile.restype = st
         L.cn_profile_read.argtypes = [C.c_void_p, _P_F64, _P_I64, _P_F64, _P_I64]
         L.cn_profile_read.restype = st
+        L.cn_solve_trees.argtypes = [C.c_int32, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+        L.cn_solve_trees.restype = st
         L.cn_last_error.argtypes = [C.c_void_p]
         L.cn_last_error.restype = C.c_char_p
         L.cn_model_destroy.argtypes = [C.c_void_p]
@@ -135,6 +138,30 @@ def cn_geometry(cell_offset, parent, dx, diam, Ra):
     _check(lib().cn_geometry(len(off) - 1, _p(off, _P_I32), _p(par, _P_I32), _p(dx, _P_F64), _p(diam, _P_F64),
                              _p(Ra, _P_F64), _p(area, _P_F64), _p(ri, _P_F64)))
     return area, ri
+
+
+def _device_tree_args(offset, parent, a, b, d, rhs, device):
+    import torch
+    dev = torch.device("cuda", device)
+    t = dict(offset=torch.as_tensor(_i32(offset), device=dev), parent=torch.as_tensor(_i32(parent), device=dev),
+             a=torch.as_tensor(_f64(a), device=dev), b=torch.as_tensor(_f64(b), device=dev),
+             d=torch.as_tensor(_f64(d), device=dev), rhs=torch.as_tensor(_f64(rhs), device=dev))
+    t["x"] = torch.empty_like(t["rhs"])
+    return t
+
+
+def cn_solve_trees(offset, parent, a, b, d, rhs, device=0):
+    """Solve concatenated tree systems on the GPU; host arrays in, host array out."""
+    import torch
+    t = _device_tree_args(offset, parent, a, b, d, rhs, device)
+    stream = torch.cuda.current_stream(device).cuda_stream
+    n_trees = t["offset"].numel() - 1
+    st = lib().cn_solve_trees(n_trees, t["rhs"].numel(), t["offset"].data_ptr(), t["parent"].data_ptr(),
+                              t["a"].data_ptr(), t["b"].data_ptr(), t["d"].data_ptr(), t["rhs"].data_ptr(),
+                              t["x"].data_ptr(), stream)
+    if st != CN_OK:
+        raise CNError(st, "cn_solve_trees failed")
+    return t["x"].cpu().numpy()
 
 
 def _torch_allocator(device):

@@ -2,11 +2,16 @@
 //
 // Layout ("one cell per thread", Section 4.4's interleaved idea, rebuilt for
 // sm_103a): cells are sorted by size and packed 32 to a warp ("group"); node
-// row j of lane l lives at element base_g + 32*j + l of every per-node
-// array, so the 32 lanes of a warp touch one contiguous 256-byte row of
-// FP64 per array.  Mechanism instances (synapses, HH, stimuli) and records
-// use the same interleaving with their own row counts.  Each thread owns one
-// cell for a whole minimum-delay interval: there is no communication between
+// row j of lane l lives at element base_g + 32*j + l of every per-row array,
+// so the 32 lanes of a warp touch one contiguous 256-byte row of FP64 per
+// array.  Inside a cell, rows follow a depth-first preorder that visits the
+// smaller child subtree first: then a row's parent is the previous row except
+// for the "far" children of branch points, and far contributions nest
+// last-in-first-out, so a per-lane stack of depth <= log2(cell size) + 1 in
+// shared memory replaces every random parent access.  Each row of the tree
+// matrix is scaled by 1/cdt (cdt = 1e-3 cm/dt), so the right-hand side is
+// v + (sum g E)/cdt and no capacitance term is streamed.  Each thread owns
+// one cell for a whole minimum-delay interval: no communication between
 // threads inside the interval kernel.
 #pragma once
 #include <cstdint>
@@ -27,13 +32,25 @@ struct EvRec {
   double w;       // uS
 };
 
+// Per-row flag word: mechanism slot (low 16 bits, kNoSlot if none), "far"
+// bit (the parent is not the previous row), count of far children.
+constexpr int32_t kNoSlot = 0xffff;
+constexpr int32_t kFarBit = 1 << 16;
+constexpr int kNFarShift = 17;
+
+// Rows streamed per cp.async ring (pairs of rows).
+constexpr int kRingPairs = 4;
+
 // Plain-old-data view of a model's device buffers, passed by value.
 struct DevModel {
   int32_t n_groups, n_slots, n_cells, D, n_rec;
+  int32_t max_slots, stack_depth;
   double dt;
   // per group
-  const int64_t* g_node_base;
-  const int32_t* g_rows;
+  const int64_t* g_node_base;  // element index of row 0, lane 0 (multiple of 64)
+  const int32_t* g_rows;       // rows (even)
+  const int64_t* g_slot_base;
+  const int32_t* g_slot_rows;
   const int64_t* g_syn_base;
   const int32_t* g_syn_rows;
   const int64_t* g_hh_base;
@@ -44,6 +61,7 @@ struct DevModel {
   const int32_t* g_rec_rows;
   // per slot (group * 32 + lane)
   const int32_t* s_rows;
+  const int32_t* s_nslot;
   const int32_t* s_nsyn;
   const int32_t* s_nhh;
   const int32_t* s_nst;
@@ -52,34 +70,37 @@ struct DevModel {
   const int32_t* s_spike_row;
   const double* s_thresh;
   uint8_t* s_above;
-  // nodes (interleaved)
-  double* v;
-  double* acc;    // right-hand side accumulator, reset to ge after each solve
-  double* dacc;   // diagonal accumulator, reset to d0 after each solve
-  const double* a;     // row p, column i coupling (-100/(ri area_p))
-  const double* b;     // row i, column p coupling (-100/(ri area_i))
-  const double* cdt;   // 1e-3 cm / dt
-  const double* ge;    // constant part of sum g E (pas)
-  const double* d0;    // constant diagonal: cdt + pas g + axial sums
-  const int32_t* prow; // parent row (-1 at the root)
+  // rows (interleaved); constants are scaled by 1/cdt of their row
+  double* v;           // v_k; holds rhs/d between elimination and back substitution
+  double* bp;          // b/d of each row, from elimination to back substitution
+  const double* ge;    // (pas g e)/cdt
+  const double* d0;    // (cdt + pas g + axial couplings)/cdt
+  const double* a;     // row p, column i coupling / cdt_p
+  const double* b;     // row i, column p coupling / cdt_i
+  const int32_t* flags;
+  // mechanism slots (rows carrying point processes or channels)
+  const int32_t* slot_row;
+  const double* slot_ge0;   // ge of the slot's row
+  const double* slot_d00;   // d0 of the slot's row
   // synapses (ExpSyn)
-  const int32_t* syn_row;
+  const int32_t* syn_slot;
   double* syn_g;
-  const double* syn_s;      // 100 / area of the synapse node
+  const double* syn_s;      // 100 / (area cdt) of the synapse row
   const double* syn_e;
   const double* syn_decay;  // exp(-dt / tau)
   // HH
+  const int32_t* hh_slot;
   const int32_t* hh_row;
   void* hh_m;
   void* hh_h;
   void* hh_n;
-  const double* hh_p;       // [6][hh_elems]: gnabar gkbar gl el ena ek
+  const double* hh_p;       // [6][hh_elems]: gnabar/cdt gkbar/cdt gl/cdt el ena ek
   int64_t hh_elems;
   // stimuli
-  const int32_t* st_row;
+  const int32_t* st_slot;
   const double* st_del;
   const double* st_dur;
-  const double* st_amp;     // 100 amp / area (mA/cm2)
+  const double* st_amp;     // 100 amp / (area cdt)
   // records
   const int32_t* rec_row;
   const int32_t* rec_id;
@@ -103,6 +124,22 @@ struct DevModel {
   uint64_t* hist;
   int32_t* status;
 };
+
+// Dynamic shared memory of one interval-kernel block (one warp).
+__host__ __device__ inline size_t interval_smem_bytes(int stack_depth, int max_slots) {
+  const size_t ring = (size_t)2 * kRingPairs * kLanes * (5 * sizeof(double) + sizeof(int32_t));
+  return ring + (size_t)stack_depth * kLanes * 2 * sizeof(double) + (size_t)max_slots * kLanes * 2 * sizeof(double);
+}
+
+// 16-byte asynchronous global->shared copy (through L1, so a warp's own
+// earlier global stores are observed), and its group bookkeeping.
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 // --------------------------------------------------------------- arithmetic
 // Reciprocal of a positive FP64 number in [2^-126, 2^126] (always true for a

@@ -46,6 +46,8 @@ struct cn_model {
   std::vector<double> st_del, st_dur, st_amp;
   std::vector<int32_t> rec_node;
   std::vector<int32_t> node_cell;
+  std::vector<int32_t> node_row;   // global node -> row inside its cell
+  size_t smem_bytes = 0;
 
   // ---- layout
   bool finalized = false;
@@ -175,6 +177,69 @@ cn_status launch_checked(cn_model* m, F&& f) {
   return CN_OK;
 }
 
+// Depth-first preorder of one cell that visits the smaller child subtree
+// first.  Returns row_of[local] and, per row, the parent row and flags
+// (far bit, far-children count); also the far-stack depths needed by
+// elimination (descending rows) and back substitution (ascending rows).
+struct CellOrder {
+  std::vector<int32_t> row_of, prow, nfar;
+  std::vector<uint8_t> far;
+  int depth = 1;
+};
+
+CellOrder order_cell(const int32_t* parent, int n) {
+  CellOrder o;
+  std::vector<int32_t> size(n, 1), head(n, -1), next(n, -1);
+  for (int i = n - 1; i > 0; --i) size[parent[i]] += size[i];
+  // children lists sorted by (subtree size, index), built by insertion
+  for (int i = n - 1; i > 0; --i) {
+    int p = parent[i];
+    int* link = &head[p];
+    while (*link >= 0 && (size[*link] < size[i] || (size[*link] == size[i] && *link < i))) link = &next[*link];
+    next[i] = *link;
+    *link = i;
+  }
+  o.row_of.assign(n, -1);
+  o.prow.assign(n, -1);
+  o.nfar.assign(n, 0);
+  o.far.assign(n, 0);
+  std::vector<int32_t> stack{0};
+  int row = 0;
+  while (!stack.empty()) {
+    int u = stack.back();
+    stack.pop_back();
+    o.row_of[u] = row++;
+    // push children in reverse so the smallest subtree is visited first
+    std::vector<int32_t> ch;
+    for (int c = head[u]; c >= 0; c = next[c]) ch.push_back(c);
+    for (auto it = ch.rbegin(); it != ch.rend(); ++it) stack.push_back(*it);
+  }
+  std::vector<int32_t> local_of(n);
+  for (int i = 0; i < n; ++i) local_of[o.row_of[i]] = i;
+  for (int r = 1; r < n; ++r) {
+    int pr = o.row_of[parent[local_of[r]]];
+    o.prow[r] = pr;
+    if (pr != r - 1) {
+      o.far[r] = 1;
+      o.nfar[pr]++;
+    }
+  }
+  int top = 0, mx = 0;
+  for (int r = n - 1; r >= 0; --r) {  // elimination
+    top -= o.nfar[r];
+    if (r > 0 && o.far[r]) mx = std::max(mx, ++top);
+  }
+  top = o.nfar[0];
+  mx = std::max(mx, top);
+  for (int r = 1; r < n; ++r) {  // back substitution
+    if (o.far[r]) --top;
+    top += o.nfar[r];
+    mx = std::max(mx, top);
+  }
+  o.depth = std::max(1, mx);
+  return o;
+}
+
 cn_status finalize(cn_model* m) {
   cn::DevModel& dm = m->dm;
   const double dt = m->opt.dt_ms;
@@ -201,12 +266,27 @@ cn_status finalize(cn_model* m) {
   m->cell_slot.assign(m->n_cells, -1);
   std::vector<int32_t> slot_gid(m->n_slots, -1), slot_rows(m->n_slots, 0), slot_spike(m->n_slots, 0);
   std::vector<double> slot_thresh(m->n_slots, 0.0);
+  // per-cell row order
+  m->node_row.assign(m->n_nodes, 0);
+  std::vector<int32_t> row_prow(m->n_nodes), row_flag(m->n_nodes);  // by global (cell offset + row)
+  int depth = 1;
+  for (int c = 0; c < m->n_cells; ++c) {
+    const int n = m->off[c + 1] - m->off[c];
+    CellOrder o = order_cell(m->parent.data() + m->off[c], n);
+    depth = std::max(depth, o.depth);
+    for (int li = 0; li < n; ++li) m->node_row[m->off[c] + li] = o.row_of[li];
+    for (int r = 0; r < n; ++r) {
+      row_prow[m->off[c] + r] = o.prow[r];
+      if (o.nfar[r] > 15) return m->fail(CN_EINVAL, "a node has more than 16 children");
+      row_flag[m->off[c] + r] = cn::kNoSlot | (o.far[r] ? cn::kFarBit : 0) | (o.nfar[r] << cn::kNFarShift);
+    }
+  }
   for (int r = 0; r < m->n_cells; ++r) {
     int c = order[r];
     m->cell_slot[c] = r;
     slot_gid[r] = c;
     slot_rows[r] = m->off[c + 1] - m->off[c];
-    slot_spike[r] = m->spike_node[c];
+    slot_spike[r] = m->node_row[m->off[c] + m->spike_node[c]];
     slot_thresh[r] = m->thresh[c];
   }
   std::vector<int32_t> g_rows(m->n_groups, 0);
@@ -214,29 +294,76 @@ cn_status finalize(cn_model* m) {
   for (int s = 0; s < m->n_slots; ++s) g_rows[s / cn::kLanes] = std::max(g_rows[s / cn::kLanes], slot_rows[s]);
   int64_t acc = 0;
   for (int g = 0; g < m->n_groups; ++g) {
+    g_rows[g] += g_rows[g] & 1;  // even: rows stream in pairs
     m->g_node_base[g] = acc;
     acc += (int64_t)g_rows[g] * cn::kLanes;
   }
   m->node_elems = acc;
-  auto node_elem = [&](int64_t node) {
-    int c = m->node_cell[node];
+  auto row_elem = [&](int c, int row) {
     int s = m->cell_slot[c];
-    return m->g_node_base[s / cn::kLanes] + (int64_t)(node - m->off[c]) * cn::kLanes + s % cn::kLanes;
+    return m->g_node_base[s / cn::kLanes] + (int64_t)row * cn::kLanes + s % cn::kLanes;
   };
-  // per-node inputs, interleaved
+  auto node_elem = [&](int64_t node) { return row_elem(m->node_cell[node], m->node_row[node]); };
+  // mechanism slots: distinct rows carrying a point process or channel, per cell
+  std::vector<std::vector<int32_t>> cell_slot_rows(m->n_cells);
+  std::vector<int32_t> row_slot(m->n_nodes, -1);  // by global node
+  auto slot_of_node = [&](int64_t node) {
+    if (row_slot[node] < 0) {
+      int c = m->node_cell[node];
+      row_slot[node] = (int32_t)cell_slot_rows[c].size();
+      cell_slot_rows[c].push_back(m->node_row[node]);
+    }
+    return row_slot[node];
+  };
+  std::vector<int32_t> syn_slotid(m->syn_node.size()), hh_slotid(m->hh_node.size()), st_slotid(m->st_node.size());
+  for (size_t i = 0; i < m->syn_node.size(); ++i) syn_slotid[i] = slot_of_node(m->syn_node[i]);
+  for (size_t i = 0; i < m->hh_node.size(); ++i) hh_slotid[i] = slot_of_node(m->hh_node[i]);
+  for (size_t i = 0; i < m->st_node.size(); ++i) st_slotid[i] = slot_of_node(m->st_node[i]);
+  int max_slots = 1;
+  for (int c = 0; c < m->n_cells; ++c) max_slots = std::max<int>(max_slots, (int)cell_slot_rows[c].size());
+  if (max_slots >= cn::kNoSlot) return m->fail(CN_EINVAL, "too many mechanism rows in one cell");
+  const size_t smem = cn::interval_smem_bytes(depth, max_slots);
+  if (smem > 227 * 1024)
+    return m->fail(CN_EINVAL, "cell needs " + std::to_string(smem) + " bytes of shared memory (slots " +
+                                  std::to_string(max_slots) + ", stack " + std::to_string(depth) + ")");
+  m->smem_bytes = smem;
+  // per-row inputs, interleaved
   std::vector<double> h_area(acc, 1.0), h_ri(acc, 1.0), h_cm(acc, 1.0), h_gp(acc, 0.0), h_ep(acc, 0.0);
-  std::vector<int32_t> h_prow(acc, -1);
-  for (int64_t i = 0; i < m->n_nodes; ++i) {
-    int64_t e = node_elem(i);
-    h_area[e] = m->area[i];
-    h_ri[e] = m->ri[i];
-    h_cm[e] = m->cm[i];
-    h_prow[e] = m->parent[i];
+  std::vector<int32_t> h_prow(acc, -1), h_flags(acc, cn::kNoSlot);
+  for (int c = 0; c < m->n_cells; ++c) {
+    for (int32_t li = 0; li < m->off[c + 1] - m->off[c]; ++li) {
+      int64_t node = m->off[c] + li;
+      int row = m->node_row[node];
+      int64_t e = row_elem(c, row);
+      h_area[e] = m->area[node];
+      h_ri[e] = m->ri[node];
+      h_cm[e] = m->cm[node];
+      h_prow[e] = row_prow[m->off[c] + row];
+      int32_t f = row_flag[m->off[c] + row];
+      if (row_slot[node] >= 0) f = (f & ~cn::kNoSlot) | row_slot[node];
+      h_flags[e] = f;
+    }
   }
   for (size_t q = 0; q < m->pas_node.size(); ++q) {
     int64_t e = node_elem(m->pas_node[q]);
     h_gp[e] = m->pas_g[q];
     h_ep[e] = m->pas_e[q];
+  }
+  // slot rows, interleaved
+  std::vector<int32_t> slot_n(m->n_slots, 0), g_slot_rows(m->n_groups, 0);
+  std::vector<int64_t> g_slot_base(m->n_groups, 0);
+  for (int c = 0; c < m->n_cells; ++c) slot_n[m->cell_slot[c]] = (int32_t)cell_slot_rows[c].size();
+  for (int s = 0; s < m->n_slots; ++s) g_slot_rows[s / cn::kLanes] = std::max(g_slot_rows[s / cn::kLanes], slot_n[s]);
+  int64_t sacc = 0;
+  for (int g = 0; g < m->n_groups; ++g) {
+    g_slot_base[g] = sacc;
+    sacc += (int64_t)g_slot_rows[g] * cn::kLanes;
+  }
+  std::vector<int32_t> h_slot_row(std::max<int64_t>(sacc, 1), 0);
+  for (int c = 0; c < m->n_cells; ++c) {
+    int s = m->cell_slot[c];
+    for (size_t t = 0; t < cell_slot_rows[c].size(); ++t)
+      h_slot_row[g_slot_base[s / cn::kLanes] + (int64_t)t * cn::kLanes + s % cn::kLanes] = cell_slot_rows[c][t];
   }
   // synapses, HH, stimuli, records
   Rows rs = interleave(m, m->syn_node), rh = interleave(m, m->hh_node), rt = interleave(m, m->st_node),
@@ -246,39 +373,43 @@ cn_status finalize(cn_model* m) {
   m->g_syn_base = rs.g_base;
   m->g_hh_base = rh.g_base;
   m->syn_elems = rs.elems; m->hh_elems = rh.elems; m->st_elems = rt.elems; m->rec_elems = rr.elems;
-  std::vector<int32_t> h_syn_row(rs.elems, 0);
-  std::vector<double> h_syn_tau(rs.elems, 1.0), h_syn_e(rs.elems, 0.0), h_syn_area(rs.elems, 1.0);
+  std::vector<int32_t> h_syn_slot(rs.elems, 0);
+  std::vector<double> h_syn_tau(rs.elems, 1.0), h_syn_e(rs.elems, 0.0), h_syn_area(rs.elems, 1.0),
+      h_syn_cm(rs.elems, 1.0);
   for (size_t i = 0; i < m->syn_node.size(); ++i) {
     int64_t e = elem_of(rs, i);
-    int c = m->node_cell[m->syn_node[i]];
-    h_syn_row[e] = m->syn_node[i] - m->off[c];
+    h_syn_slot[e] = syn_slotid[i];
     h_syn_tau[e] = m->syn_tau[i];
     h_syn_e[e] = m->syn_e[i];
     h_syn_area[e] = m->area[m->syn_node[i]];
+    h_syn_cm[e] = m->cm[m->syn_node[i]];
   }
-  std::vector<int32_t> h_hh_row(rh.elems, 0);
-  std::vector<double> h_hh_p(6 * rh.elems, 0.0);
+  std::vector<int32_t> h_hh_row(rh.elems, 0), h_hh_slot(rh.elems, 0);
+  std::vector<double> h_hh_p(6 * rh.elems, 0.0), h_hh_cm(rh.elems, 1.0);
   size_t nhh = m->hh_node.size();
   for (size_t i = 0; i < nhh; ++i) {
     int64_t e = elem_of(rh, i);
-    h_hh_row[e] = m->hh_node[i] - m->off[m->node_cell[m->hh_node[i]]];
+    h_hh_row[e] = m->node_row[m->hh_node[i]];
+    h_hh_slot[e] = hh_slotid[i];
+    h_hh_cm[e] = m->cm[m->hh_node[i]];
     for (int p = 0; p < 6; ++p) h_hh_p[p * rh.elems + e] = m->hh_par[p * nhh + i];
   }
-  std::vector<int32_t> h_st_row(rt.elems, 0);
+  std::vector<int32_t> h_st_slot(rt.elems, 0);
   std::vector<double> h_st_del(rt.elems, 0.0), h_st_dur(rt.elems, 0.0), h_st_amp(rt.elems, 0.0),
-      h_st_area(rt.elems, 1.0);
+      h_st_area(rt.elems, 1.0), h_st_cm(rt.elems, 1.0);
   for (size_t i = 0; i < m->st_node.size(); ++i) {
     int64_t e = elem_of(rt, i);
-    h_st_row[e] = m->st_node[i] - m->off[m->node_cell[m->st_node[i]]];
+    h_st_slot[e] = st_slotid[i];
     h_st_del[e] = m->st_del[i];
     h_st_dur[e] = m->st_dur[i];
     h_st_amp[e] = m->st_amp[i];
     h_st_area[e] = m->area[m->st_node[i]];
+    h_st_cm[e] = m->cm[m->st_node[i]];
   }
   std::vector<int32_t> h_rec_row(rr.elems, 0), h_rec_id(rr.elems, 0);
   for (size_t i = 0; i < m->rec_node.size(); ++i) {
     int64_t e = elem_of(rr, i);
-    h_rec_row[e] = m->rec_node[i] - m->off[m->node_cell[m->rec_node[i]]];
+    h_rec_row[e] = m->node_row[m->rec_node[i]];
     h_rec_id[e] = (int32_t)i;
   }
   // incoming NetCons per target slot, by (source gid, NetCon index)
@@ -338,12 +469,16 @@ cn_status finalize(cn_model* m) {
   dm.n_cells = m->n_cells;
   dm.D = m->D;
   dm.n_rec = (int32_t)m->rec_node.size();
+  dm.max_slots = max_slots;
+  dm.stack_depth = depth;
   dm.dt = dt;
   int64_t* p64;
   int32_t* p32;
   double* pd;
   CN_CHECK(upload(m, &p64, m->g_node_base)); dm.g_node_base = p64;
   CN_CHECK(upload(m, &p32, g_rows)); dm.g_rows = p32;
+  CN_CHECK(upload(m, &p64, g_slot_base)); dm.g_slot_base = p64;
+  CN_CHECK(upload(m, &p32, g_slot_rows)); dm.g_slot_rows = p32;
   CN_CHECK(upload(m, &p64, rs.g_base)); dm.g_syn_base = p64;
   CN_CHECK(upload(m, &p32, rs.g_rows)); dm.g_syn_rows = p32;
   CN_CHECK(upload(m, &p64, rh.g_base)); dm.g_hh_base = p64;
@@ -353,6 +488,7 @@ cn_status finalize(cn_model* m) {
   CN_CHECK(upload(m, &p64, rr.g_base)); dm.g_rec_base = p64;
   CN_CHECK(upload(m, &p32, rr.g_rows)); dm.g_rec_rows = p32;
   CN_CHECK(upload(m, &p32, slot_rows)); dm.s_rows = p32;
+  CN_CHECK(upload(m, &p32, slot_n)); dm.s_nslot = p32;
   CN_CHECK(upload(m, &p32, rs.slot_n)); dm.s_nsyn = p32;
   CN_CHECK(upload(m, &p32, rh.slot_n)); dm.s_nhh = p32;
   CN_CHECK(upload(m, &p32, rt.slot_n)); dm.s_nst = p32;
@@ -363,19 +499,21 @@ cn_status finalize(cn_model* m) {
   uint8_t* pu8;
   CN_CHECK(zeros(m, &pu8, m->n_slots)); dm.s_above = pu8;
   CN_CHECK(zeros(m, &pd, acc)); dm.v = pd;
-  CN_CHECK(zeros(m, &pd, acc)); dm.acc = pd;
-  CN_CHECK(zeros(m, &pd, acc)); dm.dacc = pd;
-  CN_CHECK(zeros(m, &pd, acc)); dm.a = pd;
-  CN_CHECK(zeros(m, &pd, acc)); dm.b = pd;
-  CN_CHECK(zeros(m, &pd, acc)); dm.cdt = pd;
+  CN_CHECK(zeros(m, &pd, acc)); dm.bp = pd;
   CN_CHECK(zeros(m, &pd, acc)); dm.ge = pd;
   CN_CHECK(zeros(m, &pd, acc)); dm.d0 = pd;
-  CN_CHECK(upload(m, &p32, h_prow)); dm.prow = p32;
-  CN_CHECK(upload(m, &p32, h_syn_row)); dm.syn_row = p32;
+  CN_CHECK(zeros(m, &pd, acc)); dm.a = pd;
+  CN_CHECK(zeros(m, &pd, acc)); dm.b = pd;
+  CN_CHECK(upload(m, &p32, h_flags)); dm.flags = p32;
+  CN_CHECK(upload(m, &p32, h_slot_row)); dm.slot_row = p32;
+  CN_CHECK(zeros(m, &pd, std::max<int64_t>(sacc, 1))); dm.slot_ge0 = pd;
+  CN_CHECK(zeros(m, &pd, std::max<int64_t>(sacc, 1))); dm.slot_d00 = pd;
+  CN_CHECK(upload(m, &p32, h_syn_slot)); dm.syn_slot = p32;
   CN_CHECK(zeros(m, &pd, rs.elems)); dm.syn_g = pd;
   CN_CHECK(zeros(m, &pd, rs.elems)); dm.syn_s = pd;
   CN_CHECK(upload(m, &pd, h_syn_e)); dm.syn_e = pd;
   CN_CHECK(zeros(m, &pd, rs.elems)); dm.syn_decay = pd;
+  CN_CHECK(upload(m, &p32, h_hh_slot)); dm.hh_slot = p32;
   CN_CHECK(upload(m, &p32, h_hh_row)); dm.hh_row = p32;
   m->gate_bytes = m->opt.precision == CN_PREC_FP64 ? 8 : (m->opt.precision == CN_PREC_GATE_FP32 ? 4 : 2);
   for (void** gp : {&dm.hh_m, &dm.hh_h, &dm.hh_n}) {
@@ -386,7 +524,7 @@ cn_status finalize(cn_model* m) {
   }
   CN_CHECK(upload(m, &pd, h_hh_p)); dm.hh_p = pd;
   dm.hh_elems = rh.elems;
-  CN_CHECK(upload(m, &p32, h_st_row)); dm.st_row = p32;
+  CN_CHECK(upload(m, &p32, h_st_slot)); dm.st_slot = p32;
   CN_CHECK(upload(m, &pd, h_st_del)); dm.st_del = pd;
   CN_CHECK(upload(m, &pd, h_st_dur)); dm.st_dur = pd;
   CN_CHECK(zeros(m, &pd, rt.elems)); dm.st_amp = pd;
@@ -412,30 +550,41 @@ cn_status finalize(cn_model* m) {
   dm.trace = nullptr;
 
   // temporaries for the setup kernels
-  double *d_area, *d_ri, *d_cm, *d_gp, *d_ep, *d_syn_area, *d_syn_tau, *d_st_amp, *d_st_area;
+  double *d_area, *d_ri, *d_cm, *d_gp, *d_ep, *d_syn_area, *d_syn_cm, *d_syn_tau, *d_hh_cm, *d_st_amp, *d_st_area,
+      *d_st_cm;
+  int32_t* d_prow;
   CN_CHECK(upload(m, &d_area, h_area));
   CN_CHECK(upload(m, &d_ri, h_ri));
   CN_CHECK(upload(m, &d_cm, h_cm));
   CN_CHECK(upload(m, &d_gp, h_gp));
   CN_CHECK(upload(m, &d_ep, h_ep));
+  CN_CHECK(upload(m, &d_prow, h_prow));
   CN_CHECK(upload(m, &d_syn_area, h_syn_area));
+  CN_CHECK(upload(m, &d_syn_cm, h_syn_cm));
   CN_CHECK(upload(m, &d_syn_tau, h_syn_tau));
+  CN_CHECK(upload(m, &d_hh_cm, h_hh_cm));
   CN_CHECK(upload(m, &d_st_amp, h_st_amp));
   CN_CHECK(upload(m, &d_st_area, h_st_area));
+  CN_CHECK(upload(m, &d_st_cm, h_st_cm));
   const int tb = 128, nb = (m->n_slots + tb - 1) / tb;
   cudaStream_t st = m->stream;
   double v0 = m->opt.v_init_mV;
-  CN_CHECK(launch_checked(m, [&] { cn::k_setup_nodes<<<nb, tb, 0, st>>>(dm, d_area, d_ri, d_cm, d_gp, d_ep, v0); }));
-  CN_CHECK(launch_checked(m, [&] { cn::k_setup_syn<<<nb, tb, 0, st>>>(dm, d_syn_area, d_syn_tau); }));
+  CN_CHECK(launch_checked(m, [&] { cn::k_setup_nodes<<<nb, tb, 0, st>>>(dm, d_area, d_ri, d_cm, d_gp, d_ep, d_prow, v0); }));
+  CN_CHECK(launch_checked(m, [&] { cn::k_setup_slots<<<nb, tb, 0, st>>>(dm); }));
+  CN_CHECK(launch_checked(m, [&] { cn::k_setup_syn<<<nb, tb, 0, st>>>(dm, d_syn_area, d_syn_cm, d_syn_tau); }));
   switch (m->opt.precision) {
-    case CN_PREC_FP64: CN_CHECK(launch_checked(m, [&] { cn::k_setup_hh<0><<<nb, tb, 0, st>>>(dm, v0); })); break;
-    case CN_PREC_GATE_FP32: CN_CHECK(launch_checked(m, [&] { cn::k_setup_hh<1><<<nb, tb, 0, st>>>(dm, v0); })); break;
-    default: CN_CHECK(launch_checked(m, [&] { cn::k_setup_hh<2><<<nb, tb, 0, st>>>(dm, v0); })); break;
+    case CN_PREC_FP64: CN_CHECK(launch_checked(m, [&] { cn::k_setup_hh<0><<<nb, tb, 0, st>>>(dm, d_hh_cm, v0); })); break;
+    case CN_PREC_GATE_FP32: CN_CHECK(launch_checked(m, [&] { cn::k_setup_hh<1><<<nb, tb, 0, st>>>(dm, d_hh_cm, v0); })); break;
+    default: CN_CHECK(launch_checked(m, [&] { cn::k_setup_hh<2><<<nb, tb, 0, st>>>(dm, d_hh_cm, v0); })); break;
   }
-  CN_CHECK(launch_checked(m, [&] { cn::k_setup_stim<<<nb, tb, 0, st>>>(dm, d_st_amp, d_st_area); }));
+  CN_CHECK(launch_checked(m, [&] { cn::k_setup_stim<<<nb, tb, 0, st>>>(dm, d_st_amp, d_st_area, d_st_cm); }));
   CN_CHECK(launch_checked(m, [&] { cn::k_init_above<<<nb, tb, 0, st>>>(dm); }));
   CN_TRY_CUDA(m, cudaStreamSynchronize(st));
-  for (double* p : {d_area, d_ri, d_cm, d_gp, d_ep, d_syn_area, d_syn_tau, d_st_amp, d_st_area}) dfree_raw(m, p);
+  for (double* p : {d_area, d_ri, d_cm, d_gp, d_ep, d_syn_area, d_syn_cm, d_syn_tau, d_hh_cm, d_st_amp, d_st_area, d_st_cm})
+    dfree_raw(m, p);
+  dfree_raw(m, d_prow);
+  for (auto fn : {(const void*)cn::k_interval<0>, (const void*)cn::k_interval<1>, (const void*)cn::k_interval<2>})
+    CN_TRY_CUDA(m, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m->smem_bytes));
   m->finalized = true;
   m->cells_nodes = m->n_nodes;
   return CN_OK;
@@ -516,13 +665,13 @@ cn_status launch_interval(cn_model* m, int64_t J, int s0, int s1) {
   }
   switch (m->opt.precision) {
     case CN_PREC_FP64:
-      CN_CHECK(launch_checked(m, [&] { cn::k_interval<0><<<blocks, 32 * wpb, 0, st>>>(dm, J, s0, s1); }));
+      CN_CHECK(launch_checked(m, [&] { cn::k_interval<0><<<blocks, 32 * wpb, m->smem_bytes, st>>>(dm, J, s0, s1); }));
       break;
     case CN_PREC_GATE_FP32:
-      CN_CHECK(launch_checked(m, [&] { cn::k_interval<1><<<blocks, 32 * wpb, 0, st>>>(dm, J, s0, s1); }));
+      CN_CHECK(launch_checked(m, [&] { cn::k_interval<1><<<blocks, 32 * wpb, m->smem_bytes, st>>>(dm, J, s0, s1); }));
       break;
     default:
-      CN_CHECK(launch_checked(m, [&] { cn::k_interval<2><<<blocks, 32 * wpb, 0, st>>>(dm, J, s0, s1); }));
+      CN_CHECK(launch_checked(m, [&] { cn::k_interval<2><<<blocks, 32 * wpb, m->smem_bytes, st>>>(dm, J, s0, s1); }));
       break;
   }
   if (m->profiling) {
@@ -828,7 +977,7 @@ cn_status cn_get_v(cn_model* m, double* out, size_t cap) {
   for (int64_t i = 0; i < m->n_nodes; ++i) {
     int c = m->node_cell[i];
     int s = m->cell_slot[c];
-    out[i] = h[m->g_node_base[s / cn::kLanes] + (int64_t)(i - m->off[c]) * cn::kLanes + s % cn::kLanes];
+    out[i] = h[m->g_node_base[s / cn::kLanes] + (int64_t)m->node_row[i] * cn::kLanes + s % cn::kLanes];
   }
   return CN_OK;
 }

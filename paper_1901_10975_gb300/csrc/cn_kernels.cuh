@@ -5,14 +5,15 @@
 namespace cn {
 
 // ------------------------------------------------------------------ setup
-// Matrix constants of every node (Eq. 1 discretised on the tree):
-//   b_i = -100/(ri_i area_i)   (row i, column parent)
-//   a_i = -100/(ri_i area_p)   (row parent, column i)
-//   d0_i = 1e-3 cm_i/dt + sum(pas g) + sum of axial couplings of row i
-//   ge_i = pas g e
-// and the initial state v = v_init, acc = ge, dacc = d0.
+// Matrix constants of every row (Eq. 1 discretised on the tree), with row i
+// divided by cdt_i = 1e-3 cm_i/dt:
+//   b_i  = -100/(ri_i area_i) / cdt_i          (row i, column parent)
+//   a_i  = -100/(ri_i area_p) / cdt_p          (row parent, column i)
+//   d0_i = (cdt_i + pas g_i + axial couplings of row i) / cdt_i
+//   ge_i = pas g_i e_i / cdt_i
+// and v = v_init.  One thread per cell; prow holds parent rows.
 __global__ void k_setup_nodes(DevModel M, const double* area, const double* ri, const double* cm,
-                              const double* gpas, const double* epas, double v_init) {
+                              const double* gpas, const double* epas, const int32_t* prow, double v_init) {
   const int slot = blockIdx.x * blockDim.x + threadIdx.x;
   if (slot >= M.n_slots) return;
   const int g = slot / kLanes, lane = slot % kLanes;
@@ -21,34 +22,52 @@ __global__ void k_setup_nodes(DevModel M, const double* area, const double* ri, 
   double* d0 = const_cast<double*>(M.d0);
   double* a = const_cast<double*>(M.a);
   double* b = const_cast<double*>(M.b);
-  double* cdt = const_cast<double*>(M.cdt);
   double* ge = const_cast<double*>(M.ge);
   for (int j = 0; j < N; ++j) {
     const int64_t i = nb + (int64_t)j * kLanes;
-    cdt[i] = 1e-3 * cm[i] / M.dt;
-    d0[i] = cdt[i] + gpas[i];
-    ge[i] = gpas[i] * epas[i];
+    d0[i] = 1e-3 * cm[i] / M.dt + gpas[i];
     a[i] = 0.0;
     b[i] = 0.0;
   }
   for (int j = 1; j < N; ++j) {
     const int64_t i = nb + (int64_t)j * kLanes;
-    const int64_t ip = nb + (int64_t)M.prow[i] * kLanes;
-    b[i] = -100.0 / (ri[i] * area[i]);
-    a[i] = -100.0 / (ri[i] * area[ip]);
-    d0[i] -= b[i];
-    d0[ip] -= a[i];
+    const int64_t ip = nb + (int64_t)prow[i] * kLanes;
+    const double bb = -100.0 / (ri[i] * area[i]);
+    const double aa = -100.0 / (ri[i] * area[ip]);
+    d0[i] -= bb;
+    d0[ip] -= aa;
+    b[i] = bb / (1e-3 * cm[i] / M.dt);
+    a[i] = aa / (1e-3 * cm[ip] / M.dt);
   }
   for (int j = 0; j < N; ++j) {
     const int64_t i = nb + (int64_t)j * kLanes;
+    const double cdt = 1e-3 * cm[i] / M.dt;
+    d0[i] = d0[i] / cdt;
+    ge[i] = gpas[i] * epas[i] / cdt;
     M.v[i] = v_init;
-    M.acc[i] = ge[i];
-    M.dacc[i] = d0[i];
+    M.bp[i] = 0.0;
   }
 }
 
-// ExpSyn constants: s = 100/area (nA -> mA/cm2), decay = exp(-dt/tau), g = 0.
-__global__ void k_setup_syn(DevModel M, const double* node_area, const double* tau) {
+// Per-slot copies of the slot row's constants (the slot buffer is reset to
+// them at the start of every step).
+__global__ void k_setup_slots(DevModel M) {
+  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot >= M.n_slots) return;
+  const int g = slot / kLanes, lane = slot % kLanes;
+  const int n = M.s_nslot[slot];
+  const int64_t sb = M.g_slot_base[g] + lane, nb = M.g_node_base[g] + lane;
+  for (int t = 0; t < n; ++t) {
+    const int64_t i = sb + (int64_t)t * kLanes;
+    const int64_t r = nb + (int64_t)M.slot_row[i] * kLanes;
+    const_cast<double*>(M.slot_ge0)[i] = M.ge[r];
+    const_cast<double*>(M.slot_d00)[i] = M.d0[r];
+  }
+}
+
+// ExpSyn constants: s = 100/(area cdt) (nA -> mA/cm2, row-scaled),
+// decay = exp(-dt/tau), g = 0.
+__global__ void k_setup_syn(DevModel M, const double* node_area, const double* node_cm, const double* tau) {
   const int slot = blockIdx.x * blockDim.x + threadIdx.x;
   if (slot >= M.n_slots) return;
   const int g = slot / kLanes, lane = slot % kLanes;
@@ -56,15 +75,16 @@ __global__ void k_setup_syn(DevModel M, const double* node_area, const double* t
   const int64_t base = M.g_syn_base[g] + lane;
   for (int q = 0; q < n; ++q) {
     const int64_t i = base + (int64_t)q * kLanes;
-    const_cast<double*>(M.syn_s)[i] = 100.0 / node_area[i];
+    const_cast<double*>(M.syn_s)[i] = 100.0 / (node_area[i] * (1e-3 * node_cm[i] / M.dt));
     const_cast<double*>(M.syn_decay)[i] = exp(-M.dt / tau[i]);
     M.syn_g[i] = 0.0;
   }
 }
 
-// HH gates at their steady state of v_init.
+// HH: conductance densities divided by cdt of their row; gates at their
+// steady state of v_init.
 template <int PREC>
-__global__ void k_setup_hh(DevModel M, double v_init) {
+__global__ void k_setup_hh(DevModel M, const double* node_cm, double v_init) {
   using S = typename GateT<PREC>::S;
   using T = typename GateT<PREC>::M;
   const int slot = blockIdx.x * blockDim.x + threadIdx.x;
@@ -72,8 +92,11 @@ __global__ void k_setup_hh(DevModel M, double v_init) {
   const int g = slot / kLanes, lane = slot % kLanes;
   const int n = M.s_nhh[slot];
   const int64_t base = M.g_hh_base[g] + lane;
+  double* P = const_cast<double*>(M.hh_p);
   for (int q = 0; q < n; ++q) {
     const int64_t i = base + (int64_t)q * kLanes;
+    const double cdt = 1e-3 * node_cm[i] / M.dt;
+    for (int c = 0; c < 3; ++c) P[c * M.hh_elems + i] /= cdt;
     T am, bm, ah, bh, an, bn;
     hh_rates<T>(T(v_init), am, bm, ah, bh, an, bn);
     g_store(static_cast<S*>(M.hh_m) + i, am / (am + bm));
@@ -82,8 +105,8 @@ __global__ void k_setup_hh(DevModel M, double v_init) {
   }
 }
 
-// IClamp amplitude as a density: 100 amp / area (mA/cm2).
-__global__ void k_setup_stim(DevModel M, const double* amp, const double* node_area) {
+// IClamp amplitude as a row-scaled density: 100 amp / (area cdt).
+__global__ void k_setup_stim(DevModel M, const double* amp, const double* node_area, const double* node_cm) {
   const int slot = blockIdx.x * blockDim.x + threadIdx.x;
   if (slot >= M.n_slots) return;
   const int g = slot / kLanes, lane = slot % kLanes;
@@ -91,7 +114,7 @@ __global__ void k_setup_stim(DevModel M, const double* amp, const double* node_a
   const int64_t base = M.g_st_base[g] + lane;
   for (int q = 0; q < n; ++q) {
     const int64_t i = base + (int64_t)q * kLanes;
-    const_cast<double*>(M.st_amp)[i] = 100.0 * amp[i] / node_area[i];
+    const_cast<double*>(M.st_amp)[i] = 100.0 * amp[i] / (node_area[i] * (1e-3 * node_cm[i] / M.dt));
   }
 }
 
@@ -170,30 +193,54 @@ __global__ void k_pull_events(DevModel M, int64_t J) {
 }
 
 // ---------------------------------------------------------- interval kernel
-// Advances every cell of a warp by steps [s_begin, s_end) of interval J, one
-// cell per lane.  Per step k = J D + s (Section 2's per-step list):
+// Advances the 32 cells of one warp (one block) by steps [s_begin, s_end) of
+// interval J, one cell per lane.  Per step k = J D + s (Section 2's list):
 //  1 deliver due events (g += w, in buffer order),
-//  2 nrn_cur: ExpSyn, HH and IClamp add their conductance G to the diagonal
-//    accumulator and G E (+ I_inj) to the right-hand side accumulator,
-//  3 the tree system (C + G + L) v_{k+1} = C v_k + G E + I_inj is solved by
-//    Hines elimination (leaves to root) and back substitution,
+//  2 nrn_cur: ExpSyn, HH and IClamp add G (diagonal) and G E (+ I_inj) (right
+//    side) into the per-lane slot buffer of their row, seeded with the row's
+//    constants,
+//  3 matrix resolution: the row-scaled system (C + G + L) v_{k+1} = C v_k +
+//    G E + I_inj is eliminated leaves to root in Hines order and
+//    back-substituted root to leaves,
 //  4 nrn_state: HH gates by cnexp at v_{k+1}, ExpSyn decay,
-//  5 threshold detection at the cell's spike node, and recording.
-// Backward Euler with gates frozen over the step makes every current linear
-// in v, so the system above is exactly the paper's linearised update
+//  5 threshold detection at the cell's spike row, and recording.
+// Backward Euler with the gates frozen over a step makes every current linear
+// in v, so this is exactly the paper's linearised update
 // (C + G + L) dv = -I(v_k) - L v_k written for v_{k+1} instead of dv.
+// Row data streams through a shared-memory ring fed by cp.async, two rows per
+// copy instruction, kRingPairs pairs ahead; parents come from a register
+// carry (previous row) or the per-lane far stack.
 template <int PREC>
 __global__ void __launch_bounds__(32) k_interval(DevModel M, int64_t J, int s_begin, int s_end) {
   using S = typename GateT<PREC>::S;
   using T = typename GateT<PREC>::M;
-  const int g = blockIdx.x * (blockDim.x / kLanes) + threadIdx.x / kLanes;
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int KR = 2 * kRingPairs;  // ring rows
+  const int g = blockIdx.x;
   if (g >= M.n_groups) return;
-  const int lane = threadIdx.x % kLanes;
+  const int lane = threadIdx.x;
   const int slot = g * kLanes + lane;
   const int N = M.s_rows[slot];
   const int R = M.g_rows[g];
-  const int64_t nb = M.g_node_base[g] + lane;
+  const int PT = R / 2 - 1;                       // top row pair
+  const int64_t gb = M.g_node_base[g];
+  const int64_t nb = gb + lane;
   const int gid = M.s_gid[slot];
+  const int DS = M.stack_depth;
+
+  double* r_v = reinterpret_cast<double*>(smem);  // [KR][32] each
+  double* r_ge = r_v + KR * kLanes;
+  double* r_d0 = r_ge + KR * kLanes;
+  double* r_a = r_d0 + KR * kLanes;
+  double* r_b = r_a + KR * kLanes;
+  int32_t* r_fl = reinterpret_cast<int32_t*>(r_b + KR * kLanes);
+  double* st_x = reinterpret_cast<double*>(r_fl + KR * kLanes);  // [DS][32]
+  double* st_y = st_x + DS * kLanes;
+  double* sl_ge = st_y + DS * kLanes;             // [max_slots][32]
+  double* sl_d = sl_ge + M.max_slots * kLanes;
+
+  const int SLR = M.g_slot_rows[g], nslot = M.s_nslot[slot];
+  const int64_t slb = M.g_slot_base[g] + lane;
   const int SR = M.g_syn_rows[g], nsyn = M.s_nsyn[slot];
   const int64_t sb = M.g_syn_base[g] + lane;
   const int HR = M.g_hh_rows[g], nhh = M.s_nhh[slot];
@@ -201,10 +248,10 @@ __global__ void __launch_bounds__(32) k_interval(DevModel M, int64_t J, int s_be
   const int STR = M.g_st_rows[g], nst = M.s_nst[slot];
   const int64_t stb = M.g_st_base[g] + lane;
   const int RR = M.g_rec_rows[g], nrec = M.s_nrec[slot];
-  const int64_t rb = M.g_rec_base[g] + lane;
+  const int64_t rcb = M.g_rec_base[g] + lane;
   const double dt = M.dt;
   const int64_t T0 = J * M.D;
-  const int64_t spike_i = nb + (int64_t)M.s_spike_row[slot] * kLanes;
+  const int spike_row = M.s_spike_row[slot];
   const double thresh = M.s_thresh[slot];
   int above = M.s_above[slot];
   uint64_t mask = (s_begin > 0 && gid >= 0) ? M.hist[J * M.n_cells + gid] : 0ull;
@@ -215,27 +262,61 @@ __global__ void __launch_bounds__(32) k_interval(DevModel M, int64_t J, int s_be
   S* const gm = static_cast<S*>(M.hh_m);
   S* const gh = static_cast<S*>(M.hh_h);
   S* const gn = static_cast<S*>(M.hh_n);
+  // copy roles: lanes 0-15 move row 2P, lanes 16-31 row 2P+1, 16 bytes each
+  const int half = lane >> 4, chunk = lane & 15;
+
+  auto prefetch_elim = [&](int P) {
+    if (P >= 0) {
+      const int rr = ((P % kRingPairs) * 2 + half) * kLanes;
+      const int64_t src = gb + (int64_t)(2 * P + half) * kLanes + 2 * chunk;
+      cp_async16(r_v + rr + 2 * chunk, M.v + src);
+      cp_async16(r_ge + rr + 2 * chunk, M.ge + src);
+      cp_async16(r_d0 + rr + 2 * chunk, M.d0 + src);
+      cp_async16(r_a + rr + 2 * chunk, M.a + src);
+      cp_async16(r_b + rr + 2 * chunk, M.b + src);
+      if (chunk < 8) cp_async16(r_fl + rr + 4 * chunk, M.flags + gb + (int64_t)(2 * P + half) * kLanes + 4 * chunk);
+    }
+    cp_async_commit();
+  };
+  auto prefetch_back = [&](int P) {
+    if (P <= PT) {
+      const int rr = ((P % kRingPairs) * 2 + half) * kLanes;
+      const int64_t src = gb + (int64_t)(2 * P + half) * kLanes + 2 * chunk;
+      cp_async16(r_v + rr + 2 * chunk, M.v + src);
+      cp_async16(r_b + rr + 2 * chunk, M.bp + src);
+      if (chunk < 8) cp_async16(r_fl + rr + 4 * chunk, M.flags + gb + (int64_t)(2 * P + half) * kLanes + 4 * chunk);
+    }
+    cp_async_commit();
+  };
 
   for (int s = s_begin; s < s_end; ++s) {
     const int64_t k = T0 + s;
+    // start streaming the top rows while the mechanisms are evaluated
+    for (int i = 0; i < kRingPairs; ++i) prefetch_elim(PT - i);
     // (1) event delivery
     while (ei < ne && ev[ei].step == s) {
       M.syn_g[sb + (int64_t)ev[ei].syn * kLanes] += ev[ei].w;
       ++ei;
     }
-    // (2) nrn_cur: synapses
+    // (2) nrn_cur into the slot buffer
+    for (int t = 0; t < SLR; ++t) {
+      if (t < nslot) {
+        const int64_t i = slb + (int64_t)t * kLanes;
+        sl_ge[t * kLanes + lane] = M.slot_ge0[i];
+        sl_d[t * kLanes + lane] = M.slot_d00[i];
+      }
+    }
     for (int q = 0; q < SR; ++q) {
       if (q < nsyn) {
         const int64_t i = sb + (int64_t)q * kLanes;
         const double gs = M.syn_g[i];
         const double G = gs * M.syn_s[i];
-        const int64_t ni = nb + (int64_t)M.syn_row[i] * kLanes;
-        M.acc[ni] = fma(G, M.syn_e[i], M.acc[ni]);
-        M.dacc[ni] += G;
-        M.syn_g[i] = gs * M.syn_decay[i];  // state update (g' = g exp(-dt/tau)), v-independent
+        const int t = M.syn_slot[i] * kLanes + lane;
+        sl_ge[t] = fma(G, M.syn_e[i], sl_ge[t]);
+        sl_d[t] += G;
+        M.syn_g[i] = gs * M.syn_decay[i];  // ExpSyn state update: v-independent
       }
     }
-    //     HH
     for (int q = 0; q < HR; ++q) {
       if (q < nhh) {
         const int64_t i = hb + (int64_t)q * kLanes;
@@ -243,63 +324,108 @@ __global__ void __launch_bounds__(32) k_interval(DevModel M, int64_t J, int s_be
         const double gna = M.hh_p[i] * (m * m * m * h);
         const double gk = M.hh_p[M.hh_elems + i] * ((n * n) * (n * n));
         const double gl = M.hh_p[2 * M.hh_elems + i];
-        const int64_t ni = nb + (int64_t)M.hh_row[i] * kLanes;
-        M.acc[ni] += gna * M.hh_p[4 * M.hh_elems + i] + gk * M.hh_p[5 * M.hh_elems + i] +
-                     gl * M.hh_p[3 * M.hh_elems + i];
-        M.dacc[ni] += gna + gk + gl;
+        const int t = M.hh_slot[i] * kLanes + lane;
+        sl_ge[t] += gna * M.hh_p[4 * M.hh_elems + i] + gk * M.hh_p[5 * M.hh_elems + i] +
+                    gl * M.hh_p[3 * M.hh_elems + i];
+        sl_d[t] += gna + gk + gl;
       }
     }
-    //     IClamp (midpoint rule)
     if (STR > 0) {
       const double tmid = ((double)k + 0.5) * dt;
       for (int q = 0; q < STR; ++q) {
         if (q < nst) {
           const int64_t i = stb + (int64_t)q * kLanes;
-          if (M.st_del[i] <= tmid && tmid < M.st_del[i] + M.st_dur[i]) {
-            const int64_t ni = nb + (int64_t)M.st_row[i] * kLanes;
-            M.acc[ni] += M.st_amp[i];
-          }
+          if (M.st_del[i] <= tmid && tmid < M.st_del[i] + M.st_dur[i]) sl_ge[M.st_slot[i] * kLanes + lane] += M.st_amp[i];
         }
       }
     }
-    // (3) Hines elimination, leaves to root.  Row j's pivot is final once all
-    //     its children (rows > j) are eliminated.
-    for (int j = R - 1; j >= 1; --j) {
-      if (j < N) {
-        const int64_t i = nb + (int64_t)j * kLanes;
-        const double rhs = fma(M.cdt[i], M.v[i], M.acc[i]);
-        const double r = rcp64(M.dacc[i]);
-        const double x = rhs * r;
-        const double bp = M.b[i] * r;
-        const int64_t ip = nb + (int64_t)M.prow[i] * kLanes;
-        const double na = -M.a[i];
-        M.acc[ip] = fma(na, x, M.acc[ip]);
-        M.dacc[ip] = fma(na, bp, M.dacc[ip]);
-        M.v[i] = x;       // holds rhs/d until back substitution
-        M.dacc[i] = bp;   // holds b/d until back substitution
+    // (3) elimination, leaves to root
+    double ca = 0.0, cx = 0.0, cb = 0.0, x0 = 0.0;
+    int top = 0;
+    int nfar0 = 0;
+    for (int P = PT; P >= 0; --P) {
+      cp_async_wait<kRingPairs - 1>();
+      __syncwarp();
+      for (int h = 1; h >= 0; --h) {
+        const int j = 2 * P + h;
+        if (j < N) {
+          const int rr = ((P % kRingPairs) * 2 + h) * kLanes + lane;
+          const int f = r_fl[rr];
+          const int sl = f & kNoSlot;
+          double gE = r_ge[rr], dd = r_d0[rr];
+          if (sl != kNoSlot) {
+            gE = sl_ge[sl * kLanes + lane];
+            dd = sl_d[sl * kLanes + lane];
+          }
+          double rhs = fma(ca, cx, r_v[rr] + gE);
+          double d = fma(ca, cb, dd);
+          for (int np = f >> kNFarShift; np > 0; --np) {
+            --top;
+            rhs += st_x[top * kLanes + lane];
+            d += st_y[top * kLanes + lane];
+          }
+          const double r = rcp64(d);
+          const double x = rhs * r;
+          const int64_t gi = nb + (int64_t)j * kLanes;
+          if (j == 0) {
+            x0 = x;
+            nfar0 = f >> kNFarShift;
+            M.v[gi] = x;
+          } else {
+            const double bp = r_b[rr] * r;
+            M.v[gi] = x;
+            M.bp[gi] = bp;
+            const double na = -r_a[rr];
+            if (f & kFarBit) {
+              st_x[top * kLanes + lane] = na * x;
+              st_y[top * kLanes + lane] = na * bp;
+              ++top;
+              ca = 0.0;
+            } else {
+              ca = na;
+              cx = x;
+              cb = bp;
+            }
+          }
+        }
       }
+      __syncwarp();
+      prefetch_elim(P - kRingPairs);
     }
-    if (N > 0) {
-      const double x0 = fma(M.cdt[nb], M.v[nb], M.acc[nb]) * rcp64(M.dacc[nb]);
-      M.v[nb] = x0;
-      M.acc[nb] = M.ge[nb];
-      M.dacc[nb] = M.d0[nb];
-    }
-    //     back substitution, root to leaves; reset the accumulators.
-    for (int j = 1; j < R; ++j) {
-      if (j < N) {
-        const int64_t i = nb + (int64_t)j * kLanes;
-        const int64_t ip = nb + (int64_t)M.prow[i] * kLanes;
-        M.v[i] = fma(-M.dacc[i], M.v[ip], M.v[i]);
-        M.acc[i] = M.ge[i];
-        M.dacc[i] = M.d0[i];
+    cp_async_wait<0>();
+    __syncwarp();  // every lane's elimination stores precede the copies below
+    // back substitution, root to leaves
+    for (int i = 0; i < kRingPairs; ++i) prefetch_back(i);
+    double vprev = x0;
+    for (int q = 0; q < nfar0; ++q) st_x[(top + q) * kLanes + lane] = x0;
+    top += nfar0;
+    for (int P = 0; P <= PT; ++P) {
+      cp_async_wait<kRingPairs - 1>();
+      __syncwarp();
+      for (int h = 0; h < 2; ++h) {
+        const int j = 2 * P + h;
+        if (j >= 1 && j < N) {
+          const int rr = ((P % kRingPairs) * 2 + h) * kLanes + lane;
+          const int f = r_fl[rr];
+          double vp = vprev;
+          if (f & kFarBit) vp = st_x[--top * kLanes + lane];
+          const double vj = fma(-r_b[rr], vp, r_v[rr]);
+          M.v[nb + (int64_t)j * kLanes] = vj;
+          for (int np = f >> kNFarShift; np > 0; --np) st_x[top++ * kLanes + lane] = vj;
+          vprev = vj;
+        }
       }
+      __syncwarp();
+      prefetch_back(P + kRingPairs);
     }
+    cp_async_wait<0>();
+    __syncwarp();
     // (4) nrn_state: HH gates (cnexp) at v_{k+1}
     for (int q = 0; q < HR; ++q) {
       if (q < nhh) {
         const int64_t i = hb + (int64_t)q * kLanes;
-        const T vv = (T)M.v[nb + (int64_t)M.hh_row[i] * kLanes];
+        const int row = M.hh_row[i];
+        const T vv = (T)(row == 0 ? x0 : M.v[nb + (int64_t)row * kLanes]);
         T am, bm, ah, bh, an, bn;
         hh_rates<T>(vv, am, bm, ah, bh, an, bn);
         const T tdt = (T)dt;
@@ -310,16 +436,19 @@ __global__ void __launch_bounds__(32) k_interval(DevModel M, int64_t J, int s_be
     }
     // (5) threshold detection and recording
     if (N > 0) {
-      const int now = M.v[spike_i] > thresh;
+      const double vs = spike_row == 0 ? x0 : M.v[nb + (int64_t)spike_row * kLanes];
+      const int now = vs > thresh;
       if (now && !above) mask |= 1ull << s;
       above = now;
       for (int q = 0; q < RR; ++q) {
         if (q < nrec) {
-          const int64_t i = rb + (int64_t)q * kLanes;
-          M.trace[(k + 1) * M.n_rec + M.rec_id[i]] = M.v[nb + (int64_t)M.rec_row[i] * kLanes];
+          const int64_t i = rcb + (int64_t)q * kLanes;
+          const int row = M.rec_row[i];
+          M.trace[(k + 1) * M.n_rec + M.rec_id[i]] = row == 0 ? x0 : M.v[nb + (int64_t)row * kLanes];
         }
       }
     }
+    __syncwarp();  // back-substitution stores precede the next step's copies
   }
   if (gid >= 0) {
     M.hist[J * M.n_cells + gid] = mask;
@@ -327,7 +456,7 @@ __global__ void __launch_bounds__(32) k_interval(DevModel M, int64_t J, int s_be
   }
 }
 
-// Record step-0 voltages.
+// Record step-k voltages.
 __global__ void k_record0(DevModel M, int64_t k) {
   const int slot = blockIdx.x * blockDim.x + threadIdx.x;
   if (slot >= M.n_slots) return;
@@ -345,7 +474,10 @@ __global__ void k_record0(DevModel M, int64_t k) {
 __global__ void k_init_above(DevModel M) {
   const int slot = blockIdx.x * blockDim.x + threadIdx.x;
   if (slot >= M.n_slots) return;
-  if (M.s_rows[slot] == 0) { M.s_above[slot] = 0; return; }
+  if (M.s_rows[slot] == 0) {
+    M.s_above[slot] = 0;
+    return;
+  }
   const int g = slot / kLanes, lane = slot % kLanes;
   const int64_t i = M.g_node_base[g] + lane + (int64_t)M.s_spike_row[slot] * kLanes;
   M.s_above[slot] = M.v[i] > M.s_thresh[slot];

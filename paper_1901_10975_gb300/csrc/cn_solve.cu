@@ -1,0 +1,105 @@
+// cn_solve.cu -- batched tree solves (cn_solve_trees).
+//
+// Gaussian elimination in Hines order (Section 2, citing Hines 1984) of many
+// independent tree matrices given in device memory: row i of tree t has
+// diagonal d[i], coupling b[i] to its parent p and, in row p, coupling a[i]
+// to i.  One thread per tree eliminates leaves to root and back-substitutes
+// root to leaves.  The inputs stay untouched: the eliminated diagonal lives
+// in scratch memory and the right-hand side is copied into the output first.
+#include <cstdint>
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "cn.h"
+
+namespace cn {
+
+enum : int32_t { kSolveBadParent = 1, kSolveZeroPivot = 2 };
+
+// dd: scratch of n_nodes doubles.  status: one int32, OR-ed with error bits;
+// a tree with a bad parent index or a zero pivot is left unsolved.
+__global__ void k_solve_trees(int32_t n_trees, const int32_t* __restrict__ off, const int32_t* __restrict__ parent,
+                              const double* __restrict__ a, const double* __restrict__ b,
+                              const double* __restrict__ d, const double* __restrict__ rhs, double* __restrict__ x,
+                              double* __restrict__ dd, int32_t* status) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_trees) return;
+  const int32_t i0 = off[t], i1 = off[t + 1];
+  if (i1 <= i0) return;
+  if (parent[i0] != -1) {
+    atomicOr(status, kSolveBadParent);
+    return;
+  }
+  for (int32_t i = i0 + 1; i < i1; ++i) {
+    const int32_t p = parent[i];
+    if (p < 0 || p >= i - i0) {
+      atomicOr(status, kSolveBadParent);
+      return;
+    }
+  }
+  for (int32_t i = i0; i < i1; ++i) {
+    dd[i] = d[i];
+    x[i] = rhs[i];
+  }
+  for (int32_t i = i1 - 1; i > i0; --i) {
+    const int32_t p = i0 + parent[i];
+    if (dd[i] == 0.0) {
+      atomicOr(status, kSolveZeroPivot);
+      return;
+    }
+    const double f = a[i] / dd[i];
+    dd[p] -= f * b[i];
+    x[p] -= f * x[i];
+  }
+  if (dd[i0] == 0.0) {
+    atomicOr(status, kSolveZeroPivot);
+    return;
+  }
+  x[i0] /= dd[i0];
+  for (int32_t i = i0 + 1; i < i1; ++i) x[i] = (x[i] - b[i] * x[i0 + parent[i]]) / dd[i];
+}
+
+cn_status solve_status(int32_t st) {
+  if (st & kSolveBadParent) return CN_EINVAL;
+  if (st & kSolveZeroPivot) return CN_ERANGE;
+  return CN_OK;
+}
+
+}  // namespace cn
+
+extern "C" {
+
+cn_status cn_solve_trees(int32_t n_trees, int64_t n_nodes, const int32_t* offset, const int32_t* parent,
+                         const double* a, const double* b, const double* d, const double* rhs, double* x,
+                         void* stream) {
+  if (n_trees < 0 || n_nodes < 0) return CN_EINVAL;
+  if (n_trees == 0 || n_nodes == 0) return CN_OK;
+  if (!offset || !parent || !a || !b || !d || !rhs || !x) return CN_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  double* dd = nullptr;
+  int32_t* status = nullptr;
+  if (cudaMallocAsync(reinterpret_cast<void**>(&dd), (size_t)n_nodes * sizeof(double), st) != cudaSuccess)
+    return CN_ENOMEM;
+  if (cudaMallocAsync(reinterpret_cast<void**>(&status), sizeof(int32_t), st) != cudaSuccess) {
+    cudaFreeAsync(dd, st);
+    return CN_ENOMEM;
+  }
+  cn_status rc = CN_OK;
+  if (cudaMemsetAsync(status, 0, sizeof(int32_t), st) != cudaSuccess) rc = CN_ECUDA;
+  if (rc == CN_OK) {
+    const int tb = 128;
+    cn::k_solve_trees<<<(n_trees + tb - 1) / tb, tb, 0, st>>>(n_trees, offset, parent, a, b, d, rhs, x, dd, status);
+    if (cudaGetLastError() != cudaSuccess) rc = CN_ECUDA;
+  }
+  int32_t h = 0;
+  if (rc == CN_OK && cudaMemcpyAsync(&h, status, sizeof(int32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    rc = CN_ECUDA;
+  cudaFreeAsync(dd, st);
+  cudaFreeAsync(status, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess) rc = CN_ECUDA;
+  if (rc == CN_OK) rc = cn::solve_status(h);
+  return rc;
+}
+
+}  // extern "C"
