@@ -38,8 +38,12 @@ constexpr int32_t kNoSlot = 0xffff;
 constexpr int32_t kFarBit = 1 << 16;
 constexpr int kNFarShift = 17;
 
-// Rows streamed per cp.async ring (pairs of rows).
+// Row pairs kept in flight by the cp.async rings: elimination streams five
+// FP64 arrays and the flags and spends ~10 FP64 instructions per row, back
+// substitution streams two arrays and the flags and spends one, so it needs
+// a deeper ring to cover the same memory latency.  The two rings share memory.
 constexpr int kRingPairs = 4;
+constexpr int kBackPairs = 16;
 
 // Plain-old-data view of a model's device buffers, passed by value.
 struct DevModel {
@@ -126,9 +130,14 @@ struct DevModel {
 };
 
 // Dynamic shared memory of one interval-kernel block (one warp).
+__host__ __device__ inline size_t ring_bytes() {
+  const size_t elim = (size_t)2 * kRingPairs * kLanes * (5 * sizeof(double) + sizeof(int32_t));
+  const size_t back = (size_t)2 * kBackPairs * kLanes * (2 * sizeof(double) + sizeof(int32_t));
+  return elim > back ? elim : back;
+}
 __host__ __device__ inline size_t interval_smem_bytes(int stack_depth, int max_slots) {
-  const size_t ring = (size_t)2 * kRingPairs * kLanes * (5 * sizeof(double) + sizeof(int32_t));
-  return ring + (size_t)stack_depth * kLanes * 2 * sizeof(double) + (size_t)max_slots * kLanes * 2 * sizeof(double);
+  return ring_bytes() + (size_t)stack_depth * kLanes * 3 * sizeof(double) +
+         (size_t)max_slots * kLanes * 2 * sizeof(double);
 }
 
 // 16-byte asynchronous global->shared copy (through L1, so a warp's own

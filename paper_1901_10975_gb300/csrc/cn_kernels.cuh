@@ -47,6 +47,17 @@ __global__ void k_setup_nodes(DevModel M, const double* area, const double* ri, 
     M.v[i] = v_init;
     M.bp[i] = 0.0;
   }
+  // Rows past the cell's end (the group's rows are those of its largest
+  // cell) are identity rows with zero couplings: eliminating them is a no-op.
+  for (int j = N; j < M.g_rows[g]; ++j) {
+    const int64_t i = nb + (int64_t)j * kLanes;
+    d0[i] = 1.0;
+    ge[i] = 0.0;
+    a[i] = 0.0;
+    b[i] = 0.0;
+    M.v[i] = 0.0;
+    M.bp[i] = 0.0;
+  }
 }
 
 // Per-slot copies of the slot row's constants (the slot buffer is reset to
@@ -228,13 +239,18 @@ __global__ void __launch_bounds__(32) k_interval(DevModel M, int64_t J, int s_be
   const int gid = M.s_gid[slot];
   const int DS = M.stack_depth;
 
-  double* r_v = reinterpret_cast<double*>(smem);  // [KR][32] each
+  double* r_v = reinterpret_cast<double*>(smem);  // elimination ring, [KR][32] each
   double* r_ge = r_v + KR * kLanes;
   double* r_d0 = r_ge + KR * kLanes;
   double* r_a = r_d0 + KR * kLanes;
   double* r_b = r_a + KR * kLanes;
   int32_t* r_fl = reinterpret_cast<int32_t*>(r_b + KR * kLanes);
-  double* st_x = reinterpret_cast<double*>(r_fl + KR * kLanes);  // [DS][32]
+  constexpr int KB = 2 * kBackPairs;               // back-substitution ring, same memory
+  double* q_x = reinterpret_cast<double*>(smem);
+  double* q_bp = q_x + KB * kLanes;
+  int32_t* q_fl = reinterpret_cast<int32_t*>(q_bp + KB * kLanes);
+  double* st_a = reinterpret_cast<double*>(smem + ring_bytes());  // far stack, [DS][32] each
+  double* st_x = st_a + DS * kLanes;
   double* st_y = st_x + DS * kLanes;
   double* sl_ge = st_y + DS * kLanes;             // [max_slots][32]
   double* sl_d = sl_ge + M.max_slots * kLanes;
@@ -280,14 +296,24 @@ __global__ void __launch_bounds__(32) k_interval(DevModel M, int64_t J, int s_be
   };
   auto prefetch_back = [&](int P) {
     if (P <= PT) {
-      const int rr = ((P % kRingPairs) * 2 + half) * kLanes;
+      const int rr = ((P % kBackPairs) * 2 + half) * kLanes;
       const int64_t src = gb + (int64_t)(2 * P + half) * kLanes + 2 * chunk;
-      cp_async16(r_v + rr + 2 * chunk, M.v + src);
-      cp_async16(r_b + rr + 2 * chunk, M.bp + src);
-      if (chunk < 8) cp_async16(r_fl + rr + 4 * chunk, M.flags + gb + (int64_t)(2 * P + half) * kLanes + 4 * chunk);
+      cp_async16(q_x + rr + 2 * chunk, M.v + src);
+      cp_async16(q_bp + rr + 2 * chunk, M.bp + src);
+      if (chunk < 8) cp_async16(q_fl + rr + 4 * chunk, M.flags + gb + (int64_t)(2 * P + half) * kLanes + 4 * chunk);
     }
     cp_async_commit();
   };
+
+  // Slot buffer: seeded once per launch with the rows' constants; after that
+  // every elimination row re-seeds its own slot from the ring for the next step.
+  for (int t = 0; t < SLR; ++t) {
+    if (t < nslot) {
+      const int64_t i = slb + (int64_t)t * kLanes;
+      sl_ge[t * kLanes + lane] = M.slot_ge0[i];
+      sl_d[t * kLanes + lane] = M.slot_d00[i];
+    }
+  }
 
   for (int s = s_begin; s < s_end; ++s) {
     const int64_t k = T0 + s;
@@ -298,23 +324,34 @@ __global__ void __launch_bounds__(32) k_interval(DevModel M, int64_t J, int s_be
       M.syn_g[sb + (int64_t)ev[ei].syn * kLanes] += ev[ei].w;
       ++ei;
     }
-    // (2) nrn_cur into the slot buffer
-    for (int t = 0; t < SLR; ++t) {
-      if (t < nslot) {
-        const int64_t i = slb + (int64_t)t * kLanes;
-        sl_ge[t * kLanes + lane] = M.slot_ge0[i];
-        sl_d[t * kLanes + lane] = M.slot_d00[i];
+    // (2) nrn_cur into the slot buffer; synapses in batches of 8 so that
+    //     their loads are in flight together
+    constexpr int kSynBatch = 8;
+    for (int q0 = 0; q0 < SR; q0 += kSynBatch) {
+      double gs[kSynBatch], ss[kSynBatch], se[kSynBatch], sd[kSynBatch];
+      int st[kSynBatch];
+#pragma unroll
+      for (int u = 0; u < kSynBatch; ++u) {
+        const int q = q0 + u;
+        if (q < nsyn) {
+          const int64_t i = sb + (int64_t)q * kLanes;
+          gs[u] = M.syn_g[i];
+          ss[u] = M.syn_s[i];
+          se[u] = M.syn_e[i];
+          sd[u] = M.syn_decay[i];
+          st[u] = M.syn_slot[i];
+        }
       }
-    }
-    for (int q = 0; q < SR; ++q) {
-      if (q < nsyn) {
-        const int64_t i = sb + (int64_t)q * kLanes;
-        const double gs = M.syn_g[i];
-        const double G = gs * M.syn_s[i];
-        const int t = M.syn_slot[i] * kLanes + lane;
-        sl_ge[t] = fma(G, M.syn_e[i], sl_ge[t]);
-        sl_d[t] += G;
-        M.syn_g[i] = gs * M.syn_decay[i];  // ExpSyn state update: v-independent
+#pragma unroll
+      for (int u = 0; u < kSynBatch; ++u) {
+        const int q = q0 + u;
+        if (q < nsyn) {
+          const double G = gs[u] * ss[u];
+          const int t = st[u] * kLanes + lane;
+          sl_ge[t] = fma(G, se[u], sl_ge[t]);
+          sl_d[t] += G;
+          M.syn_g[sb + (int64_t)q * kLanes] = gs[u] * sd[u];  // ExpSyn state update: v-independent
+        }
       }
     }
     for (int q = 0; q < HR; ++q) {
@@ -339,84 +376,96 @@ __global__ void __launch_bounds__(32) k_interval(DevModel M, int64_t J, int s_be
         }
       }
     }
-    // (3) elimination, leaves to root
-    double ca = 0.0, cx = 0.0, cb = 0.0, x0 = 0.0;
+    // (3) elimination, leaves to root.  Branch-free per row: a far child
+    //     pushes its raw (-a, x, b/d) onto the lane's stack and its parent
+    //     pops it into two FMAs (with zero coefficients on rows that pop
+    //     nothing); the previous row's carry enters the same way.
+    double ca = 0.0, cx = 0.0, cb = 0.0, x = 0.0;
     int top = 0;
-    int nfar0 = 0;
     for (int P = PT; P >= 0; --P) {
       cp_async_wait<kRingPairs - 1>();
       __syncwarp();
+      const int rb = (P & (kRingPairs - 1)) * 2 * kLanes + lane;
+#pragma unroll
       for (int h = 1; h >= 0; --h) {
         const int j = 2 * P + h;
-        if (j < N) {
-          const int rr = ((P % kRingPairs) * 2 + h) * kLanes + lane;
-          const int f = r_fl[rr];
-          const int sl = f & kNoSlot;
-          double gE = r_ge[rr], dd = r_d0[rr];
-          if (sl != kNoSlot) {
-            gE = sl_ge[sl * kLanes + lane];
-            dd = sl_d[sl * kLanes + lane];
-          }
-          double rhs = fma(ca, cx, r_v[rr] + gE);
-          double d = fma(ca, cb, dd);
-          for (int np = f >> kNFarShift; np > 0; --np) {
-            --top;
-            rhs += st_x[top * kLanes + lane];
-            d += st_y[top * kLanes + lane];
-          }
-          const double r = rcp64(d);
-          const double x = rhs * r;
-          const int64_t gi = nb + (int64_t)j * kLanes;
-          if (j == 0) {
-            x0 = x;
-            nfar0 = f >> kNFarShift;
-            M.v[gi] = x;
-          } else {
-            const double bp = r_b[rr] * r;
-            M.v[gi] = x;
-            M.bp[gi] = bp;
-            const double na = -r_a[rr];
-            if (f & kFarBit) {
-              st_x[top * kLanes + lane] = na * x;
-              st_y[top * kLanes + lane] = na * bp;
-              ++top;
-              ca = 0.0;
-            } else {
-              ca = na;
-              cx = x;
-              cb = bp;
-            }
-          }
+        const int rr = rb + h * kLanes;
+        const int f = r_fl[rr];
+        const int sl = f & kNoSlot;
+        const bool hs = sl != kNoSlot;
+        const int si = (hs ? sl : 0) * kLanes + lane;
+        const double g0 = r_ge[rr], d00 = r_d0[rr];
+        const double sg = sl_ge[si], sd = sl_d[si];
+        if (hs) {
+          sl_ge[si] = g0;  // re-seed the slot for the next step
+          sl_d[si] = d00;
         }
+        const int np = f >> kNFarShift;
+        const int tp = np > 0 ? top - 1 : top;
+        const int ti = (tp < DS ? tp : DS - 1) * kLanes + lane;
+        // stale stack words must not reach the FMAs (0 * NaN is NaN): select
+        const double fa = np > 0 ? st_a[ti] : 0.0;
+        const double fx = np > 0 ? st_x[ti] : 0.0;
+        const double fb = np > 0 ? st_y[ti] : 0.0;
+        top = tp;
+        double rhs = fma(fa, fx, r_v[rr] + (hs ? sg : g0));
+        double d = fma(fa, fb, hs ? sd : d00);
+        for (int q = 1; q < np; ++q) {  // third and further children (rare)
+          --top;
+          rhs = fma(st_a[top * kLanes + lane], st_x[top * kLanes + lane], rhs);
+          d = fma(st_a[top * kLanes + lane], st_y[top * kLanes + lane], d);
+        }
+        rhs = fma(ca, cx, rhs);
+        d = fma(ca, cb, d);
+        const double r = rcp64(d);
+        x = rhs * r;
+        const double bp = r_b[rr] * r;
+        const int64_t gi = nb + (int64_t)j * kLanes;
+        M.v[gi] = x;
+        M.bp[gi] = bp;
+        const double na = -r_a[rr];
+        const bool far = (f & kFarBit) != 0;
+        if (far) {
+          st_a[top * kLanes + lane] = na;
+          st_x[top * kLanes + lane] = x;
+          st_y[top * kLanes + lane] = bp;
+        }
+        top += far ? 1 : 0;
+        ca = far ? 0.0 : na;
+        cx = x;
+        cb = bp;
       }
       __syncwarp();
       prefetch_elim(P - kRingPairs);
     }
+    const double x0 = x;  // row 0 is eliminated last
     cp_async_wait<0>();
     __syncwarp();  // every lane's elimination stores precede the copies below
-    // back substitution, root to leaves
-    for (int i = 0; i < kRingPairs; ++i) prefetch_back(i);
-    double vprev = x0;
-    for (int q = 0; q < nfar0; ++q) st_x[(top + q) * kLanes + lane] = x0;
-    top += nfar0;
+    // back substitution, root to leaves (row 0: b = 0, so v_0 = x_0)
+    for (int i = 0; i < kBackPairs; ++i) prefetch_back(i);
+    double vprev = 0.0;
     for (int P = 0; P <= PT; ++P) {
-      cp_async_wait<kRingPairs - 1>();
+      cp_async_wait<kBackPairs - 1>();
       __syncwarp();
+      const int rb = (P & (kBackPairs - 1)) * 2 * kLanes + lane;
+#pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int j = 2 * P + h;
-        if (j >= 1 && j < N) {
-          const int rr = ((P % kRingPairs) * 2 + h) * kLanes + lane;
-          const int f = r_fl[rr];
-          double vp = vprev;
-          if (f & kFarBit) vp = st_x[--top * kLanes + lane];
-          const double vj = fma(-r_b[rr], vp, r_v[rr]);
-          M.v[nb + (int64_t)j * kLanes] = vj;
-          for (int np = f >> kNFarShift; np > 0; --np) st_x[top++ * kLanes + lane] = vj;
-          vprev = vj;
-        }
+        const int rr = rb + h * kLanes;
+        const int f = q_fl[rr];
+        const bool far = (f & kFarBit) != 0;
+        const int tp = far ? top - 1 : top;
+        const double pv = st_x[(tp < DS ? tp : DS - 1) * kLanes + lane];
+        const double vj = fma(-q_bp[rr], far ? pv : vprev, q_x[rr]);
+        M.v[nb + (int64_t)j * kLanes] = vj;
+        const int np = f >> kNFarShift;
+        if (np > 0) st_x[tp * kLanes + lane] = vj;
+        for (int q = 1; q < np; ++q) st_x[(tp + q) * kLanes + lane] = vj;
+        top = tp + np;
+        vprev = vj;
       }
       __syncwarp();
-      prefetch_back(P + kRingPairs);
+      prefetch_back(P + kBackPairs);
     }
     cp_async_wait<0>();
     __syncwarp();
