@@ -227,6 +227,23 @@ cn_status cn_solve_trees(int32_t n_trees, int64_t n_nodes, const int32_t* offset
                          const double* a, const double* b, const double* d, const double* rhs, double* x,
                          void* stream);
 
+/* cn_solve_trees without any device allocation.  The paper has no
+ * counterpart: this exists for callers that cannot allocate device memory
+ * when they solve -- for example because another allocator already reserved
+ * the whole GPU, or because an allocation would stall a latency-critical
+ * loop.  Same arguments, layout and results as cn_solve_trees, but the
+ * working diagonal lives in a fixed array built into the library: at most
+ * 1,048,576 rows (n_nodes) per call (CN_ERANGE above that); every GPU that
+ * loads the library holds that 8 MiB array until the process exits.  The
+ * first call on a device looks up the array's device address (once per
+ * device), so make that first call before any stream capture.  All calls on
+ * a device share the one array: calls whose execution overlaps on the GPU
+ * (other streams, other host threads) race and must be serialized by the
+ * caller.  Synchronizes the stream before returning; allocates nothing.    */
+cn_status cn_solve_trees_noalloc(int32_t n_trees, int64_t n_nodes, const int32_t* offset, const int32_t* parent,
+                                 const double* a, const double* b, const double* d, const double* rhs, double* x,
+                                 void* stream);
+
 /* Error text of the last failed call on m (or of the last failed
  * cn_model_create when m is NULL).  Valid until the next call on m.        */
 const char* cn_last_error(const cn_model* m);

@@ -104,6 +104,8 @@ def lib():
         L.cn_solve_trees.argtypes = [C.c_int32, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         L.cn_solve_trees.restype = st
+        L.cn_solve_trees_noalloc.argtypes = list(L.cn_solve_trees.argtypes)
+        L.cn_solve_trees_noalloc.restype = st
         L.cn_last_error.argtypes = [C.c_void_p]
         L.cn_last_error.restype = C.c_char_p
         L.cn_model_destroy.argtypes = [C.c_void_p]
@@ -161,6 +163,21 @@ def cn_solve_trees(offset, parent, a, b, d, rhs, device=0):
                               t["x"].data_ptr(), stream)
     if st != CN_OK:
         raise CNError(st, "cn_solve_trees failed")
+    return t["x"].cpu().numpy()
+
+
+def cn_solve_trees_noalloc(offset, parent, a, b, d, rhs, device=0):
+    """cn_solve_trees through the allocation-free entry point (the library's
+    fixed scratch array instead of a per-call allocation)."""
+    import torch
+    t = _device_tree_args(offset, parent, a, b, d, rhs, device)
+    stream = torch.cuda.current_stream(device).cuda_stream
+    n_trees = t["offset"].numel() - 1
+    st = lib().cn_solve_trees_noalloc(n_trees, t["rhs"].numel(), t["offset"].data_ptr(), t["parent"].data_ptr(),
+                                      t["a"].data_ptr(), t["b"].data_ptr(), t["d"].data_ptr(),
+                                      t["rhs"].data_ptr(), t["x"].data_ptr(), stream)
+    if st != CN_OK:
+        raise CNError(st, "cn_solve_trees_noalloc failed")
     return t["x"].cpu().numpy()
 
 

@@ -7,6 +7,7 @@
 // root to leaves.  The inputs stay untouched: the eliminated diagonal lives
 // in scratch memory and the right-hand side is copied into the output first.
 #include <cstdint>
+#include <mutex>
 #include <string>
 
 #include <cuda_runtime.h>
@@ -103,3 +104,72 @@ cn_status cn_solve_trees(int32_t n_trees, int64_t n_nodes, const int32_t* offset
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------
+// Allocation-free variant of cn_solve_trees.
+//
+// Some callers cannot allocate device memory at the moment they need a
+// solve: their GPU memory is already reserved in full by another allocator
+// (a framework's caching pool), or an allocation would synchronize or stall
+// a latency-critical loop.  For them the working diagonal and the status
+// word live in the fixed arrays below, which are part of this library's
+// device image: every GPU that loads the library holds them (8 MiB + 4
+// bytes) until the process exits.  In host code these names are host-side
+// stand-ins, never device addresses; their device addresses are looked up
+// once per device with cudaGetSymbolAddress.
+namespace {
+
+constexpr int64_t kNoAllocMaxNodes = int64_t(1) << 20;  // rows across all trees of one call
+
+static __device__ __align__(256) double g_noalloc_dd[kNoAllocMaxNodes];
+static __device__ __align__(256) int32_t g_noalloc_status[1];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double* g_noalloc_dd_ptr[kMaxDevices] = {};
+int32_t* g_noalloc_status_ptr[kMaxDevices] = {};
+
+// Device addresses of the fixed scratch on the current device (set up on the
+// first call per device).
+cn_status noalloc_scratch(double** dd, int32_t** status) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return CN_ECUDA;
+  if (dev < 0 || dev >= kMaxDevices) return CN_EINVAL;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_dd_ptr[dev]) {
+    void* p = nullptr;
+    void* q = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_dd) != cudaSuccess) return CN_ECUDA;
+    if (cudaGetSymbolAddress(&q, g_noalloc_status) != cudaSuccess) return CN_ECUDA;
+    g_noalloc_dd_ptr[dev] = static_cast<double*>(p);
+    g_noalloc_status_ptr[dev] = static_cast<int32_t*>(q);
+  }
+  *dd = g_noalloc_dd_ptr[dev];
+  *status = g_noalloc_status_ptr[dev];
+  return CN_OK;
+}
+
+}  // namespace
+
+extern "C" cn_status cn_solve_trees_noalloc(int32_t n_trees, int64_t n_nodes, const int32_t* offset,
+                                            const int32_t* parent, const double* a, const double* b,
+                                            const double* d, const double* rhs, double* x, void* stream) {
+  if (n_trees < 0 || n_nodes < 0) return CN_EINVAL;
+  if (n_nodes > kNoAllocMaxNodes) return CN_ERANGE;
+  if (n_trees == 0 || n_nodes == 0) return CN_OK;
+  if (!offset || !parent || !a || !b || !d || !rhs || !x) return CN_EINVAL;
+  double* dd = nullptr;
+  int32_t* status = nullptr;
+  cn_status rc = noalloc_scratch(&dd, &status);
+  if (rc != CN_OK) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // The status word must start at zero; the diagonal is fully overwritten.
+  if (cudaMemsetAsync(status, 0, sizeof(int32_t), st) != cudaSuccess) return CN_ECUDA;
+  const int tb = 128;
+  cn::k_solve_trees<<<(n_trees + tb - 1) / tb, tb, 0, st>>>(n_trees, offset, parent, a, b, d, rhs, x, dd, status);
+  if (cudaGetLastError() != cudaSuccess) return CN_ECUDA;
+  int32_t h = 0;
+  if (cudaMemcpyAsync(&h, status, sizeof(int32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess) return CN_ECUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return CN_ECUDA;
+  return cn::solve_status(h);
+}
