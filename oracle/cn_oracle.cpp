@@ -559,6 +559,222 @@ void run(Model& M, int64_t nsteps, int nthreads) {
   }
 }
 
+
+// ------------------------------------------------------------------ adjoint
+// Discrete adjoint of one cell's backward-Euler trajectory.  The forward map
+// of step k is A_k v_{k+1} = C v_k + b_k with A_k = C + G_k + L (C = cdt,
+// G_k the membrane conductances frozen at the gates of step k, L the axial
+// couplings) and gates_{k+1} = Phi(gates_k, v_{k+1}) (cnexp).  With the loss
+// J = sum_r sum_{k=1..K} (v_r,k - target_r,k)^2 over the cell's recorded
+// nodes, walking k from K-1 down to 0:
+//   mu_k     = A_k^-T lambda_{k+1}                       (Hines, a and b swapped)
+//   xi_k     = dPhi_k/dgates_k xi_{k+1} + mu_s d(GE - G v_{s,k+1})/dgates_k
+//   lambda_k = dJ/dv_k (direct) + C mu_k + (dPhi_{k-1}/dv_k)^T xi_k
+// and parameter gradients mu_k . d(b_k - A_k v_{k+1})/dtheta.
+
+// HH rate derivatives (same rates as hh_rates).
+double vtrap_deriv(double A, double vh, double k, double v) {
+  double u = (v - vh) / k;
+  if (std::fabs(u) < 1e-6) return A * (0.5 + u / 3.0);
+  double em = std::exp(-u);
+  double den = 1.0 - em;
+  return A * (den - u * em) / (den * den);
+}
+
+void hh_rate_derivs(double v, double* dam, double* dbm, double* dah, double* dbh, double* dan, double* dbn) {
+  *dam = vtrap_deriv(0.1, -40.0, 10.0, v);
+  *dbm = -4.0 * std::exp(-(v + 65.0) / 18.0) / 18.0;
+  *dah = -0.07 * std::exp(-(v + 65.0) / 20.0) / 20.0;
+  double bh = 1.0 / (1.0 + std::exp(-(v + 35.0) / 10.0));
+  *dbh = bh * (1.0 - bh) / 10.0;
+  *dan = vtrap_deriv(0.01, -55.0, 10.0, v);
+  *dbn = -0.125 * std::exp(-(v + 65.0) / 80.0) / 80.0;
+}
+
+// d x_{k+1} / d v_{k+1} and d x_{k+1} / d x_k of the cnexp update.
+void cnexp_derivs(double x, double al, double be, double dal, double dbe, double dt, double* dv, double* dx) {
+  double s = al + be;
+  double inf = al / s;
+  double E = std::exp(-dt * s);
+  double dinf = (dal * be - al * dbe) / (s * s);
+  double dE = -dt * (dal + dbe) * E;
+  *dv = dinf * (1.0 - E) + (x - inf) * dE;
+  *dx = E;
+}
+
+struct CellSnap {
+  std::vector<double> v;
+  std::vector<std::vector<double>> hh;  // [3][instances of the cell]
+  std::vector<double> syn;
+};
+
+void cell_adjoint(Model& M, int c, int64_t K, int seg, const double* target, const std::vector<int32_t>& recs,
+                  double* J, double* g_na, double* g_k, double* g_pas) {
+  const int i0 = M.off[c], i1 = M.off[c + 1], n = i1 - i0;
+  const double dt = M.dt;
+  Mech& hh = M.mech[OR_HH];
+  Mech& pas = M.mech[OR_PAS];
+  Mech& syn = M.mech[OR_EXPSYN];
+  std::vector<int> hh_inst, pas_inst, syn_inst;
+  if (hh.kind >= 0) for (int q = hh.cell_start[c]; q < hh.cell_start[c + 1]; ++q) hh_inst.push_back(hh.by_cell[q]);
+  if (pas.kind >= 0) for (int q = pas.cell_start[c]; q < pas.cell_start[c + 1]; ++q) pas_inst.push_back(pas.by_cell[q]);
+  if (syn.kind >= 0) for (int q = syn.cell_start[c]; q < syn.cell_start[c + 1]; ++q) syn_inst.push_back(syn.by_cell[q]);
+  auto snap = [&]() {
+    CellSnap s;
+    s.v.assign(M.v.begin() + i0, M.v.begin() + i1);
+    s.hh.assign(3, {});
+    for (int g = 0; g < 3; ++g)
+      for (int q : hh_inst) s.hh[g].push_back(hh.S[g][q]);
+    for (int q : syn_inst) s.syn.push_back(syn.S[0][q]);
+    return s;
+  };
+  auto restore = [&](const CellSnap& s) {
+    std::copy(s.v.begin(), s.v.end(), M.v.begin() + i0);
+    for (int g = 0; g < 3; ++g)
+      for (size_t t = 0; t < hh_inst.size(); ++t) hh.S[g][hh_inst[t]] = s.hh[g][t];
+    for (size_t t = 0; t < syn_inst.size(); ++t) syn.S[0][syn_inst[t]] = s.syn[t];
+  };
+  std::vector<std::pair<int64_t, int32_t>> dummy;
+  // forward with checkpoints every `seg` steps; loss
+  std::vector<CellSnap> cps;
+  double loss = 0.0;
+  for (int64_t k = 0; k < K; ++k) {
+    if (k % seg == 0) cps.push_back(snap());
+    cell_step(M, c, k, dummy);
+    for (size_t r = 0; r < recs.size(); ++r) {
+      double e = M.v[M.rec_node[recs[r]]] - target[(size_t)recs[r] * (K + 1) + (k + 1)];
+      loss += e * e;
+    }
+  }
+  *J = loss;
+  // backward
+  std::vector<double> lam(n, 0.0), mu(n), d(n), rhs(n);
+  for (size_t r = 0; r < recs.size(); ++r) {
+    int i = M.rec_node[recs[r]];
+    lam[i - i0] += 2.0 * (M.v[i] - target[(size_t)recs[r] * (K + 1) + K]);
+  }
+  const int nh = (int)hh_inst.size();
+  std::vector<double> xi(3 * nh, 0.0);
+  for (int64_t sb = ((K - 1) / seg) * seg; sb >= 0; sb -= seg) {
+    const int64_t se = std::min<int64_t>(K, sb + seg);
+    // recompute v_k (all nodes) and gates_k for k in [sb, se]
+    restore(cps[sb / seg]);
+    std::vector<std::vector<double>> vs(se - sb + 1), gs(se - sb + 1), ss(se - sb + 1);
+    auto record = [&](int64_t t) {
+      vs[t].assign(M.v.begin() + i0, M.v.begin() + i1);
+      gs[t].clear();
+      for (int g = 0; g < 3; ++g)
+        for (int q : hh_inst) gs[t].push_back(hh.S[g][q]);
+      ss[t].clear();
+      for (int q : syn_inst) ss[t].push_back(syn.S[0][q]);
+    };
+    record(0);
+    for (int64_t k = sb; k < se; ++k) {
+      cell_step(M, c, k, dummy);
+      record(k - sb + 1);
+    }
+    for (int64_t k = se - 1; k >= sb; --k) {
+      const std::vector<double>& vk1 = vs[k - sb + 1];
+      const std::vector<double>& gk = gs[k - sb];
+      // A_k: diagonal from the conductances of step k
+      for (int i = 0; i < n; ++i) d[i] = 1e-3 * M.cm[i0 + i] / dt;
+      for (int q : pas_inst) d[pas.node[q] - i0] += pas.P[0][q];
+      for (int t = 0; t < nh; ++t) {
+        int q = hh_inst[t];
+        double m = gk[t], h = gk[nh + t], nn = gk[2 * nh + t];
+        d[hh.node[q] - i0] += hh.P[0][q] * m * m * m * h + hh.P[1][q] * nn * nn * nn * nn + hh.P[2][q];
+      }
+      for (size_t t = 0; t < syn_inst.size(); ++t) {
+        int q = syn_inst[t];
+        int nd = syn.node[q];
+        d[nd - i0] += 100.0 * ss[k - sb][t] / M.area[nd];
+      }
+      for (int i = 1; i < n; ++i) {
+        int p = M.parent[i0 + i] - i0;
+        d[i] -= M.b[i0 + i];
+        d[p] -= M.a[i0 + i];
+      }
+      // transposed Hines solve: A^T has b where A has a and vice versa
+      for (int i = 0; i < n; ++i) rhs[i] = lam[i];
+      for (int i = n - 1; i > 0; --i) {
+        int p = M.parent[i0 + i] - i0;
+        double f = M.b[i0 + i] / d[i];
+        d[p] -= f * M.a[i0 + i];
+        rhs[p] -= f * rhs[i];
+      }
+      rhs[0] /= d[0];
+      for (int i = 1; i < n; ++i) {
+        int p = M.parent[i0 + i] - i0;
+        rhs[i] = (rhs[i] - M.a[i0 + i] * rhs[p]) / d[i];
+      }
+      mu = rhs;
+      // parameter gradients and the gates' adjoint
+      for (int t = 0; t < nh; ++t) {
+        int q = hh_inst[t];
+        int si = hh.node[q] - i0;
+        double vs1 = vk1[si];
+        double m = gk[t], h = gk[nh + t], nn = gk[2 * nh + t];
+        double ena = hh.P[4][q], ek = hh.P[5][q];
+        g_na[q] += mu[si] * m * m * m * h * (ena - vs1);
+        g_k[q] += mu[si] * nn * nn * nn * nn * (ek - vs1);
+        double am, bm, ah, bh, an, bn, dam, dbm, dah, dbh, dan, dbn;
+        hh_rates(vs1, &am, &bm, &ah, &bh, &an, &bn);
+        double dvx, Em, Eh, En;
+        cnexp_derivs(m, am, bm, 0, 0, dt, &dvx, &Em);
+        cnexp_derivs(h, ah, bh, 0, 0, dt, &dvx, &Eh);
+        cnexp_derivs(nn, an, bn, 0, 0, dt, &dvx, &En);
+        (void)dam; (void)dbm; (void)dah; (void)dbh; (void)dan; (void)dbn;
+        double gna = hh.P[0][q], gkb = hh.P[1][q];
+        double xm = Em * xi[t] + mu[si] * gna * 3.0 * m * m * h * (ena - vs1);
+        double xh = Eh * xi[nh + t] + mu[si] * gna * m * m * m * (ena - vs1);
+        double xn = En * xi[2 * nh + t] + mu[si] * gkb * 4.0 * nn * nn * nn * (ek - vs1);
+        xi[t] = xm;
+        xi[nh + t] = xh;
+        xi[2 * nh + t] = xn;
+      }
+      for (int q : pas_inst) {
+        int i = pas.node[q] - i0;
+        g_pas[q] += mu[i] * (pas.P[1][q] - vk1[i]);
+      }
+      // lambda_k
+      const std::vector<double>& vk = vs[k - sb];
+      for (int i = 0; i < n; ++i) lam[i] = 1e-3 * M.cm[i0 + i] / dt * mu[i];
+      if (k >= 1) {
+        for (size_t r = 0; r < recs.size(); ++r) {
+          int i = M.rec_node[recs[r]];
+          lam[i - i0] += 2.0 * (vk[i - i0] - target[(size_t)recs[r] * (K + 1) + k]);
+        }
+        // gates_k = Phi(gates_{k-1}, v_k): needs gates_{k-1}
+        if (nh > 0) {
+          std::vector<double> gprev;
+          if (k - 1 >= sb) gprev = gs[k - 1 - sb];
+          else {  // previous segment's last gate state: recompute it from its checkpoint
+            CellSnap cur = snap();
+            restore(cps[(k - 1) / seg]);
+            for (int64_t kk = ((k - 1) / seg) * seg; kk < k - 1; ++kk) cell_step(M, c, kk, dummy);
+            for (int g = 0; g < 3; ++g)
+              for (int q : hh_inst) gprev.push_back(hh.S[g][q]);
+            restore(cur);
+          }
+          for (int t = 0; t < nh; ++t) {
+            int q = hh_inst[t];
+            int si = hh.node[q] - i0;
+            double vv = vk[si];
+            double am, bm, ah, bh, an, bn, dam, dbm, dah, dbh, dan, dbn;
+            hh_rates(vv, &am, &bm, &ah, &bh, &an, &bn);
+            hh_rate_derivs(vv, &dam, &dbm, &dah, &dbh, &dan, &dbn);
+            double dvm, dvh, dvn, e_;
+            cnexp_derivs(gprev[t], am, bm, dam, dbm, dt, &dvm, &e_);
+            cnexp_derivs(gprev[nh + t], ah, bh, dah, dbh, dt, &dvh, &e_);
+            cnexp_derivs(gprev[2 * nh + t], an, bn, dan, dbn, dt, &dvn, &e_);
+            lam[si] += xi[t] * dvm + xi[nh + t] * dvh + xi[2 * nh + t] * dvn;
+          }
+        }
+      }
+    }
+  }
+}
+
 }  // namespace
 
 extern "C" {
@@ -639,6 +855,47 @@ void or_hines_solve(int32_t n, const int32_t* parent, const double* a, const dou
   }
   rhs[0] /= d[0];
   for (int i = 1; i < n; ++i) rhs[i] = (rhs[i] - b[i] * rhs[parent[i]]) / d[i];
+}
+
+// Adjoint of J = sum over recorded nodes and steps 1..K of (v - target)^2 for
+// a network without NetCons: target is [n_rec][K+1]; gradients with respect
+// to every HH instance's gnabar and gkbar and every pas instance's g.
+// Checkpoints every `seg` steps, recomputed forward per segment.
+int or_adjoint(const or_scenario* s, int64_t K, const double* target, int32_t seg, int nthreads, double* J,
+               double* g_na, double* g_k, double* g_pas, char* errbuf, int errlen) {
+  Model M;
+  if (!build(M, s)) {
+    if (errbuf && errlen > 0) std::snprintf(errbuf, errlen, "%s", M.err.c_str());
+    return -1;
+  }
+  if (s->n_netcon > 0 || seg < 1 || K < 1) {
+    if (errbuf && errlen > 0) std::snprintf(errbuf, errlen, "adjoint needs no NetCons, seg >= 1, K >= 1");
+    return -1;
+  }
+  std::vector<std::vector<int32_t>> cell_rec(M.n_cells);
+  for (int r = 0; r < s->n_rec; ++r) {
+    int c = 0;
+    while (M.off[c + 1] <= M.rec_node[r]) ++c;
+    cell_rec[c].push_back(r);
+  }
+  if (M.mech[OR_HH].kind >= 0) {
+    std::fill(g_na, g_na + M.mech[OR_HH].n, 0.0);
+    std::fill(g_k, g_k + M.mech[OR_HH].n, 0.0);
+  }
+  if (M.mech[OR_PAS].kind >= 0) std::fill(g_pas, g_pas + M.mech[OR_PAS].n, 0.0);
+  std::vector<double> Jc(M.n_cells, 0.0);
+  if (nthreads < 1) nthreads = 1;
+  auto work = [&](int tid) {
+    for (int c = tid; c < M.n_cells; c += nthreads)
+      cell_adjoint(M, c, K, seg, target, cell_rec[c], &Jc[c], g_na, g_k, g_pas);
+  };
+  std::vector<std::thread> th;
+  for (int t = 0; t < nthreads; ++t) th.emplace_back(work, t);
+  for (auto& x : th) x.join();
+  double tot = 0.0;
+  for (double x : Jc) tot += x;
+  *J = tot;
+  return 0;
 }
 
 }  // extern "C"

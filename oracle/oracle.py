@@ -77,6 +77,9 @@ def lib():
         L.or_get_state.restype = C.c_int
         L.or_get_geometry.argtypes = [C.c_void_p, _P_F64, _P_F64]
         L.or_hines_solve.argtypes = [C.c_int32, _P_I32, _P_F64, _P_F64, _P_F64, _P_F64]
+        L.or_adjoint.argtypes = [C.POINTER(_Scenario), C.c_int64, _P_F64, C.c_int32, C.c_int, _P_F64, _P_F64,
+                                 _P_F64, _P_F64, C.c_char_p, C.c_int]
+        L.or_adjoint.restype = C.c_int
         _lib = L
     return _lib
 
@@ -95,6 +98,64 @@ def hines_solve(parent, a, b, d, rhs):
     lib().or_hines_solve(len(parent), _p(parent, _P_I32), _p(a, _P_F64), _p(b, _P_F64),
                          _p(d, _P_F64), _p(x, _P_F64))
     return x
+
+
+def _marshal(sc, keep):
+    def i32(x):
+        a = np.ascontiguousarray(x, np.int32)
+        keep.append(a)
+        return _p(a, _P_I32)
+
+    def f64(x):
+        a = np.ascontiguousarray(x, np.float64)
+        keep.append(a)
+        return _p(a, _P_F64)
+
+    mechs = (_MechIn * max(1, len(sc.mechs)))()
+    keep.append(mechs)
+    for t, m in enumerate(sc.mechs):
+        mechs[t].kind = KIND[m.kind]
+        mechs[t].n = m.n
+        mechs[t].node = i32(m.node)
+        mechs[t].param = f64(m.param_matrix().reshape(-1))
+    s = _Scenario()
+    s.dt, s.v_init, s.n_cells = sc.dt, sc.v_init, sc.n_cells
+    s.cell_offset, s.parent = i32(sc.cell_offset), i32(sc.parent)
+    s.dx, s.diam, s.Ra, s.cm = f64(sc.dx), f64(sc.diam), f64(sc.Ra), f64(sc.cm)
+    s.spike_node, s.threshold = i32(sc.spike_node), f64(sc.threshold)
+    s.n_mech, s.mechs = len(sc.mechs), mechs
+    s.n_netcon = len(sc.netcon_src)
+    s.nc_src, s.nc_syn, s.nc_w, s.nc_delay = (i32(sc.netcon_src), i32(sc.netcon_syn),
+                                              f64(sc.netcon_w), f64(sc.netcon_delay))
+    s.n_ev = len(sc.ev_syn)
+    s.ev_syn, s.ev_t, s.ev_w = i32(sc.ev_syn), f64(sc.ev_t), f64(sc.ev_w)
+    s.n_stim = len(sc.stim_node)
+    s.stim_node, s.stim_del, s.stim_dur, s.stim_amp = (i32(sc.stim_node), f64(sc.stim_del),
+                                                       f64(sc.stim_dur), f64(sc.stim_amp))
+    s.n_rec, s.rec_node = len(sc.rec_node), i32(sc.rec_node)
+    return s
+
+
+def adjoint(sc, nsteps, target, seg=200, nthreads=None):
+    """Oracle adjoint of J = sum over recorded nodes, steps 1..nsteps of
+    (v - target)^2.  target: [n_rec, nsteps+1].  Returns (J, dJ/dgnabar per HH
+    instance, dJ/dgkbar per HH instance, dJ/dg per pas instance)."""
+    keep = []
+    s = _marshal(sc, keep)
+    tg = np.ascontiguousarray(target, np.float64)
+    assert tg.shape == (len(sc.rec_node), nsteps + 1)
+    nh = sc.mech("hh").n if sc.mech("hh") is not None else 0
+    npas = sc.mech("pas").n if sc.mech("pas") is not None else 0
+    gna, gk, gp = np.zeros(max(nh, 1)), np.zeros(max(nh, 1)), np.zeros(max(npas, 1))
+    J = C.c_double()
+    err = C.create_string_buffer(256)
+    if nthreads is None:
+        nthreads = os.cpu_count() or 1
+    rc = lib().or_adjoint(C.byref(s), int(nsteps), _p(tg, _P_F64), int(seg), int(nthreads), C.byref(J),
+                          _p(gna, _P_F64), _p(gk, _P_F64), _p(gp, _P_F64), err, 256)
+    if rc != 0:
+        raise ValueError("oracle adjoint failed: " + err.value.decode())
+    return J.value, gna[:nh], gk[:nh], gp[:npas]
 
 
 class OracleModel:

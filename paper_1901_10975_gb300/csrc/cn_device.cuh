@@ -38,13 +38,6 @@ constexpr int32_t kNoSlot = 0xffff;
 constexpr int32_t kFarBit = 1 << 16;
 constexpr int kNFarShift = 17;
 
-// Row pairs kept in flight by the cp.async rings: elimination streams five
-// FP64 arrays and the flags and spends ~10 FP64 instructions per row, back
-// substitution streams two arrays and the flags and spends one, so it needs
-// a deeper ring to cover the same memory latency.  The two rings share memory.
-constexpr int kRingPairs = 4;
-constexpr int kBackPairs = 16;
-
 // Plain-old-data view of a model's device buffers, passed by value.
 struct DevModel {
   int32_t n_groups, n_slots, n_cells, D, n_rec;
@@ -129,22 +122,33 @@ struct DevModel {
   int32_t* status;
 };
 
-// Dynamic shared memory of one interval-kernel block (one warp).
+// Rows kept in flight by the per-lane cp.async rings.  Elimination streams
+// five FP64 arrays and the flags and spends ~10 FP64 instructions per row;
+// back substitution streams two arrays and the flags and spends one, so its
+// ring is deeper.  Each lane copies and reads only its own elements, so the
+// rings need no warp synchronisation.  The two rings share memory.
+constexpr int kElimRows = 8;
+constexpr int kBackRows = 24;
+
 __host__ __device__ inline size_t ring_bytes() {
-  const size_t elim = (size_t)2 * kRingPairs * kLanes * (5 * sizeof(double) + sizeof(int32_t));
-  const size_t back = (size_t)2 * kBackPairs * kLanes * (2 * sizeof(double) + sizeof(int32_t));
-  return elim > back ? elim : back;
+  const size_t elim = (size_t)kElimRows * kLanes * (5 * sizeof(double) + sizeof(int32_t));
+  const size_t back = (size_t)kBackRows * kLanes * (2 * sizeof(double) + sizeof(int32_t));
+  return ((elim > back ? elim : back) + 15) / 16 * 16;
 }
 __host__ __device__ inline size_t interval_smem_bytes(int stack_depth, int max_slots) {
   return ring_bytes() + (size_t)stack_depth * kLanes * 3 * sizeof(double) +
          (size_t)max_slots * kLanes * 2 * sizeof(double);
 }
 
-// 16-byte asynchronous global->shared copy (through L1, so a warp's own
-// earlier global stores are observed), and its group bookkeeping.
-__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+// Per-thread asynchronous global->shared copies (through L1, so a lane's own
+// earlier global stores are observed) and their group bookkeeping.
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem_src) : "memory");
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gmem_src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem_src) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>

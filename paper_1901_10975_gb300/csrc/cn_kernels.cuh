@@ -218,42 +218,48 @@ __global__ void k_pull_events(DevModel M, int64_t J) {
 // Backward Euler with the gates frozen over a step makes every current linear
 // in v, so this is exactly the paper's linearised update
 // (C + G + L) dv = -I(v_k) - L v_k written for v_{k+1} instead of dv.
-// Row data streams through a shared-memory ring fed by cp.async, two rows per
-// copy instruction, kRingPairs pairs ahead; parents come from a register
+// Row data streams through a per-lane shared-memory ring fed by cp.async, each
+// lane copying its own elements kElimRows rows ahead; parents come from a register
 // carry (previous row) or the per-lane far stack.
 template <int PREC>
 __global__ void __launch_bounds__(32) k_interval(DevModel M, int64_t J, int s_begin, int s_end) {
   using S = typename GateT<PREC>::S;
   using T = typename GateT<PREC>::M;
   extern __shared__ __align__(16) unsigned char smem[];
-  constexpr int KR = 2 * kRingPairs;  // ring rows
   const int g = blockIdx.x;
   if (g >= M.n_groups) return;
   const int lane = threadIdx.x;
   const int slot = g * kLanes + lane;
   const int N = M.s_rows[slot];
   const int R = M.g_rows[g];
-  const int PT = R / 2 - 1;                       // top row pair
-  const int64_t gb = M.g_node_base[g];
-  const int64_t nb = gb + lane;
+  const int64_t nb = M.g_node_base[g] + lane;
   const int gid = M.s_gid[slot];
   const int DS = M.stack_depth;
 
-  double* r_v = reinterpret_cast<double*>(smem);  // elimination ring, [KR][32] each
-  double* r_ge = r_v + KR * kLanes;
-  double* r_d0 = r_ge + KR * kLanes;
-  double* r_a = r_d0 + KR * kLanes;
-  double* r_b = r_a + KR * kLanes;
-  int32_t* r_fl = reinterpret_cast<int32_t*>(r_b + KR * kLanes);
-  constexpr int KB = 2 * kBackPairs;               // back-substitution ring, same memory
-  double* q_x = reinterpret_cast<double*>(smem);
-  double* q_bp = q_x + KB * kLanes;
-  int32_t* q_fl = reinterpret_cast<int32_t*>(q_bp + KB * kLanes);
-  double* st_a = reinterpret_cast<double*>(smem + ring_bytes());  // far stack, [DS][32] each
-  double* st_x = st_a + DS * kLanes;
-  double* st_y = st_x + DS * kLanes;
-  double* sl_ge = st_y + DS * kLanes;             // [max_slots][32]
-  double* sl_d = sl_ge + M.max_slots * kLanes;
+  // elimination ring [array][kElimRows][32]; back-substitution ring shares it
+  double* const e_v = reinterpret_cast<double*>(smem) + lane;
+  double* const e_ge = e_v + kElimRows * kLanes;
+  double* const e_d0 = e_ge + kElimRows * kLanes;
+  double* const e_a = e_d0 + kElimRows * kLanes;
+  double* const e_b = e_a + kElimRows * kLanes;
+  int32_t* const e_fl = reinterpret_cast<int32_t*>(reinterpret_cast<double*>(smem) + 5 * kElimRows * kLanes) + lane;
+  double* const b_x = reinterpret_cast<double*>(smem) + lane;
+  double* const b_bp = b_x + kBackRows * kLanes;
+  int32_t* const b_fl = reinterpret_cast<int32_t*>(reinterpret_cast<double*>(smem) + 2 * kBackRows * kLanes) + lane;
+  double* const st_a = reinterpret_cast<double*>(smem + ring_bytes()) + lane;  // far stack [DS][32] each
+  double* const st_x = st_a + DS * kLanes;
+  double* const st_y = st_x + DS * kLanes;
+  double* const sl_ge = st_y + DS * kLanes;  // slot buffer [max_slots][32]
+  double* const sl_d = sl_ge + M.max_slots * kLanes;
+
+  // this lane's column of every per-row array
+  double* const gv = M.v + nb;
+  double* const gbp = M.bp + nb;
+  const double* const gge = M.ge + nb;
+  const double* const gd0 = M.d0 + nb;
+  const double* const ga = M.a + nb;
+  const double* const gb = M.b + nb;
+  const int32_t* const gfl = M.flags + nb;
 
   const int SLR = M.g_slot_rows[g], nslot = M.s_nslot[slot];
   const int64_t slb = M.g_slot_base[g] + lane;
@@ -278,29 +284,25 @@ __global__ void __launch_bounds__(32) k_interval(DevModel M, int64_t J, int s_be
   S* const gm = static_cast<S*>(M.hh_m);
   S* const gh = static_cast<S*>(M.hh_h);
   S* const gn = static_cast<S*>(M.hh_n);
-  // copy roles: lanes 0-15 move row 2P, lanes 16-31 row 2P+1, 16 bytes each
-  const int half = lane >> 4, chunk = lane & 15;
 
-  auto prefetch_elim = [&](int P) {
-    if (P >= 0) {
-      const int rr = ((P % kRingPairs) * 2 + half) * kLanes;
-      const int64_t src = gb + (int64_t)(2 * P + half) * kLanes + 2 * chunk;
-      cp_async16(r_v + rr + 2 * chunk, M.v + src);
-      cp_async16(r_ge + rr + 2 * chunk, M.ge + src);
-      cp_async16(r_d0 + rr + 2 * chunk, M.d0 + src);
-      cp_async16(r_a + rr + 2 * chunk, M.a + src);
-      cp_async16(r_b + rr + 2 * chunk, M.b + src);
-      if (chunk < 8) cp_async16(r_fl + rr + 4 * chunk, M.flags + gb + (int64_t)(2 * P + half) * kLanes + 4 * chunk);
+  auto fetch_elim = [&](int j, int u) {  // row j into ring row u (a no-op group past the root)
+    if (j >= 0) {
+      const int64_t o = (int64_t)j * kLanes;
+      cp_async8(e_v + u * kLanes, gv + o);
+      cp_async8(e_ge + u * kLanes, gge + o);
+      cp_async8(e_d0 + u * kLanes, gd0 + o);
+      cp_async8(e_a + u * kLanes, ga + o);
+      cp_async8(e_b + u * kLanes, gb + o);
+      cp_async4(e_fl + u * kLanes, gfl + o);
     }
     cp_async_commit();
   };
-  auto prefetch_back = [&](int P) {
-    if (P <= PT) {
-      const int rr = ((P % kBackPairs) * 2 + half) * kLanes;
-      const int64_t src = gb + (int64_t)(2 * P + half) * kLanes + 2 * chunk;
-      cp_async16(q_x + rr + 2 * chunk, M.v + src);
-      cp_async16(q_bp + rr + 2 * chunk, M.bp + src);
-      if (chunk < 8) cp_async16(q_fl + rr + 4 * chunk, M.flags + gb + (int64_t)(2 * P + half) * kLanes + 4 * chunk);
+  auto fetch_back = [&](int j, int u) {
+    if (j < R) {
+      const int64_t o = (int64_t)j * kLanes;
+      cp_async8(b_x + u * kLanes, gv + o);
+      cp_async8(b_bp + u * kLanes, gbp + o);
+      cp_async4(b_fl + u * kLanes, gfl + o);
     }
     cp_async_commit();
   };
@@ -310,15 +312,16 @@ __global__ void __launch_bounds__(32) k_interval(DevModel M, int64_t J, int s_be
   for (int t = 0; t < SLR; ++t) {
     if (t < nslot) {
       const int64_t i = slb + (int64_t)t * kLanes;
-      sl_ge[t * kLanes + lane] = M.slot_ge0[i];
-      sl_d[t * kLanes + lane] = M.slot_d00[i];
+      sl_ge[t * kLanes] = M.slot_ge0[i];
+      sl_d[t * kLanes] = M.slot_d00[i];
     }
   }
 
   for (int s = s_begin; s < s_end; ++s) {
     const int64_t k = T0 + s;
     // start streaming the top rows while the mechanisms are evaluated
-    for (int i = 0; i < kRingPairs; ++i) prefetch_elim(PT - i);
+#pragma unroll
+    for (int u = 0; u < kElimRows; ++u) fetch_elim(R - 1 - u, u);
     // (1) event delivery
     while (ei < ne && ev[ei].step == s) {
       M.syn_g[sb + (int64_t)ev[ei].syn * kLanes] += ev[ei].w;
@@ -347,7 +350,7 @@ __global__ void __launch_bounds__(32) k_interval(DevModel M, int64_t J, int s_be
         const int q = q0 + u;
         if (q < nsyn) {
           const double G = gs[u] * ss[u];
-          const int t = st[u] * kLanes + lane;
+          const int t = st[u] * kLanes;
           sl_ge[t] = fma(G, se[u], sl_ge[t]);
           sl_d[t] += G;
           M.syn_g[sb + (int64_t)q * kLanes] = gs[u] * sd[u];  // ExpSyn state update: v-independent
@@ -361,7 +364,7 @@ __global__ void __launch_bounds__(32) k_interval(DevModel M, int64_t J, int s_be
         const double gna = M.hh_p[i] * (m * m * m * h);
         const double gk = M.hh_p[M.hh_elems + i] * ((n * n) * (n * n));
         const double gl = M.hh_p[2 * M.hh_elems + i];
-        const int t = M.hh_slot[i] * kLanes + lane;
+        const int t = M.hh_slot[i] * kLanes;
         sl_ge[t] += gna * M.hh_p[4 * M.hh_elems + i] + gk * M.hh_p[5 * M.hh_elems + i] +
                     gl * M.hh_p[3 * M.hh_elems + i];
         sl_d[t] += gna + gk + gl;
@@ -372,103 +375,99 @@ __global__ void __launch_bounds__(32) k_interval(DevModel M, int64_t J, int s_be
       for (int q = 0; q < STR; ++q) {
         if (q < nst) {
           const int64_t i = stb + (int64_t)q * kLanes;
-          if (M.st_del[i] <= tmid && tmid < M.st_del[i] + M.st_dur[i]) sl_ge[M.st_slot[i] * kLanes + lane] += M.st_amp[i];
+          if (M.st_del[i] <= tmid && tmid < M.st_del[i] + M.st_dur[i]) sl_ge[M.st_slot[i] * kLanes] += M.st_amp[i];
         }
       }
     }
     // (3) elimination, leaves to root.  Branch-free per row: a far child
     //     pushes its raw (-a, x, b/d) onto the lane's stack and its parent
-    //     pops it into two FMAs (with zero coefficients on rows that pop
+    //     pops it into two FMAs (zero coefficients on rows that pop
     //     nothing); the previous row's carry enters the same way.
     double ca = 0.0, cx = 0.0, cb = 0.0, x = 0.0;
     int top = 0;
-    for (int P = PT; P >= 0; --P) {
-      cp_async_wait<kRingPairs - 1>();
-      __syncwarp();
-      const int rb = (P & (kRingPairs - 1)) * 2 * kLanes + lane;
+    for (int jb = R - 1; jb >= 0; jb -= kElimRows) {
 #pragma unroll
-      for (int h = 1; h >= 0; --h) {
-        const int j = 2 * P + h;
-        const int rr = rb + h * kLanes;
-        const int f = r_fl[rr];
-        const int sl = f & kNoSlot;
-        const bool hs = sl != kNoSlot;
-        const int si = (hs ? sl : 0) * kLanes + lane;
-        const double g0 = r_ge[rr], d00 = r_d0[rr];
-        const double sg = sl_ge[si], sd = sl_d[si];
-        if (hs) {
-          sl_ge[si] = g0;  // re-seed the slot for the next step
-          sl_d[si] = d00;
+      for (int u = 0; u < kElimRows; ++u) {
+        const int j = jb - u;
+        cp_async_wait<kElimRows - 1>();
+        if (j >= 0) {
+          const int ro = u * kLanes;
+          const int f = e_fl[ro];
+          const int sl = f & kNoSlot;
+          const bool hs = sl != kNoSlot;
+          const int si = (hs ? sl : 0) * kLanes;
+          const double g0 = e_ge[ro], d00 = e_d0[ro];
+          const double sg = sl_ge[si], sd = sl_d[si];
+          if (hs) {
+            sl_ge[si] = g0;  // re-seed the slot for the next step
+            sl_d[si] = d00;
+          }
+          const int np = f >> kNFarShift;
+          const int tp = np > 0 ? top - 1 : top;
+          const int ti = (tp < DS ? tp : DS - 1) * kLanes;
+          // stale stack words must not reach the FMAs (0 * NaN is NaN): select
+          const double fa = np > 0 ? st_a[ti] : 0.0;
+          const double fx = np > 0 ? st_x[ti] : 0.0;
+          const double fb = np > 0 ? st_y[ti] : 0.0;
+          top = tp;
+          double rhs = fma(fa, fx, e_v[ro] + (hs ? sg : g0));
+          double d = fma(fa, fb, hs ? sd : d00);
+          for (int q = 1; q < np; ++q) {  // third and further children (rare)
+            --top;
+            rhs = fma(st_a[top * kLanes], st_x[top * kLanes], rhs);
+            d = fma(st_a[top * kLanes], st_y[top * kLanes], d);
+          }
+          rhs = fma(ca, cx, rhs);
+          d = fma(ca, cb, d);
+          const double r = rcp64(d);
+          x = rhs * r;
+          const double bp = e_b[ro] * r;
+          gv[(int64_t)j * kLanes] = x;
+          gbp[(int64_t)j * kLanes] = bp;
+          const double na = -e_a[ro];
+          const bool far = (f & kFarBit) != 0;
+          if (far) {
+            st_a[top * kLanes] = na;
+            st_x[top * kLanes] = x;
+            st_y[top * kLanes] = bp;
+          }
+          top += far ? 1 : 0;
+          ca = far ? 0.0 : na;
+          cx = x;
+          cb = bp;
         }
-        const int np = f >> kNFarShift;
-        const int tp = np > 0 ? top - 1 : top;
-        const int ti = (tp < DS ? tp : DS - 1) * kLanes + lane;
-        // stale stack words must not reach the FMAs (0 * NaN is NaN): select
-        const double fa = np > 0 ? st_a[ti] : 0.0;
-        const double fx = np > 0 ? st_x[ti] : 0.0;
-        const double fb = np > 0 ? st_y[ti] : 0.0;
-        top = tp;
-        double rhs = fma(fa, fx, r_v[rr] + (hs ? sg : g0));
-        double d = fma(fa, fb, hs ? sd : d00);
-        for (int q = 1; q < np; ++q) {  // third and further children (rare)
-          --top;
-          rhs = fma(st_a[top * kLanes + lane], st_x[top * kLanes + lane], rhs);
-          d = fma(st_a[top * kLanes + lane], st_y[top * kLanes + lane], d);
-        }
-        rhs = fma(ca, cx, rhs);
-        d = fma(ca, cb, d);
-        const double r = rcp64(d);
-        x = rhs * r;
-        const double bp = r_b[rr] * r;
-        const int64_t gi = nb + (int64_t)j * kLanes;
-        M.v[gi] = x;
-        M.bp[gi] = bp;
-        const double na = -r_a[rr];
-        const bool far = (f & kFarBit) != 0;
-        if (far) {
-          st_a[top * kLanes + lane] = na;
-          st_x[top * kLanes + lane] = x;
-          st_y[top * kLanes + lane] = bp;
-        }
-        top += far ? 1 : 0;
-        ca = far ? 0.0 : na;
-        cx = x;
-        cb = bp;
+        fetch_elim(j - kElimRows, u);
       }
-      __syncwarp();
-      prefetch_elim(P - kRingPairs);
     }
     const double x0 = x;  // row 0 is eliminated last
     cp_async_wait<0>();
-    __syncwarp();  // every lane's elimination stores precede the copies below
     // back substitution, root to leaves (row 0: b = 0, so v_0 = x_0)
-    for (int i = 0; i < kBackPairs; ++i) prefetch_back(i);
-    double vprev = 0.0;
-    for (int P = 0; P <= PT; ++P) {
-      cp_async_wait<kBackPairs - 1>();
-      __syncwarp();
-      const int rb = (P & (kBackPairs - 1)) * 2 * kLanes + lane;
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int j = 2 * P + h;
-        const int rr = rb + h * kLanes;
-        const int f = q_fl[rr];
-        const bool far = (f & kFarBit) != 0;
-        const int tp = far ? top - 1 : top;
-        const double pv = st_x[(tp < DS ? tp : DS - 1) * kLanes + lane];
-        const double vj = fma(-q_bp[rr], far ? pv : vprev, q_x[rr]);
-        M.v[nb + (int64_t)j * kLanes] = vj;
-        const int np = f >> kNFarShift;
-        if (np > 0) st_x[tp * kLanes + lane] = vj;
-        for (int q = 1; q < np; ++q) st_x[(tp + q) * kLanes + lane] = vj;
-        top = tp + np;
-        vprev = vj;
+    for (int u = 0; u < kBackRows; ++u) fetch_back(u, u);
+    double vprev = 0.0;
+    for (int jb = 0; jb < R; jb += kBackRows) {
+#pragma unroll
+      for (int u = 0; u < kBackRows; ++u) {
+        const int j = jb + u;
+        cp_async_wait<kBackRows - 1>();
+        if (j < R) {
+          const int ro = u * kLanes;
+          const int f = b_fl[ro];
+          const bool far = (f & kFarBit) != 0;
+          const int tp = far ? top - 1 : top;
+          const double pv = st_x[(tp < DS ? tp : DS - 1) * kLanes];
+          const double vj = fma(-b_bp[ro], far ? pv : vprev, b_x[ro]);
+          gv[(int64_t)j * kLanes] = vj;
+          const int np = f >> kNFarShift;
+          if (np > 0) st_x[tp * kLanes] = vj;
+          for (int q = 1; q < np; ++q) st_x[(tp + q) * kLanes] = vj;
+          top = tp + np;
+          vprev = vj;
+        }
+        fetch_back(j + kBackRows, u);
       }
-      __syncwarp();
-      prefetch_back(P + kBackPairs);
     }
     cp_async_wait<0>();
-    __syncwarp();
     // (4) nrn_state: HH gates (cnexp) at v_{k+1}
     for (int q = 0; q < HR; ++q) {
       if (q < nhh) {
@@ -497,7 +496,6 @@ __global__ void __launch_bounds__(32) k_interval(DevModel M, int64_t J, int s_be
         }
       }
     }
-    __syncwarp();  // back-substitution stores precede the next step's copies
   }
   if (gid >= 0) {
     M.hist[J * M.n_cells + gid] = mask;
