@@ -204,6 +204,40 @@ int64_t cn_updates(const cn_model* m);
 /* Diagnostics of the last cn_run: kernel launches issued.                  */
 int64_t cn_launch_count(const cn_model* m);
 
+/* Return to step 0: v = v_init, gates at steady state, synaptic g = 0,
+ * external-event cursors rewound, spike raster and traces cleared.
+ * Parameters set with cn_set_cell_param are kept.                          */
+cn_status cn_reset(cn_model* m);
+
+/* Per-cell maximal conductances (the adjoint's parameters): */
+typedef enum {
+  CN_PARAM_GNABAR = 0,  /* gnabar of every HH instance of the cell (S/cm2) */
+  CN_PARAM_GKBAR = 1,   /* gkbar of every HH instance of the cell (S/cm2)  */
+  CN_PARAM_GPAS = 2     /* g of every pas instance of the cell (S/cm2)     */
+} cn_cell_param;
+
+/* Set / read one per-cell parameter, values[n_cells] in gid order.  A set
+ * takes effect from the next step.                                        */
+cn_status cn_set_cell_param(cn_model* m, int32_t param, const double* values);
+cn_status cn_get_cell_param(cn_model* m, int32_t param, double* values);
+
+/* Prepare the discrete adjoint of the FP64 run (the benchmark spec's
+ * differentiation pattern; the paper has no adjoint): from step 0, cn_run
+ * stores the state (v, HH gates, synaptic g) every checkpoint_steps steps.
+ * Needs FP64, no NetCons, no external events, at most one HH instance per
+ * cell.  Errors: CN_ESTATE, CN_EINVAL.                                     */
+cn_status cn_enable_adjoint(cn_model* m, int32_t checkpoint_steps);
+
+/* Gradient of a loss J(traces) with respect to the per-cell parameters
+ * above, by the discrete adjoint of the run from step 0 to the current step
+ * K: dJ_dtrace is [n_rec][K+1] (host, the derivative of J with respect to
+ * every recorded voltage); grad is [3][n_cells] (host; CN_PARAM order).  The
+ * reverse pass walks the checkpoint segments backwards, recomputing each
+ * segment's trajectory with the forward kernel, and solves the transposed
+ * tree system of every step (Hines with the couplings swapped) plus the HH
+ * gate sensitivities.  The model's state is left at step K.               */
+cn_status cn_run_adjoint(cn_model* m, const double* dJ_dtrace, double* grad);
+
 /* Kernel timing (diagnostics): while enabled, cn_run brackets every
  * interval-kernel and spike-pull launch with CUDA events on the model's
  * stream.  cn_profile_read synchronizes, returns the summed device time (ms)

@@ -15,6 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libcn.so")
 
 CN_OK, CN_EINVAL, CN_ENOMEM, CN_ECUDA, CN_ESTATE, CN_ETIMEOUT, CN_ERANGE = range(7)
+CN_PARAM_GNABAR, CN_PARAM_GKBAR, CN_PARAM_GPAS = range(3)
 STATUS_NAMES = {0: "CN_OK", 1: "CN_EINVAL", 2: "CN_ENOMEM", 3: "CN_ECUDA", 4: "CN_ESTATE",
                 5: "CN_ETIMEOUT", 6: "CN_ERANGE"}
 MECH = {"pas": 0, "hh": 1, "expsyn": 2, "na3h": 3, "kdr4": 4, "ka": 5, "ih": 6, "cahva": 7, "kca": 8}
@@ -97,6 +98,16 @@ def lib():
         L.cn_get_v.restype = st
         L.cn_get_state.argtypes = [C.c_void_p, C.c_int32, C.c_int32, _P_F64, C.c_size_t]
         L.cn_get_state.restype = st
+        L.cn_reset.argtypes = [C.c_void_p]
+        L.cn_reset.restype = st
+        L.cn_set_cell_param.argtypes = [C.c_void_p, C.c_int32, _P_F64]
+        L.cn_set_cell_param.restype = st
+        L.cn_get_cell_param.argtypes = [C.c_void_p, C.c_int32, _P_F64]
+        L.cn_get_cell_param.restype = st
+        L.cn_enable_adjoint.argtypes = [C.c_void_p, C.c_int32]
+        L.cn_enable_adjoint.restype = st
+        L.cn_run_adjoint.argtypes = [C.c_void_p, _P_F64, _P_F64]
+        L.cn_run_adjoint.restype = st
         L.cn_profile.argtypes = [C.c_void_p, C.c_int32]
         L.cn_profile.restype = st
         L.cn_profile_read.argtypes = [C.c_void_p, _P_F64, _P_I64, _P_F64, _P_I64]
@@ -287,6 +298,29 @@ class Model:
     @property
     def launches(self) -> int:
         return int(lib().cn_launch_count(self._h))
+
+    def cn_reset(self):
+        _check(lib().cn_reset(self._h), self._h)
+
+    def cn_set_cell_param(self, param, values):
+        v = _f64(values)
+        assert v.shape == (self.n_cells,)
+        _check(lib().cn_set_cell_param(self._h, int(param), _p(v, _P_F64)), self._h)
+
+    def cn_get_cell_param(self, param):
+        out = np.empty(self.n_cells)
+        _check(lib().cn_get_cell_param(self._h, int(param), _p(out, _P_F64)), self._h)
+        return out
+
+    def cn_enable_adjoint(self, checkpoint_steps):
+        _check(lib().cn_enable_adjoint(self._h, int(checkpoint_steps)), self._h)
+
+    def cn_run_adjoint(self, dj_dtrace):
+        """dj_dtrace: [n_rec, K+1]; returns the gradient [3, n_cells]."""
+        dj = _f64(dj_dtrace)
+        out = np.empty((3, self.n_cells))
+        _check(lib().cn_run_adjoint(self._h, _p(dj, _P_F64), _p(out, _P_F64)), self._h)
+        return out
 
     def cn_profile(self, enable=True):
         _check(lib().cn_profile(self._h, int(bool(enable))), self._h)

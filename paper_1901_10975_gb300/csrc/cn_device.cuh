@@ -36,12 +36,15 @@ struct EvRec {
 // bit (the parent is not the previous row), count of far children.
 constexpr int32_t kNoSlot = 0xffff;
 constexpr int32_t kFarBit = 1 << 16;
-constexpr int kNFarShift = 17;
+constexpr int kNFarShift = 17;      // 4 bits: far children of the row
+constexpr int32_t kNFarMask = 15;
+constexpr int32_t kHasPasBit = 1 << 21;
 
 // Plain-old-data view of a model's device buffers, passed by value.
 struct DevModel {
   int32_t n_groups, n_slots, n_cells, D, n_rec;
   int32_t max_slots, stack_depth;
+  int64_t node_elems;
   double dt;
   // per group
   const int64_t* g_node_base;  // element index of row 0, lane 0 (multiple of 64)
@@ -92,7 +95,17 @@ struct DevModel {
   void* hh_h;
   void* hh_n;
   const double* hh_p;       // [6][hh_elems]: gnabar/cdt gkbar/cdt gl/cdt el ena ek
+  double* hh_raw;           // [6][hh_elems]: the same, unscaled
   int64_t hh_elems;
+  // pas and row scaling, kept to rebuild d0/ge when parameters change
+  double* pas_g;            // per row (0 without pas)
+  double* pas_e;            // per row
+  double* cdt;              // per row: 1e-3 cm/dt
+  double* dax;              // per row: axial part of the unscaled diagonal
+  // adjoint trajectory (recompute only)
+  double* traj_v;           // [step - traj_k0][node_elems]
+  double* traj_g;           // [step - traj_k0][3][hh_elems]
+  int64_t traj_k0;
   // stimuli
   const int32_t* st_slot;
   const double* st_del;

@@ -48,6 +48,11 @@ struct cn_model {
   std::vector<int32_t> node_cell;
   std::vector<int32_t> node_row;   // global node -> row inside its cell
   size_t smem_bytes = 0;
+  std::vector<int64_t> x_pos0;     // initial external-event cursors
+  // adjoint checkpoints: state at steps 0, S, 2S, ...
+  int32_t ck_steps = 0;
+  std::vector<void*> ck_buf;
+  size_t ck_bytes = 0;
 
   // ---- layout
   bool finalized = false;
@@ -175,6 +180,18 @@ cn_status launch_checked(cn_model* m, F&& f) {
   m->launches++;
   CN_TRY_CUDA(m, cudaGetLastError());
   return CN_OK;
+}
+
+cn_status state_init(cn_model* m) {
+  const int tb = 128, nb = (m->n_slots + tb - 1) / tb;
+  cn::DevModel dm = m->dm;
+  cudaStream_t st = m->stream;
+  double v0 = m->opt.v_init_mV;
+  switch (m->opt.precision) {
+    case CN_PREC_FP64: return launch_checked(m, [&] { cn::k_state_init<0><<<nb, tb, 0, st>>>(dm, v0); });
+    case CN_PREC_GATE_FP32: return launch_checked(m, [&] { cn::k_state_init<1><<<nb, tb, 0, st>>>(dm, v0); });
+    default: return launch_checked(m, [&] { cn::k_state_init<2><<<nb, tb, 0, st>>>(dm, v0); });
+  }
 }
 
 // Depth-first preorder of one cell that visits the smaller child subtree
@@ -348,6 +365,7 @@ cn_status finalize(cn_model* m) {
     int64_t e = node_elem(m->pas_node[q]);
     h_gp[e] = m->pas_g[q];
     h_ep[e] = m->pas_e[q];
+    h_flags[e] |= cn::kHasPasBit;
   }
   // slot rows, interleaved
   std::vector<int32_t> slot_n(m->n_slots, 0), g_slot_rows(m->n_groups, 0);
@@ -471,6 +489,7 @@ cn_status finalize(cn_model* m) {
   dm.n_rec = (int32_t)m->rec_node.size();
   dm.max_slots = max_slots;
   dm.stack_depth = depth;
+  dm.node_elems = acc;
   dm.dt = dt;
   int64_t* p64;
   int32_t* p32;
@@ -522,8 +541,13 @@ cn_status finalize(cn_model* m) {
     CN_TRY_CUDA(m, cudaMemsetAsync(q, 0, std::max<int64_t>(rh.elems, 1) * m->gate_bytes, m->stream));
     *gp = q;
   }
-  CN_CHECK(upload(m, &pd, h_hh_p)); dm.hh_p = pd;
+  CN_CHECK(zeros(m, &pd, 6 * std::max<int64_t>(rh.elems, 1))); dm.hh_p = pd;
+  CN_CHECK(upload(m, &pd, h_hh_p, 6)); dm.hh_raw = pd;
   dm.hh_elems = rh.elems;
+  CN_CHECK(upload(m, &pd, h_gp)); dm.pas_g = pd;
+  CN_CHECK(upload(m, &pd, h_ep)); dm.pas_e = pd;
+  CN_CHECK(zeros(m, &pd, acc)); dm.cdt = pd;
+  CN_CHECK(zeros(m, &pd, acc)); dm.dax = pd;
   CN_CHECK(upload(m, &p32, h_st_slot)); dm.st_slot = p32;
   CN_CHECK(upload(m, &pd, h_st_del)); dm.st_del = pd;
   CN_CHECK(upload(m, &pd, h_st_dur)); dm.st_dur = pd;
@@ -550,40 +574,33 @@ cn_status finalize(cn_model* m) {
   dm.trace = nullptr;
 
   // temporaries for the setup kernels
-  double *d_area, *d_ri, *d_cm, *d_gp, *d_ep, *d_syn_area, *d_syn_cm, *d_syn_tau, *d_hh_cm, *d_st_amp, *d_st_area,
-      *d_st_cm;
+  double *d_area, *d_ri, *d_cm, *d_syn_area, *d_syn_cm, *d_syn_tau, *d_st_amp, *d_st_area, *d_st_cm;
   int32_t* d_prow;
   CN_CHECK(upload(m, &d_area, h_area));
   CN_CHECK(upload(m, &d_ri, h_ri));
   CN_CHECK(upload(m, &d_cm, h_cm));
-  CN_CHECK(upload(m, &d_gp, h_gp));
-  CN_CHECK(upload(m, &d_ep, h_ep));
   CN_CHECK(upload(m, &d_prow, h_prow));
   CN_CHECK(upload(m, &d_syn_area, h_syn_area));
   CN_CHECK(upload(m, &d_syn_cm, h_syn_cm));
   CN_CHECK(upload(m, &d_syn_tau, h_syn_tau));
-  CN_CHECK(upload(m, &d_hh_cm, h_hh_cm));
   CN_CHECK(upload(m, &d_st_amp, h_st_amp));
   CN_CHECK(upload(m, &d_st_area, h_st_area));
   CN_CHECK(upload(m, &d_st_cm, h_st_cm));
   const int tb = 128, nb = (m->n_slots + tb - 1) / tb;
   cudaStream_t st = m->stream;
-  double v0 = m->opt.v_init_mV;
-  CN_CHECK(launch_checked(m, [&] { cn::k_setup_nodes<<<nb, tb, 0, st>>>(dm, d_area, d_ri, d_cm, d_gp, d_ep, d_prow, v0); }));
+  CN_CHECK(launch_checked(m, [&] { cn::k_setup_nodes<<<nb, tb, 0, st>>>(dm, d_area, d_ri, d_cm, d_prow); }));
+  CN_CHECK(launch_checked(m, [&] { cn::k_pas_apply<<<nb, tb, 0, st>>>(dm); }));
   CN_CHECK(launch_checked(m, [&] { cn::k_setup_slots<<<nb, tb, 0, st>>>(dm); }));
   CN_CHECK(launch_checked(m, [&] { cn::k_setup_syn<<<nb, tb, 0, st>>>(dm, d_syn_area, d_syn_cm, d_syn_tau); }));
-  switch (m->opt.precision) {
-    case CN_PREC_FP64: CN_CHECK(launch_checked(m, [&] { cn::k_setup_hh<0><<<nb, tb, 0, st>>>(dm, d_hh_cm, v0); })); break;
-    case CN_PREC_GATE_FP32: CN_CHECK(launch_checked(m, [&] { cn::k_setup_hh<1><<<nb, tb, 0, st>>>(dm, d_hh_cm, v0); })); break;
-    default: CN_CHECK(launch_checked(m, [&] { cn::k_setup_hh<2><<<nb, tb, 0, st>>>(dm, d_hh_cm, v0); })); break;
-  }
+  CN_CHECK(launch_checked(m, [&] { cn::k_hh_params<<<nb, tb, 0, st>>>(dm); }));
   CN_CHECK(launch_checked(m, [&] { cn::k_setup_stim<<<nb, tb, 0, st>>>(dm, d_st_amp, d_st_area, d_st_cm); }));
-  CN_CHECK(launch_checked(m, [&] { cn::k_init_above<<<nb, tb, 0, st>>>(dm); }));
+  CN_CHECK(state_init(m));
   CN_TRY_CUDA(m, cudaStreamSynchronize(st));
-  for (double* p : {d_area, d_ri, d_cm, d_gp, d_ep, d_syn_area, d_syn_cm, d_syn_tau, d_hh_cm, d_st_amp, d_st_area, d_st_cm})
-    dfree_raw(m, p);
+  for (double* p : {d_area, d_ri, d_cm, d_syn_area, d_syn_cm, d_syn_tau, d_st_amp, d_st_area, d_st_cm}) dfree_raw(m, p);
   dfree_raw(m, d_prow);
-  for (auto fn : {(const void*)cn::k_interval<0>, (const void*)cn::k_interval<1>, (const void*)cn::k_interval<2>})
+  m->x_pos0 = x_pos;
+  for (auto fn : {(const void*)cn::k_interval<0, false>, (const void*)cn::k_interval<1, false>,
+                  (const void*)cn::k_interval<2, false>, (const void*)cn::k_interval<0, true>})
     CN_TRY_CUDA(m, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m->smem_bytes));
   m->finalized = true;
   m->cells_nodes = m->n_nodes;
@@ -665,18 +682,59 @@ cn_status launch_interval(cn_model* m, int64_t J, int s0, int s1) {
   }
   switch (m->opt.precision) {
     case CN_PREC_FP64:
-      CN_CHECK(launch_checked(m, [&] { cn::k_interval<0><<<blocks, 32 * wpb, m->smem_bytes, st>>>(dm, J, s0, s1); }));
+      CN_CHECK(launch_checked(m, [&] { cn::k_interval<0, false><<<blocks, 32 * wpb, m->smem_bytes, st>>>(dm, J, s0, s1); }));
       break;
     case CN_PREC_GATE_FP32:
-      CN_CHECK(launch_checked(m, [&] { cn::k_interval<1><<<blocks, 32 * wpb, m->smem_bytes, st>>>(dm, J, s0, s1); }));
+      CN_CHECK(launch_checked(m, [&] { cn::k_interval<1, false><<<blocks, 32 * wpb, m->smem_bytes, st>>>(dm, J, s0, s1); }));
       break;
     default:
-      CN_CHECK(launch_checked(m, [&] { cn::k_interval<2><<<blocks, 32 * wpb, m->smem_bytes, st>>>(dm, J, s0, s1); }));
+      CN_CHECK(launch_checked(m, [&] { cn::k_interval<2, false><<<blocks, 32 * wpb, m->smem_bytes, st>>>(dm, J, s0, s1); }));
       break;
   }
   if (m->profiling) {
     CN_TRY_CUDA(m, cudaEventRecord(e1, st));
     m->ev_interval.emplace_back(e0, e1);
+  }
+  return CN_OK;
+}
+
+
+// State snapshot (v, HH gates, synaptic g) into / out of a device buffer.
+size_t snapshot_bytes(const cn_model* m) {
+  return (size_t)m->node_elems * 8 + 3 * (size_t)std::max<int64_t>(m->hh_elems, 1) * m->gate_bytes +
+         (size_t)std::max<int64_t>(m->syn_elems, 1) * 8;
+}
+
+cn_status snapshot(cn_model* m, void* buf, bool save) {
+  char* p = static_cast<char*>(buf);
+  const size_t nv = (size_t)m->node_elems * 8, ng = (size_t)std::max<int64_t>(m->hh_elems, 1) * m->gate_bytes,
+               ns = (size_t)std::max<int64_t>(m->syn_elems, 1) * 8;
+  void* dev[5] = {m->dm.v, m->dm.hh_m, m->dm.hh_h, m->dm.hh_n, m->dm.syn_g};
+  size_t sz[5] = {nv, ng, ng, ng, ns};
+  for (int i = 0; i < 5; ++i) {
+    if (save) CN_TRY_CUDA(m, cudaMemcpyAsync(p, dev[i], sz[i], cudaMemcpyDeviceToDevice, m->stream));
+    else CN_TRY_CUDA(m, cudaMemcpyAsync(dev[i], p, sz[i], cudaMemcpyDeviceToDevice, m->stream));
+    p += sz[i];
+  }
+  return CN_OK;
+}
+
+// Advance from the current step to K (< next interval boundary handling as
+// in cn_run), with the trajectory-recording kernel when traj is set.
+cn_status advance(cn_model* m, int64_t K, bool traj) {
+  while (m->step < K) {
+    const int64_t J = m->step / m->D;
+    const int s0 = (int)(m->step - J * m->D);
+    const int s1 = (int)std::min<int64_t>(m->D, K - J * m->D);
+    if (traj) {
+      cn::DevModel dm = m->dm;
+      CN_CHECK(launch_checked(m, [&] {
+        cn::k_interval<0, true><<<m->n_groups, 32, m->smem_bytes, m->stream>>>(dm, J, s0, s1);
+      }));
+    } else {
+      CN_CHECK(launch_interval(m, J, s0, s1));
+    }
+    m->step = J * m->D + s1;
   }
   return CN_OK;
 }
@@ -892,12 +950,20 @@ cn_status cn_run(cn_model* m, double tstop_ms) {
   CN_TRY_CUDA(m, cudaSetDevice(m->opt.device));
   if (!m->finalized) CN_CHECK(finalize(m));
   CN_CHECK(ensure_capacity(m, K));
+  if (m->ck_steps <= 0) return advance(m, K, false);
+  // with adjoint checkpoints: snapshot the state at every multiple of S
   while (m->step < K) {
-    const int64_t J = m->step / m->D;
-    const int s0 = (int)(m->step - J * m->D);
-    const int s1 = (int)std::min<int64_t>(m->D, K - J * m->D);
-    CN_CHECK(launch_interval(m, J, s0, s1));
-    m->step = J * m->D + s1;
+    const int64_t S = m->ck_steps;
+    if (m->step % S == 0) {
+      const size_t idx = (size_t)(m->step / S);
+      while (m->ck_buf.size() <= idx) {
+        void* b = dalloc_raw(m, m->ck_bytes);
+        if (!b) return m->fail(CN_ENOMEM, "checkpoint allocation failed");
+        m->ck_buf.push_back(b);
+      }
+      CN_CHECK(snapshot(m, m->ck_buf[idx], true));
+    }
+    CN_CHECK(advance(m, std::min<int64_t>(K, (m->step / S + 1) * S), false));
   }
   return CN_OK;
 }
@@ -1049,6 +1115,150 @@ cn_status cn_profile_read(cn_model* m, double* interval_ms, int64_t* interval_la
   };
   CN_CHECK(sum(m->ev_interval, interval_ms, interval_launches));
   CN_CHECK(sum(m->ev_pull, pull_ms, pull_launches));
+  return CN_OK;
+}
+
+cn_status cn_reset(cn_model* m) {
+  if (!m) return CN_EINVAL;
+  if (!m->finalized) return CN_OK;
+  CN_TRY_CUDA(m, cudaSetDevice(m->opt.device));
+  CN_CHECK(state_init(m));
+  if (!m->x_pos0.empty())
+    CN_TRY_CUDA(m, cudaMemcpyAsync(m->dm.x_pos, m->x_pos0.data(), m->x_pos0.size() * sizeof(int64_t),
+                                   cudaMemcpyHostToDevice, m->stream));
+  if (m->dm.hist) CN_TRY_CUDA(m, cudaMemsetAsync(m->dm.hist, 0, (size_t)m->hist_cap * m->n_cells * 8, m->stream));
+  CN_TRY_CUDA(m, cudaMemsetAsync(m->dm.status, 0, sizeof(int32_t), m->stream));
+  m->step = 0;
+  if (m->dm.trace) {
+    const int tb = 128, nb = (m->n_slots + tb - 1) / tb;
+    cn::DevModel dm = m->dm;
+    CN_CHECK(launch_checked(m, [&] { cn::k_record0<<<nb, tb, 0, m->stream>>>(dm, 0); }));
+  }
+  CN_TRY_CUDA(m, cudaStreamSynchronize(m->stream));
+  return CN_OK;
+}
+
+static cn_status cell_values_to_slots(cn_model* m, const double* values, double** d_out) {
+  std::vector<double> h(m->n_slots, 0.0);
+  for (int c = 0; c < m->n_cells; ++c) {
+    if (!std::isfinite(values[c])) return m->fail(CN_EINVAL, "non-finite parameter value");
+    h[m->cell_slot[c]] = values[c];
+  }
+  return upload(m, d_out, h);
+}
+
+cn_status cn_set_cell_param(cn_model* m, int32_t param, const double* values) {
+  if (!m || !values || param < 0 || param > 2) return m ? m->fail(CN_EINVAL, "bad parameter id") : CN_EINVAL;
+  CN_TRY_CUDA(m, cudaSetDevice(m->opt.device));
+  if (!m->finalized) CN_CHECK(finalize(m));
+  CN_CHECK(ensure_capacity(m, m->step));
+  double* d = nullptr;
+  CN_CHECK(cell_values_to_slots(m, values, &d));
+  const int tb = 128, nb = (m->n_slots + tb - 1) / tb;
+  cn::DevModel dm = m->dm;
+  CN_CHECK(launch_checked(m, [&] { cn::k_set_cell_param<<<nb, tb, 0, m->stream>>>(dm, param, d); }));
+  if (param < 2) CN_CHECK(launch_checked(m, [&] { cn::k_hh_params<<<nb, tb, 0, m->stream>>>(dm); }));
+  else CN_CHECK(launch_checked(m, [&] { cn::k_pas_apply<<<nb, tb, 0, m->stream>>>(dm); }));
+  CN_CHECK(launch_checked(m, [&] { cn::k_setup_slots<<<nb, tb, 0, m->stream>>>(dm); }));
+  CN_TRY_CUDA(m, cudaStreamSynchronize(m->stream));
+  dfree_raw(m, d);
+  return CN_OK;
+}
+
+cn_status cn_get_cell_param(cn_model* m, int32_t param, double* values) {
+  if (!m || !values || param < 0 || param > 2) return m ? m->fail(CN_EINVAL, "bad parameter id") : CN_EINVAL;
+  CN_TRY_CUDA(m, cudaSetDevice(m->opt.device));
+  if (!m->finalized) CN_CHECK(finalize(m));
+  double* d = nullptr;
+  CN_CHECK(zeros(m, &d, m->n_slots));
+  const int tb = 128, nb = (m->n_slots + tb - 1) / tb;
+  cn::DevModel dm = m->dm;
+  CN_CHECK(launch_checked(m, [&] { cn::k_get_cell_param<<<nb, tb, 0, m->stream>>>(dm, param, d); }));
+  std::vector<double> h(m->n_slots);
+  CN_TRY_CUDA(m, cudaMemcpyAsync(h.data(), d, h.size() * 8, cudaMemcpyDeviceToHost, m->stream));
+  CN_TRY_CUDA(m, cudaStreamSynchronize(m->stream));
+  dfree_raw(m, d);
+  for (int c = 0; c < m->n_cells; ++c) values[c] = h[m->cell_slot[c]];
+  return CN_OK;
+}
+
+cn_status cn_enable_adjoint(cn_model* m, int32_t checkpoint_steps) {
+  if (!m || checkpoint_steps < 1) return m ? m->fail(CN_EINVAL, "checkpoint interval must be >= 1 step") : CN_EINVAL;
+  if (m->step != 0) return m->fail(CN_ESTATE, "enable the adjoint at step 0");
+  if (m->opt.precision != CN_PREC_FP64) return m->fail(CN_ESTATE, "the adjoint is defined for the FP64 path");
+  if (!m->nc_src.empty() || !m->ev_syn.empty())
+    return m->fail(CN_ESTATE, "the adjoint needs a model without NetCons or external events");
+  std::vector<int> nh(m->n_cells, 0);
+  for (int32_t node : m->hh_node)
+    if (++nh[m->node_cell[node]] > 1) return m->fail(CN_EINVAL, "the adjoint supports one HH instance per cell");
+  m->ck_steps = checkpoint_steps;
+  CN_TRY_CUDA(m, cudaSetDevice(m->opt.device));
+  if (!m->finalized) CN_CHECK(finalize(m));
+  m->ck_bytes = snapshot_bytes(m);
+  return CN_OK;
+}
+
+cn_status cn_run_adjoint(cn_model* m, const double* dj, double* grad) {
+  if (!m || !dj || !grad) return CN_EINVAL;
+  if (m->ck_steps <= 0) return m->fail(CN_ESTATE, "call cn_enable_adjoint before the forward run");
+  const int64_t K = m->step;
+  if (K < 1) return m->fail(CN_ESTATE, "run forward at least one step first");
+  const int nr = m->dm.n_rec;
+  if (nr == 0) return m->fail(CN_ESTATE, "the loss needs recorded nodes");
+  CN_TRY_CUDA(m, cudaSetDevice(m->opt.device));
+  CN_CHECK(cn_sync(m));
+  const int64_t S = m->ck_steps, E = m->node_elems, H = std::max<int64_t>(m->hh_elems, 1);
+  // device buffers
+  std::vector<double> h_dj((size_t)(K + 1) * nr);
+  for (int r = 0; r < nr; ++r)
+    for (int64_t k = 0; k <= K; ++k) h_dj[(size_t)k * nr + r] = dj[(size_t)r * (K + 1) + k];
+  cn::AdjView A{};
+  double* p;
+  CN_CHECK(upload(m, &p, h_dj)); A.dj = p;
+  CN_CHECK(zeros(m, &A.lam, E));
+  CN_CHECK(zeros(m, &A.ytmp, E));
+  CN_CHECK(zeros(m, &A.qtmp, E));
+  CN_CHECK(zeros(m, &A.xi, 3 * (size_t)m->n_slots));
+  CN_CHECK(zeros(m, &A.grad, 3 * (size_t)m->n_slots));
+  A.K = K;
+  double *tv, *tg;
+  CN_CHECK(zeros(m, &tv, (size_t)(S + 1) * E));
+  CN_CHECK(zeros(m, &tg, (size_t)(S + 1) * 3 * H));
+  void* fin = dalloc_raw(m, m->ck_bytes);
+  if (!fin) return m->fail(CN_ENOMEM, "adjoint allocation failed");
+  CN_CHECK(snapshot(m, fin, true));
+  const int tb = 128, nb = (m->n_slots + tb - 1) / tb;
+  {
+    cn::DevModel dm = m->dm;
+    CN_CHECK(launch_checked(m, [&] { cn::k_adjoint_init<<<nb, tb, 0, m->stream>>>(dm, A); }));
+  }
+  const size_t adj_smem = (size_t)m->dm.stack_depth * cn::kLanes * 3 * sizeof(double);
+  for (int64_t seg = (K - 1) / S; seg >= 0; --seg) {
+    const int64_t k0 = seg * S, k1 = std::min<int64_t>(K, k0 + S);
+    CN_CHECK(snapshot(m, m->ck_buf[(size_t)seg], false));
+    m->dm.traj_v = tv;
+    m->dm.traj_g = tg;
+    m->dm.traj_k0 = k0;
+    cn::DevModel dm = m->dm;
+    CN_CHECK(launch_checked(m, [&] { cn::k_traj_first<<<nb, tb, 0, m->stream>>>(dm); }));
+    m->step = k0;
+    CN_CHECK(advance(m, k1, true));
+    CN_CHECK(launch_checked(m, [&] {
+      cn::k_adjoint<<<m->n_groups, 32, adj_smem, m->stream>>>(dm, A, k0, k1);
+    }));
+  }
+  m->dm.traj_v = nullptr;
+  m->dm.traj_g = nullptr;
+  CN_CHECK(snapshot(m, fin, false));
+  m->step = K;
+  std::vector<double> h_g(3 * (size_t)m->n_slots);
+  CN_TRY_CUDA(m, cudaMemcpyAsync(h_g.data(), A.grad, h_g.size() * 8, cudaMemcpyDeviceToHost, m->stream));
+  CN_TRY_CUDA(m, cudaStreamSynchronize(m->stream));
+  for (int c = 0; c < m->n_cells; ++c)
+    for (int q = 0; q < 3; ++q) grad[(size_t)q * m->n_cells + c] = h_g[(size_t)q * m->n_slots + m->cell_slot[c]];
+  for (void* b : {(void*)A.dj, (void*)A.lam, (void*)A.ytmp, (void*)A.qtmp, (void*)A.xi, (void*)A.grad, (void*)tv,
+                  (void*)tg, fin})
+    dfree_raw(m, b);
   return CN_OK;
 }
 

@@ -5,27 +5,26 @@
 namespace cn {
 
 // ------------------------------------------------------------------ setup
-// Matrix constants of every row (Eq. 1 discretised on the tree), with row i
-// divided by cdt_i = 1e-3 cm_i/dt:
+// Geometry part of every row (Eq. 1 discretised on the tree), rows scaled by
+// 1/cdt_i, cdt_i = 1e-3 cm_i/dt:
 //   b_i  = -100/(ri_i area_i) / cdt_i          (row i, column parent)
 //   a_i  = -100/(ri_i area_p) / cdt_p          (row parent, column i)
-//   d0_i = (cdt_i + pas g_i + axial couplings of row i) / cdt_i
-//   ge_i = pas g_i e_i / cdt_i
-// and v = v_init.  One thread per cell; prow holds parent rows.
+//   dax_i = sum of the unscaled axial couplings of row i
+// One thread per cell; prow holds parent rows.  Rows past the cell's end
+// (the group's rows are those of its largest cell) get zero couplings.
 __global__ void k_setup_nodes(DevModel M, const double* area, const double* ri, const double* cm,
-                              const double* gpas, const double* epas, const int32_t* prow, double v_init) {
+                              const int32_t* prow) {
   const int slot = blockIdx.x * blockDim.x + threadIdx.x;
   if (slot >= M.n_slots) return;
   const int g = slot / kLanes, lane = slot % kLanes;
   const int N = M.s_rows[slot];
   const int64_t nb = M.g_node_base[g] + lane;
-  double* d0 = const_cast<double*>(M.d0);
   double* a = const_cast<double*>(M.a);
   double* b = const_cast<double*>(M.b);
-  double* ge = const_cast<double*>(M.ge);
-  for (int j = 0; j < N; ++j) {
+  for (int j = 0; j < M.g_rows[g]; ++j) {
     const int64_t i = nb + (int64_t)j * kLanes;
-    d0[i] = 1e-3 * cm[i] / M.dt + gpas[i];
+    M.cdt[i] = j < N ? 1e-3 * cm[i] / M.dt : 1.0;
+    M.dax[i] = 0.0;
     a[i] = 0.0;
     b[i] = 0.0;
   }
@@ -34,30 +33,125 @@ __global__ void k_setup_nodes(DevModel M, const double* area, const double* ri, 
     const int64_t ip = nb + (int64_t)prow[i] * kLanes;
     const double bb = -100.0 / (ri[i] * area[i]);
     const double aa = -100.0 / (ri[i] * area[ip]);
-    d0[i] -= bb;
-    d0[ip] -= aa;
-    b[i] = bb / (1e-3 * cm[i] / M.dt);
-    a[i] = aa / (1e-3 * cm[ip] / M.dt);
+    M.dax[i] -= bb;
+    M.dax[ip] -= aa;
+    b[i] = bb / M.cdt[i];
+    a[i] = aa / M.cdt[ip];
   }
-  for (int j = 0; j < N; ++j) {
+}
+
+// Diagonal and right-hand-side constants from the pas parameters:
+//   d0_i = (cdt_i + g_i + dax_i) / cdt_i,   ge_i = g_i e_i / cdt_i,
+// identity rows past the cell's end.  Re-run when pas g changes.
+__global__ void k_pas_apply(DevModel M) {
+  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot >= M.n_slots) return;
+  const int g = slot / kLanes, lane = slot % kLanes;
+  const int N = M.s_rows[slot];
+  const int64_t nb = M.g_node_base[g] + lane;
+  double* d0 = const_cast<double*>(M.d0);
+  double* ge = const_cast<double*>(M.ge);
+  for (int j = 0; j < M.g_rows[g]; ++j) {
     const int64_t i = nb + (int64_t)j * kLanes;
-    const double cdt = 1e-3 * cm[i] / M.dt;
-    d0[i] = d0[i] / cdt;
-    ge[i] = gpas[i] * epas[i] / cdt;
-    M.v[i] = v_init;
+    if (j < N) {
+      const double c = M.cdt[i];
+      d0[i] = (c + M.pas_g[i] + M.dax[i]) / c;
+      ge[i] = M.pas_g[i] * M.pas_e[i] / c;
+    } else {
+      d0[i] = 1.0;
+      ge[i] = 0.0;
+    }
+  }
+}
+
+// HH conductance densities divided by cdt of their row.  Re-run when gnabar
+// or gkbar change.
+__global__ void k_hh_params(DevModel M) {
+  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot >= M.n_slots) return;
+  const int g = slot / kLanes, lane = slot % kLanes;
+  const int n = M.s_nhh[slot];
+  const int64_t base = M.g_hh_base[g] + lane, nb = M.g_node_base[g] + lane;
+  double* P = const_cast<double*>(M.hh_p);
+  for (int q = 0; q < n; ++q) {
+    const int64_t i = base + (int64_t)q * kLanes;
+    const double c = M.cdt[nb + (int64_t)M.hh_row[i] * kLanes];
+    for (int col = 0; col < 6; ++col) {
+      const double raw = M.hh_raw[col * M.hh_elems + i];
+      P[col * M.hh_elems + i] = col < 3 ? raw / c : raw;
+    }
+  }
+}
+
+// Per-cell parameter update: HH gnabar (0) or gkbar (1) of every HH instance
+// of the cell, or pas g (2) of every row carrying pas.  value[slot].
+__global__ void k_set_cell_param(DevModel M, int32_t param, const double* value) {
+  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot >= M.n_slots || M.s_gid[slot] < 0) return;
+  const int g = slot / kLanes, lane = slot % kLanes;
+  const double x = value[slot];
+  if (param < 2) {
+    const int n = M.s_nhh[slot];
+    const int64_t base = M.g_hh_base[g] + lane;
+    for (int q = 0; q < n; ++q) M.hh_raw[param * M.hh_elems + base + (int64_t)q * kLanes] = x;
+  } else {
+    const int N = M.s_rows[slot];
+    const int64_t nb = M.g_node_base[g] + lane;
+    for (int j = 0; j < N; ++j) {
+      const int64_t i = nb + (int64_t)j * kLanes;
+      if (M.flags[i] & kHasPasBit) M.pas_g[i] = x;
+    }
+  }
+}
+
+// Per-cell parameter read-back (value[slot]).
+__global__ void k_get_cell_param(DevModel M, int32_t param, double* value) {
+  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot >= M.n_slots) return;
+  const int g = slot / kLanes, lane = slot % kLanes;
+  double x = 0.0;
+  if (param < 2) {
+    if (M.s_nhh[slot] > 0) x = M.hh_raw[param * M.hh_elems + M.g_hh_base[g] + lane];
+  } else {
+    const int N = M.s_rows[slot];
+    const int64_t nb = M.g_node_base[g] + lane;
+    for (int j = N - 1; j >= 0; --j)
+      if (M.flags[nb + (int64_t)j * kLanes] & kHasPasBit) x = M.pas_g[nb + (int64_t)j * kLanes];
+  }
+  value[slot] = x;
+}
+
+// Initial state: v = v_init (0 on rows past the cell's end), HH gates at
+// their steady state of v_init, synaptic g = 0, threshold flags.
+template <int PREC>
+__global__ void k_state_init(DevModel M, double v_init) {
+  using S = typename GateT<PREC>::S;
+  using T = typename GateT<PREC>::M;
+  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot >= M.n_slots) return;
+  const int g = slot / kLanes, lane = slot % kLanes;
+  const int N = M.s_rows[slot];
+  const int64_t nb = M.g_node_base[g] + lane;
+  for (int j = 0; j < M.g_rows[g]; ++j) {
+    const int64_t i = nb + (int64_t)j * kLanes;
+    M.v[i] = j < N ? v_init : 0.0;
     M.bp[i] = 0.0;
   }
-  // Rows past the cell's end (the group's rows are those of its largest
-  // cell) are identity rows with zero couplings: eliminating them is a no-op.
-  for (int j = N; j < M.g_rows[g]; ++j) {
-    const int64_t i = nb + (int64_t)j * kLanes;
-    d0[i] = 1.0;
-    ge[i] = 0.0;
-    a[i] = 0.0;
-    b[i] = 0.0;
-    M.v[i] = 0.0;
-    M.bp[i] = 0.0;
+  const int nh = M.s_nhh[slot];
+  const int64_t hb = M.g_hh_base[g] + lane;
+  for (int q = 0; q < nh; ++q) {
+    const int64_t i = hb + (int64_t)q * kLanes;
+    T am, bm, ah, bh, an, bn;
+    hh_rates<T>(T(v_init), am, bm, ah, bh, an, bn);
+    g_store(static_cast<S*>(M.hh_m) + i, am / (am + bm));
+    g_store(static_cast<S*>(M.hh_h) + i, ah / (ah + bh));
+    g_store(static_cast<S*>(M.hh_n) + i, an / (an + bn));
   }
+  const int ns = M.s_nsyn[slot];
+  const int64_t sb = M.g_syn_base[g] + lane;
+  for (int q = 0; q < ns; ++q) M.syn_g[sb + (int64_t)q * kLanes] = 0.0;
+  M.s_above[slot] = N > 0 && v_init > M.s_thresh[slot];
+  M.ev_count[slot] = 0;
 }
 
 // Per-slot copies of the slot row's constants (the slot buffer is reset to
@@ -89,30 +183,6 @@ __global__ void k_setup_syn(DevModel M, const double* node_area, const double* n
     const_cast<double*>(M.syn_s)[i] = 100.0 / (node_area[i] * (1e-3 * node_cm[i] / M.dt));
     const_cast<double*>(M.syn_decay)[i] = exp(-M.dt / tau[i]);
     M.syn_g[i] = 0.0;
-  }
-}
-
-// HH: conductance densities divided by cdt of their row; gates at their
-// steady state of v_init.
-template <int PREC>
-__global__ void k_setup_hh(DevModel M, const double* node_cm, double v_init) {
-  using S = typename GateT<PREC>::S;
-  using T = typename GateT<PREC>::M;
-  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
-  if (slot >= M.n_slots) return;
-  const int g = slot / kLanes, lane = slot % kLanes;
-  const int n = M.s_nhh[slot];
-  const int64_t base = M.g_hh_base[g] + lane;
-  double* P = const_cast<double*>(M.hh_p);
-  for (int q = 0; q < n; ++q) {
-    const int64_t i = base + (int64_t)q * kLanes;
-    const double cdt = 1e-3 * node_cm[i] / M.dt;
-    for (int c = 0; c < 3; ++c) P[c * M.hh_elems + i] /= cdt;
-    T am, bm, ah, bh, an, bn;
-    hh_rates<T>(T(v_init), am, bm, ah, bh, an, bn);
-    g_store(static_cast<S*>(M.hh_m) + i, am / (am + bm));
-    g_store(static_cast<S*>(M.hh_h) + i, ah / (ah + bh));
-    g_store(static_cast<S*>(M.hh_n) + i, an / (an + bn));
   }
 }
 
@@ -221,7 +291,10 @@ __global__ void k_pull_events(DevModel M, int64_t J) {
 // Row data streams through a per-lane shared-memory ring fed by cp.async, each
 // lane copying its own elements kElimRows rows ahead; parents come from a register
 // carry (previous row) or the per-lane far stack.
-template <int PREC>
+// TRAJ: adjoint recompute -- also store v and the HH gates of every step
+// into the trajectory buffers, and leave spikes, threshold flags and traces
+// untouched.
+template <int PREC, bool TRAJ>
 __global__ void __launch_bounds__(32) k_interval(DevModel M, int64_t J, int s_begin, int s_end) {
   using S = typename GateT<PREC>::S;
   using T = typename GateT<PREC>::M;
@@ -402,7 +475,7 @@ __global__ void __launch_bounds__(32) k_interval(DevModel M, int64_t J, int s_be
             sl_ge[si] = g0;  // re-seed the slot for the next step
             sl_d[si] = d00;
           }
-          const int np = f >> kNFarShift;
+          const int np = (f >> kNFarShift) & kNFarMask;
           const int tp = np > 0 ? top - 1 : top;
           const int ti = (tp < DS ? tp : DS - 1) * kLanes;
           // stale stack words must not reach the FMAs (0 * NaN is NaN): select
@@ -458,7 +531,8 @@ __global__ void __launch_bounds__(32) k_interval(DevModel M, int64_t J, int s_be
           const double pv = st_x[(tp < DS ? tp : DS - 1) * kLanes];
           const double vj = fma(-b_bp[ro], far ? pv : vprev, b_x[ro]);
           gv[(int64_t)j * kLanes] = vj;
-          const int np = f >> kNFarShift;
+          if (TRAJ) M.traj_v[(k + 1 - M.traj_k0) * M.node_elems + nb + (int64_t)j * kLanes] = vj;
+          const int np = (f >> kNFarShift) & kNFarMask;
           if (np > 0) st_x[tp * kLanes] = vj;
           for (int q = 1; q < np; ++q) st_x[(tp + q) * kLanes] = vj;
           top = tp + np;
@@ -480,10 +554,16 @@ __global__ void __launch_bounds__(32) k_interval(DevModel M, int64_t J, int s_be
         g_store(gm + i, cnexp_step<T>(g_load(gm + i), am, bm, tdt));
         g_store(gh + i, cnexp_step<T>(g_load(gh + i), ah, bh, tdt));
         g_store(gn + i, cnexp_step<T>(g_load(gn + i), an, bn, tdt));
+        if (TRAJ) {
+          double* tg = M.traj_g + (k + 1 - M.traj_k0) * 3 * M.hh_elems + i;
+          tg[0] = (double)g_load(gm + i);
+          tg[M.hh_elems] = (double)g_load(gh + i);
+          tg[2 * M.hh_elems] = (double)g_load(gn + i);
+        }
       }
     }
     // (5) threshold detection and recording
-    if (N > 0) {
+    if (!TRAJ && N > 0) {
       const double vs = spike_row == 0 ? x0 : M.v[nb + (int64_t)spike_row * kLanes];
       const int now = vs > thresh;
       if (now && !above) mask |= 1ull << s;
@@ -497,7 +577,7 @@ __global__ void __launch_bounds__(32) k_interval(DevModel M, int64_t J, int s_be
       }
     }
   }
-  if (gid >= 0) {
+  if (!TRAJ && gid >= 0) {
     M.hist[J * M.n_cells + gid] = mask;
     M.s_above[slot] = (uint8_t)above;
   }
@@ -517,17 +597,206 @@ __global__ void k_record0(DevModel M, int64_t k) {
   }
 }
 
-// Threshold flags at the initial state.
-__global__ void k_init_above(DevModel M) {
+// -------------------------------------------------------------------- adjoint
+// Reverse pass of the FP64 backward-Euler map over steps [k0, k1) of one
+// checkpoint segment (cn_run_adjoint).  The forward step is
+// A_k v_{k+1} = C v_k + b_k, A_k = C + G_k + L, gates_{k+1} = Phi(gates_k,
+// v_{k+1}); with lambda_{k+1} = dJ/dv_{k+1} in `lam`, step k computes
+//   mu_k = A_k^-T lambda_{k+1}     (Hines on the transposed rows: a <-> b)
+//   xi_k = dPhi/dgates_k xi_{k+1} + mu_soma d(GE - G v_{k+1})/dgates_k
+//   lambda_k = C mu_k + dJ/dv_k + (dPhi_{k-1}/dv_k)^T xi_k
+// and accumulates dJ/dtheta += mu_k . d(b_k - A_k v_{k+1})/dtheta for the
+// cell's gnabar, gkbar and pas g.  The row-scaled matrix is A' = A/cdt, so
+// A'^T y = lambda gives mu = y/cdt and C mu = y.  One cell per lane, at
+// most one HH instance per cell; traj holds v_{k0..k1} and gates_{k0..k1}.
+struct AdjView {
+  double* lam;      // [node_elems]
+  double* ytmp;     // [node_elems]
+  double* qtmp;     // [node_elems]
+  double* xi;       // [3][n_slots]
+  double* grad;     // [3][n_slots]
+  const double* dj; // [K+1][n_rec] dJ/d(trace)
+  int64_t K;
+};
+
+__device__ __forceinline__ double vtrap_d(double A, double vh, double k, double v) {
+  // d/dv of A (v - vh) / (1 - exp(-(v - vh)/k))
+  const double u = (v - vh) / k;
+  if (fabs(u) < 1e-6) return A * (0.5 + u / 3.0);
+  const double em = exp(-u), den = 1.0 - em;
+  return A * (den - u * em) / (den * den);
+}
+
+// Rates, their derivatives, and the cnexp sensitivities at v: for each gate
+// dx_new/dx_old = E and dx_new/dv = dinf (1 - E) + (x - inf) dE.
+__device__ void hh_sens(double v, double xm, double xh, double xn, double dt, double* E, double* dv) {
+  double am, bm, ah, bh, an, bn;
+  hh_rates<double>(v, am, bm, ah, bh, an, bn);
+  const double dam = vtrap_d(0.1, -40.0, 10.0, v), dbm = -bm / 18.0;
+  const double dah = -ah / 20.0, dbh = bh * (1.0 - bh) / 10.0;
+  const double dan = vtrap_d(0.01, -55.0, 10.0, v), dbn = -bn / 80.0;
+  const double al[3] = {am, ah, an}, be[3] = {bm, bh, bn}, dal[3] = {dam, dah, dan}, dbe[3] = {dbm, dbh, dbn};
+  const double x[3] = {xm, xh, xn};
+  for (int c = 0; c < 3; ++c) {
+    const double s = al[c] + be[c];
+    const double inf = al[c] / s;
+    const double e = exp(-dt * s);
+    const double dinf = (dal[c] * be[c] - al[c] * dbe[c]) / (s * s);
+    E[c] = e;
+    dv[c] = dinf * (1.0 - e) + (x[c] - inf) * (-dt * (dal[c] + dbe[c]) * e);
+  }
+}
+
+__global__ void __launch_bounds__(32) k_adjoint(DevModel M, AdjView A, int64_t k0, int64_t k1) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int g = blockIdx.x;
+  if (g >= M.n_groups) return;
+  const int lane = threadIdx.x;
+  const int slot = g * kLanes + lane;
+  const int N = M.s_rows[slot];
+  const int R = M.g_rows[g];
+  const int64_t nb = M.g_node_base[g] + lane;
+  const int DS = M.stack_depth;
+  double* const st_a = reinterpret_cast<double*>(smem) + lane;
+  double* const st_x = st_a + DS * kLanes;
+  double* const st_y = st_x + DS * kLanes;
+  const int nhh = M.s_nhh[slot];
+  const int64_t hi = M.g_hh_base[g] + lane;
+  const int hrow = nhh > 0 ? M.hh_row[hi] : -1;
+  const int64_t H = M.hh_elems, E = M.node_elems;
+  const int RR = M.g_rec_rows[g], nrec = M.s_nrec[slot];
+  const int64_t rcb = M.g_rec_base[g] + lane;
+  const double dt = M.dt;
+  double xi[3] = {A.xi[slot], A.xi[M.n_slots + slot], A.xi[2 * M.n_slots + slot]};
+  double gna = 0.0, gk = 0.0, gpas = 0.0;
+  auto gate = [&](int64_t t, int c) { return M.traj_g[t * 3 * H + c * H + hi]; };
+  auto gate_term = [&](int64_t k) {  // (dPhi_{k-1}/dv_k)^T xi_k at the HH row
+    double Ek[3], dv[3];
+    const int64_t t = k - 1 - k0;
+    hh_sens(M.traj_v[(k - k0) * E + nb + (int64_t)hrow * kLanes], gate(t, 0), gate(t, 1), gate(t, 2), dt, Ek, dv);
+    return xi[0] * dv[0] + xi[1] * dv[1] + xi[2] * dv[2];
+  };
+  if (nhh > 0 && k1 < A.K) A.lam[nb + (int64_t)hrow * kLanes] += gate_term(k1);
+  for (int64_t k = k1 - 1; k >= k0; --k) {
+    const int64_t tv1 = (k + 1 - k0) * E;
+    double m = 0.0, h = 0.0, n = 0.0, Gh = 0.0;
+    if (nhh > 0) {
+      m = gate(k - k0, 0);
+      h = gate(k - k0, 1);
+      n = gate(k - k0, 2);
+      Gh = M.hh_p[hi] * (m * m * m * h) + M.hh_p[H + hi] * ((n * n) * (n * n)) + M.hh_p[2 * H + hi];
+    }
+    // elimination of the transposed rows, leaves to root
+    double ca = 0.0, cx = 0.0, cb = 0.0;
+    int top = 0;
+    for (int j = R - 1; j >= 0; --j) {
+      const int64_t e = nb + (int64_t)j * kLanes;
+      const int f = M.flags[e];
+      const int np = (f >> kNFarShift) & kNFarMask;
+      double rhs = A.lam[e];
+      double d = M.d0[e] + (j == hrow ? Gh : 0.0);
+      for (int q = 0; q < np; ++q) {
+        --top;
+        rhs = fma(st_a[top * kLanes], st_x[top * kLanes], rhs);
+        d = fma(st_a[top * kLanes], st_y[top * kLanes], d);
+      }
+      rhs = fma(ca, cx, rhs);
+      d = fma(ca, cb, d);
+      const double y = rhs / d, q = M.a[e] / d;
+      A.ytmp[e] = y;
+      A.qtmp[e] = q;
+      const double nbc = -M.b[e];
+      if (f & kFarBit) {
+        st_a[top * kLanes] = nbc;
+        st_x[top * kLanes] = y;
+        st_y[top * kLanes] = q;
+        ++top;
+        ca = 0.0;
+      } else {
+        ca = nbc;
+        cx = y;
+        cb = q;
+      }
+    }
+    // back substitution, root to leaves; gradients; lambda_k = y
+    double yprev = 0.0, mus = 0.0, vs1 = 0.0;
+    for (int j = 0; j < R; ++j) {
+      const int64_t e = nb + (int64_t)j * kLanes;
+      const int f = M.flags[e];
+      double yp = yprev;
+      if (f & kFarBit) yp = st_x[--top * kLanes];
+      const double yj = fma(-A.qtmp[e], yp, A.ytmp[e]);
+      const int np = (f >> kNFarShift) & kNFarMask;
+      for (int q = 0; q < np; ++q) st_x[top++ * kLanes] = yj;
+      yprev = yj;
+      if (j < N) {
+        const double mu = yj / M.cdt[e];
+        const double v1 = M.traj_v[tv1 + e];
+        if (f & kHasPasBit) gpas = fma(mu, M.pas_e[e] - v1, gpas);
+        if (j == hrow) {
+          mus = mu;
+          vs1 = v1;
+        }
+      }
+      A.lam[e] = yj;
+    }
+    if (nhh > 0) {
+      const double ena = M.hh_raw[4 * H + hi], ek = M.hh_raw[5 * H + hi];
+      const double gnab = M.hh_raw[hi], gkb = M.hh_raw[H + hi];
+      gna = fma(mus, (m * m * m * h) * (ena - vs1), gna);
+      gk = fma(mus, ((n * n) * (n * n)) * (ek - vs1), gk);
+      double Ek[3], dv[3];
+      hh_sens(vs1, m, h, n, dt, Ek, dv);
+      xi[0] = Ek[0] * xi[0] + mus * gnab * 3.0 * m * m * h * (ena - vs1);
+      xi[1] = Ek[1] * xi[1] + mus * gnab * m * m * m * (ena - vs1);
+      xi[2] = Ek[2] * xi[2] + mus * gkb * 4.0 * n * n * n * (ek - vs1);
+    }
+    if (k >= 1) {
+      for (int q = 0; q < RR; ++q) {
+        if (q < nrec) {
+          const int64_t i = rcb + (int64_t)q * kLanes;
+          A.lam[nb + (int64_t)M.rec_row[i] * kLanes] += A.dj[k * M.n_rec + M.rec_id[i]];
+        }
+      }
+      if (nhh > 0 && k > k0) A.lam[nb + (int64_t)hrow * kLanes] += gate_term(k);
+    }
+  }
+  A.xi[slot] = xi[0];
+  A.xi[M.n_slots + slot] = xi[1];
+  A.xi[2 * M.n_slots + slot] = xi[2];
+  A.grad[slot] += gna;
+  A.grad[M.n_slots + slot] += gk;
+  A.grad[2 * M.n_slots + slot] += gpas;
+}
+
+// lambda_K = dJ/dv_K at the recorded rows.
+__global__ void k_adjoint_init(DevModel M, AdjView A) {
   const int slot = blockIdx.x * blockDim.x + threadIdx.x;
   if (slot >= M.n_slots) return;
-  if (M.s_rows[slot] == 0) {
-    M.s_above[slot] = 0;
-    return;
-  }
   const int g = slot / kLanes, lane = slot % kLanes;
-  const int64_t i = M.g_node_base[g] + lane + (int64_t)M.s_spike_row[slot] * kLanes;
-  M.s_above[slot] = M.v[i] > M.s_thresh[slot];
+  const int nrec = M.s_nrec[slot];
+  const int64_t rcb = M.g_rec_base[g] + lane, nb = M.g_node_base[g] + lane;
+  for (int q = 0; q < nrec; ++q) {
+    const int64_t i = rcb + (int64_t)q * kLanes;
+    A.lam[nb + (int64_t)M.rec_row[i] * kLanes] += A.dj[A.K * M.n_rec + M.rec_id[i]];
+  }
+}
+
+// Trajectory entry of the segment's first step (v and gates at k0).
+__global__ void k_traj_first(DevModel M) {
+  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot >= M.n_slots) return;
+  const int g = slot / kLanes, lane = slot % kLanes;
+  const int64_t nb = M.g_node_base[g] + lane;
+  for (int j = 0; j < M.g_rows[g]; ++j) M.traj_v[nb + (int64_t)j * kLanes] = M.v[nb + (int64_t)j * kLanes];
+  const int nh = M.s_nhh[slot];
+  const int64_t hb = M.g_hh_base[g] + lane;
+  for (int q = 0; q < nh; ++q) {
+    const int64_t i = hb + (int64_t)q * kLanes;
+    M.traj_g[i] = static_cast<const double*>(M.hh_m)[i];
+    M.traj_g[M.hh_elems + i] = static_cast<const double*>(M.hh_h)[i];
+    M.traj_g[2 * M.hh_elems + i] = static_cast<const double*>(M.hh_n)[i];
+  }
 }
 
 }  // namespace cn

@@ -433,3 +433,39 @@ def test_calcium_decay_step():
     cai1 = 5e-5 + (1 - math.exp(-0.025 / 80.0)) * (5e-5 + drive * 80.0 - 5e-5)
     assert drive > 0
     assert abs(m.cai()[0] - cai1) < 1e-15
+
+
+# ---------------------------------------------------------------- adjoint
+def test_oracle_adjoint_matches_central_differences():
+    """The discrete adjoint (reverse Hines solve + HH gate Jacobians, with
+    checkpointed recompute) against central finite differences of the
+    oracle's forward map, h = 1e-6 relative, for gnabar, gkbar and pas g."""
+    import copy
+    from scenarios import adjoint_net
+    from oracle import adjoint
+    sc = adjoint_net(n_cells=3, tstop=12.0, n_range=(20, 40))
+    K = sc.nsteps
+    tgt = simulate(sc, nthreads=1).traces() + 0.5 * np.sin(np.arange(K + 1) * 0.01)[None, :]
+
+    def loss(s):
+        tr = simulate(s, nthreads=1).traces()
+        return float(np.sum((tr[:, 1:] - tgt[:, 1:]) ** 2))
+
+    J, gna, gk, gp = adjoint(sc, K, tgt, seg=37, nthreads=1)
+    assert abs(J - loss(sc)) <= 1e-12 * J
+
+    def fd(kind, name, inst):
+        h = 1e-6 * abs(sc.mech(kind).params[name][inst])
+        sp, sm = copy.deepcopy(sc), copy.deepcopy(sc)
+        sp.mech(kind).params[name][inst] += h
+        sm.mech(kind).params[name][inst] -= h
+        return (loss(sp) - loss(sm)) / (2 * h)
+
+    for inst in range(3):
+        assert abs(gna[inst] - fd("hh", "gnabar", inst)) <= 1e-6 * abs(gna[inst])
+        assert abs(gk[inst] - fd("hh", "gkbar", inst)) <= 1e-6 * abs(gk[inst])
+    for inst in (0, 17, 40):
+        assert abs(gp[inst] - fd("pas", "g", inst)) <= 1e-6 * max(abs(gp[inst]), 1.0)
+    # checkpoint spacing does not change the result
+    J2, gna2, gk2, gp2 = adjoint(sc, K, tgt, seg=K, nthreads=2)
+    assert np.allclose(gna2, gna, rtol=1e-12) and np.allclose(gp2, gp, rtol=1e-12, atol=1e-12)
