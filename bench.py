@@ -152,7 +152,8 @@ def config_dict(args, sc):
     return {"workload": f"network {args.cells} cells x 200-600 compartments (HH soma, pas dendrites), "
                         f"50 ExpSyn/cell, 100 NetCons/cell, 5 Hz background, dt 0.025 ms, FP64",
             "cells": args.cells, "compartments": int(sc.n_nodes), "step": "one 1 ms min-delay interval (40 dt)",
-            "l2": "working set > L2 (no flush needed)", "precision": args.precision}
+            "l2": "working set > L2 (no flush needed)", "precision": args.precision,
+            "mapping": getattr(args, "mapping", 0)}
 
 
 def cpu_oracle_rate(sc, intervals, warm=0):
@@ -202,7 +203,7 @@ def run_ours(args):
     from paper_1901_10975_gb300 import cn
     W, K = args.warmup, args.steps
     sc = workload(args, W + K)
-    md = cn.from_scenario(sc, precision=args.precision, device=local, record=False)
+    md = cn.from_scenario(sc, precision=args.precision, device=local, record=False, mapping=args.mapping)
     md.cn_profile(True)
     md.cn_run(float(W))                       # warm-up intervals (includes the one-time upload)
     md.cn_sync()
@@ -284,7 +285,7 @@ def e2e_measure(args, cn, K):
     h2d += sum(m.node.nbytes + m.param_matrix().nbytes for m in sc.mechs)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    md = cn.from_scenario(sc, precision=args.precision, record=True)
+    md = cn.from_scenario(sc, precision=args.precision, record=True, mapping=args.mapping)
     md.cn_run(float(K))
     g, k = md.cn_get_spikes()
     tr = [md.cn_get_trace(r) for r in range(len(sc.rec_node))]
@@ -307,6 +308,8 @@ def main():
     ap.add_argument("--cpu-intervals", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--mapping", type=int, default=0,
+                    help="0: automatic cell split, 1: one cell per lane, >=16: target rows per lane")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -106,16 +106,55 @@ typedef struct {
   cn_alloc_fn alloc;
   cn_free_fn free;
   void* alloc_ctx;
-  int32_t mapping;       /* cn_mapping: cell-to-thread mapping, CN_MAP_AUTO picks */
-  int32_t use_graph;     /* nonzero: replay intervals from a captured CUDA graph */
+  int32_t mapping;       /* CN_MAP_AUTO, CN_MAP_THREAD, CN_MAP_TUNE, or a target span (>= 16 rows) */
+  int32_t use_graph;     /* nonzero: whole intervals replay, 8 at a time, from a captured CUDA graph */
+  int32_t warps_per_block; /* 1..4 warps (each one group of 32 lanes) per block of the interval
+                              kernel; 0 = 1 (CN_MAP_TUNE picks it) */
 } cn_options;
 
+/* Cell-to-lane mapping.  Cells are packed 32 lanes to a warp with
+ * interleaved rows; a cell larger than the target span is cut into subtrees
+ * ("parts") that occupy several lanes of one warp and exchange their
+ * junction values by warp shuffles (the warp-cooperative solve of large
+ * cells).  A value >= 16 sets the target span in rows directly.           */
 typedef enum {
-  CN_MAP_AUTO = 0,       /* autotuned */
-  CN_MAP_THREAD = 1      /* one cell per thread, 32 cells per warp, interleaved nodes */
+  CN_MAP_AUTO = 0,       /* target span = mean cell size (no split when the adjoint is on) */
+  CN_MAP_THREAD = 1,     /* one cell per lane, never split */
+  CN_MAP_TUNE = 2        /* autotuned on first use: each candidate span (one cell per lane, 1/4,
+                            1/2, 1 and 2 mean cell sizes) with 1, 2 and 4 warps per block runs one
+                            timed interval from the initial state; the fastest is kept */
 } cn_mapping;
 
+/* The layout in use (after the first cn_run, or after the autotuner):
+ * mapping (CN_MAP_THREAD or the target span), warps per block, warps in all,
+ * and the autotuner's timed interval in ms (0 without tuning).  Lays the
+ * model out first if needed.                                             */
 typedef struct cn_model cn_model;
+cn_status cn_get_mapping(cn_model* m, int32_t* mapping, int32_t* warps_per_block, int32_t* n_warps,
+                         float* tuned_interval_ms);
+
+/* Host-only preview of the placement cn_model_create makes for a morphology
+ * (no GPU is touched).  The elimination order is the Hines order of
+ * Section 2: in every part the rows are a depth-first preorder of its
+ * subtree, so a row's parent is an earlier row of the same lane, or, for a
+ * part root, the junction row of the parent part, exactly one warp row
+ * earlier in another lane of the same warp.
+ *   n_cells, cell_offset[n_cells+1], parent[n_nodes]: as in cn_morph.
+ *   mapping: a cn_mapping value or a target span (>= 16 rows).
+ * Outputs (caller-owned, each may be NULL):
+ *   node_lane[n_nodes]  global lane = 32 * warp + lane of the node's part
+ *   node_row[n_nodes]   warp row of the node
+ *   node_flags[n_nodes] topology bits: 1<<12 the in-part parent is not the
+ *                       previous row ("far"); bits 13-15 number of far
+ *                       children; 1<<17 real node; 1<<18 junction (a child
+ *                       part hangs from it) with that part's lane in bits
+ *                       19-23; 1<<24 part root with its parent part's lane
+ *                       in bits 25-29.
+ *   n_warps, stack_depth: warps used; far-child stack words per lane.
+ * Errors: CN_EINVAL on malformed trees or a node with more than 8 children. */
+cn_status cn_plan_layout(int32_t n_cells, const int32_t* cell_offset, const int32_t* parent, int32_t mapping,
+                         int32_t* node_lane, int32_t* node_row, int32_t* node_flags, int32_t* n_warps,
+                         int32_t* stack_depth);
 
 /* Fill *opt with defaults: dt 0.025 ms, v_init -65 mV, FP64, device 0,
  * default stream, cudaMalloc, autotuned mapping, graphs on. */

@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(HERE, "libcn.so")
 
 CN_OK, CN_EINVAL, CN_ENOMEM, CN_ECUDA, CN_ESTATE, CN_ETIMEOUT, CN_ERANGE = range(7)
 CN_PARAM_GNABAR, CN_PARAM_GKBAR, CN_PARAM_GPAS = range(3)
+CN_MAP_AUTO, CN_MAP_THREAD, CN_MAP_TUNE = range(3)
 STATUS_NAMES = {0: "CN_OK", 1: "CN_EINVAL", 2: "CN_ENOMEM", 3: "CN_ECUDA", 4: "CN_ESTATE",
                 5: "CN_ETIMEOUT", 6: "CN_ERANGE"}
 MECH = {"pas": 0, "hh": 1, "expsyn": 2, "na3h": 3, "kdr4": 4, "ka": 5, "ih": 6, "cahva": 7, "kca": 8}
@@ -41,7 +42,8 @@ class cn_mech_table(C.Structure):
 class cn_options(C.Structure):
     _fields_ = [("dt_ms", C.c_double), ("v_init_mV", C.c_double), ("precision", C.c_int32),
                 ("device", C.c_int32), ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
-                ("alloc_ctx", C.c_void_p), ("mapping", C.c_int32), ("use_graph", C.c_int32)]
+                ("alloc_ctx", C.c_void_p), ("mapping", C.c_int32), ("use_graph", C.c_int32),
+                ("warps_per_block", C.c_int32)]
 
 
 class CNError(RuntimeError):
@@ -67,6 +69,10 @@ def lib():
         L.cn_options_default.restype = None
         L.cn_geometry.argtypes = [C.c_int32, _P_I32, _P_I32, _P_F64, _P_F64, _P_F64, _P_F64, _P_F64]
         L.cn_geometry.restype = st
+        L.cn_plan_layout.argtypes = [C.c_int32, _P_I32, _P_I32, C.c_int32, _P_I32, _P_I32, _P_I32, _P_I32, _P_I32]
+        L.cn_plan_layout.restype = st
+        L.cn_get_mapping.argtypes = [C.c_void_p, _P_I32, _P_I32, _P_I32, C.POINTER(C.c_float)]
+        L.cn_get_mapping.restype = st
         L.cn_model_create.argtypes = [C.POINTER(cn_morph), C.POINTER(cn_mech_table), C.c_int32,
                                       C.POINTER(cn_options), C.POINTER(C.c_void_p)]
         L.cn_model_create.restype = st
@@ -153,6 +159,17 @@ def cn_geometry(cell_offset, parent, dx, diam, Ra):
     return area, ri
 
 
+def cn_plan_layout(cell_offset, parent, mapping=0):
+    """Lane, warp row and topology flags of every node under `mapping` (host only)."""
+    off, par = _i32(cell_offset), _i32(parent)
+    n = par.shape[0]
+    lane, row, flags = np.empty(n, np.int32), np.empty(n, np.int32), np.empty(n, np.int32)
+    nw, depth = np.zeros(1, np.int32), np.zeros(1, np.int32)
+    _check(lib().cn_plan_layout(len(off) - 1, _p(off, _P_I32), _p(par, _P_I32), int(mapping), _p(lane, _P_I32),
+                                _p(row, _P_I32), _p(flags, _P_I32), _p(nw, _P_I32), _p(depth, _P_I32)))
+    return {"lane": lane, "row": row, "flags": flags, "n_warps": int(nw[0]), "stack_depth": int(depth[0])}
+
+
 def _device_tree_args(offset, parent, a, b, d, rhs, device):
     import torch
     dev = torch.device("cuda", device)
@@ -217,7 +234,7 @@ class Model:
 
     def __init__(self, cell_offset, parent, area, cm, ri, spike_node, threshold, mechs,
                  dt=0.025, v_init=-65.0, precision="fp64", device=0, stream=None,
-                 torch_alloc=True, use_graph=True):
+                 torch_alloc=True, use_graph=True, mapping=0, warps_per_block=0):
         L = lib()
         self._keep = []
         k = self._keep
@@ -239,6 +256,8 @@ class Model:
         opt.precision = PRECISION[precision]
         opt.device = int(device)
         opt.use_graph = int(bool(use_graph))
+        opt.mapping = int(mapping)
+        opt.warps_per_block = int(warps_per_block)
         if stream is not None:
             opt.stream = int(stream)
         if torch_alloc:
@@ -325,6 +344,13 @@ class Model:
     def cn_profile(self, enable=True):
         _check(lib().cn_profile(self._h, int(bool(enable))), self._h)
 
+    def cn_get_mapping(self):
+        """(mapping, warps per block, warps, autotuner's interval ms) of the layout in use."""
+        mp, w, nw = np.zeros(1, np.int32), np.zeros(1, np.int32), np.zeros(1, np.int32)
+        ms = C.c_float(0.0)
+        _check(lib().cn_get_mapping(self._h, _p(mp, _P_I32), _p(w, _P_I32), _p(nw, _P_I32), C.byref(ms)), self._h)
+        return int(mp[0]), int(w[0]), int(nw[0]), float(ms.value)
+
     def cn_profile_read(self):
         """(interval-kernel ms, launches, pull-kernel ms, launches) since the last read."""
         a, b, c, d = C.c_double(), C.c_int64(), C.c_double(), C.c_int64()
@@ -360,13 +386,13 @@ class Model:
 
 
 def from_scenario(sc, precision="fp64", device=0, stream=None, record=True, torch_alloc=True,
-                  use_graph=True) -> Model:
+                  use_graph=True, mapping=0, warps_per_block=0) -> Model:
     """Build a Model from a scenarios.Scenario through the C ABI calls."""
     area, ri = cn_geometry(sc.cell_offset, sc.parent, sc.dx, sc.diam, sc.Ra)
     mechs = [(m.kind, m.node, m.param_matrix()) for m in sc.mechs if m.n > 0]
     md = Model(sc.cell_offset, sc.parent, area, sc.cm, ri, sc.spike_node, sc.threshold, mechs,
                dt=sc.dt, v_init=sc.v_init, precision=precision, device=device, stream=stream,
-               torch_alloc=torch_alloc, use_graph=use_graph)
+               torch_alloc=torch_alloc, use_graph=use_graph, mapping=mapping, warps_per_block=warps_per_block)
     if len(sc.netcon_src):
         md.cn_add_netcons(sc.netcon_src, sc.netcon_syn, sc.netcon_w, sc.netcon_delay)
     if len(sc.ev_syn):

@@ -32,13 +32,37 @@ struct EvRec {
   double w;       // uS
 };
 
-// Per-row flag word: mechanism slot (low 16 bits, kNoSlot if none), "far"
-// bit (the parent is not the previous row), count of far children.
-constexpr int32_t kNoSlot = 0xffff;
-constexpr int32_t kFarBit = 1 << 16;
-constexpr int kNFarShift = 17;      // 4 bits: far children of the row
-constexpr int32_t kNFarMask = 15;
-constexpr int32_t kHasPasBit = 1 << 21;
+// Per-row flag word: mechanism slot, "far" bit (the in-lane parent is not the
+// previous row), count of far children, and the cross-lane links of cells
+// split over several lanes.
+// Bits: 0-11 slot, 12 far, 13-15 far children, 16 pas, 17 real row (not
+// padding), 18 junction (a part of the same cell hangs from this row), 19-23
+// the lane holding that part, 24 part root (the parent is in another lane),
+// 25-29 the lane holding the parent.
+constexpr int kMaxWarpsPerBlock = 4;  // warps (groups) per block of the interval kernel
+constexpr int32_t kNoSlot = 0xfff;
+constexpr int32_t kFarBit = 1 << 12;
+constexpr int kNFarShift = 13;
+constexpr int32_t kNFarMask = 7;
+constexpr int32_t kHasPasBit = 1 << 16;
+constexpr int32_t kRealBit = 1 << 17;
+constexpr int32_t kJuncBit = 1 << 18;
+constexpr int kJsrcShift = 19;
+constexpr int32_t kProotBit = 1 << 24;
+constexpr int kPsrcShift = 25;
+
+// Channel types of the batched workload (CN_MECH_NA3H .. CN_MECH_KCA), their
+// gate-state arrays and their per-cell kinetic parameters (the table columns
+// after gbar).  Offsets into the kinetics block per type:
+constexpr int kChanTypes = 6;    // NA3H KDR4 KA IH CAHVA KCA
+constexpr int kChanGates = 9;    // m h | n | a b | q | m h | c
+constexpr int kChanParams = 60;  // 13 + 7 + 13 + 7 + 16 + 4
+__host__ __device__ constexpr int chan_gate0(int t) {
+  return t == 0 ? 0 : t == 1 ? 2 : t == 2 ? 3 : t == 3 ? 5 : t == 4 ? 6 : t == 5 ? 8 : kChanGates;
+}
+__host__ __device__ constexpr int chan_kin0(int t) {
+  return t == 0 ? 0 : t == 1 ? 13 : t == 2 ? 20 : t == 3 ? 33 : t == 4 ? 40 : t == 5 ? 56 : kChanParams;
+}
 
 // Plain-old-data view of a model's device buffers, passed by value.
 struct DevModel {
@@ -46,6 +70,8 @@ struct DevModel {
   int32_t max_slots, stack_depth;
   int64_t node_elems;
   double dt;
+  int64_t smem_warp;           // dynamic shared memory of one warp (multiple of 16 bytes)
+  int64_t* jdev;               // current interval index (advanced by k_next_interval)
   // per group
   const int64_t* g_node_base;  // element index of row 0, lane 0 (multiple of 64)
   const int32_t* g_rows;       // rows (even)
@@ -102,6 +128,15 @@ struct DevModel {
   double* pas_e;            // per row
   double* cdt;              // per row: 1e-3 cm/dt
   double* dax;              // per row: axial part of the unscaled diagonal
+  // dense channel types of the batched workload (present on every row of a
+  // cell): per-group presence mask, per-row scaled gbar and gate states,
+  // per-lane kinetics [kChanParams][n_slots], per-row calcium and ica
+  const int32_t* g_chmask;
+  double* ch_gbar[kChanTypes];
+  void* ch_gate[kChanGates];
+  const double* ch_kin;
+  double* cai;
+  double* ica;
   // adjoint trajectory (recompute only)
   double* traj_v;           // [step - traj_k0][node_elems]
   double* traj_g;           // [step - traj_k0][3][hh_elems]
@@ -148,9 +183,9 @@ __host__ __device__ inline size_t ring_bytes() {
   const size_t back = (size_t)kBackRows * kLanes * (2 * sizeof(double) + sizeof(int32_t));
   return ((elim > back ? elim : back) + 15) / 16 * 16;
 }
-__host__ __device__ inline size_t interval_smem_bytes(int stack_depth, int max_slots) {
+__host__ __device__ inline size_t interval_smem_bytes(int stack_depth, int max_slots, bool dense) {
   return ring_bytes() + (size_t)stack_depth * kLanes * 3 * sizeof(double) +
-         (size_t)max_slots * kLanes * 2 * sizeof(double);
+         (size_t)max_slots * kLanes * 2 * sizeof(double) + (dense ? (size_t)kChanParams * kLanes * sizeof(double) : 0);
 }
 
 // Per-thread asynchronous global->shared copies (through L1, so a lane's own

@@ -22,8 +22,20 @@ thread_local std::string g_create_error;
 int64_t round_half_away(double x) { return (int64_t)std::llround(x); }
 
 const int kNParams[CN_MECH_NTYPES] = {2, 6, 2, 14, 8, 14, 8, 17, 5};
+constexpr int kMaxSmemPerBlock = 227 * 1024;  // opt-in dynamic shared memory per block
 
 }  // namespace
+
+// One captured chunk of whole intervals (see replay_chunk).
+struct GraphChunk {
+  cudaGraphExec_t exec = nullptr;
+  std::vector<cudaEvent_t> ev;   // profiling: pull start/end, interval start/end per interval
+  bool pending = false;          // events recorded but not read yet
+  const void* key_hist = nullptr;
+  const void* key_trace = nullptr;
+  bool key_prof = false;
+  int key_wpb = 0;
+};
 
 struct cn_model {
   cn_options opt{};
@@ -38,6 +50,10 @@ struct cn_model {
   std::vector<double> area, cm, ri, thresh;
   std::vector<int32_t> pas_node, hh_node, syn_node;
   std::vector<double> pas_g, pas_e, hh_par, syn_tau, syn_e;
+  // dense channel tables (types CN_MECH_NA3H .. CN_MECH_KCA)
+  std::vector<int32_t> ch_node[cn::kChanTypes];
+  std::vector<double> ch_par[cn::kChanTypes];  // [n_params][n]
+  bool dense = false;
   std::vector<int32_t> nc_src, nc_syn;
   std::vector<double> nc_w, nc_delay;
   std::vector<int32_t> ev_syn;
@@ -46,7 +62,9 @@ struct cn_model {
   std::vector<double> st_del, st_dur, st_amp;
   std::vector<int32_t> rec_node;
   std::vector<int32_t> node_cell;
-  std::vector<int32_t> node_row;   // global node -> row inside its cell
+  std::vector<int32_t> node_row;   // global node -> warp row of its lane
+  std::vector<int32_t> node_slot;  // global node -> lane (slot) holding it
+  std::vector<int32_t> slot_cell;  // lane -> cell (-1 when empty)
   size_t smem_bytes = 0;
   std::vector<int64_t> x_pos0;     // initial external-event cursors
   // adjoint checkpoints: state at steps 0, S, 2S, ...
@@ -72,6 +90,14 @@ struct cn_model {
   bool profiling = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_interval, ev_pull;
   std::vector<cudaEvent_t> ev_pool;
+  double acc_int_ms = 0.0, acc_pull_ms = 0.0;
+  int64_t acc_int_n = 0, acc_pull_n = 0;
+  // launch shape and graph replay
+  int wpb = 1;                        // warps (groups) per block of the interval kernel
+  cudaStream_t cap_stream = nullptr;  // private stream for graph capture
+  GraphChunk gchunk[2];
+  int gnext = 0;
+  float tuned_ms = 0.f;               // autotuner: time of one interval with the chosen shape
 
   cn_status fail(cn_status s, const std::string& msg) {
     err = msg;
@@ -152,7 +178,7 @@ Rows interleave(const cn_model* m, const std::vector<int32_t>& inst_node) {
   r.inst_slot.resize(inst_node.size());
   r.inst_q.resize(inst_node.size());
   for (size_t i = 0; i < inst_node.size(); ++i) {
-    int s = m->cell_slot[m->node_cell[inst_node[i]]];
+    int s = m->node_slot[inst_node[i]];
     r.inst_slot[i] = s;
     r.inst_q[i] = r.slot_n[s]++;
   }
@@ -188,73 +214,288 @@ cn_status state_init(cn_model* m) {
   cudaStream_t st = m->stream;
   double v0 = m->opt.v_init_mV;
   switch (m->opt.precision) {
-    case CN_PREC_FP64: return launch_checked(m, [&] { cn::k_state_init<0><<<nb, tb, 0, st>>>(dm, v0); });
-    case CN_PREC_GATE_FP32: return launch_checked(m, [&] { cn::k_state_init<1><<<nb, tb, 0, st>>>(dm, v0); });
-    default: return launch_checked(m, [&] { cn::k_state_init<2><<<nb, tb, 0, st>>>(dm, v0); });
+    case CN_PREC_FP64:
+      CN_CHECK(launch_checked(m, [&] { cn::k_state_init<0><<<nb, tb, 0, st>>>(dm, v0); }));
+      if (m->dense) CN_CHECK(launch_checked(m, [&] { cn::k_setup_dense<0><<<nb, tb, 0, st>>>(dm, v0, false); }));
+      return CN_OK;
+    case CN_PREC_GATE_FP32:
+      CN_CHECK(launch_checked(m, [&] { cn::k_state_init<1><<<nb, tb, 0, st>>>(dm, v0); }));
+      if (m->dense) CN_CHECK(launch_checked(m, [&] { cn::k_setup_dense<1><<<nb, tb, 0, st>>>(dm, v0, false); }));
+      return CN_OK;
+    default:
+      CN_CHECK(launch_checked(m, [&] { cn::k_state_init<2><<<nb, tb, 0, st>>>(dm, v0); }));
+      if (m->dense) CN_CHECK(launch_checked(m, [&] { cn::k_setup_dense<2><<<nb, tb, 0, st>>>(dm, v0, false); }));
+      return CN_OK;
   }
 }
 
-// Depth-first preorder of one cell that visits the smaller child subtree
-// first.  Returns row_of[local] and, per row, the parent row and flags
-// (far bit, far-children count); also the far-stack depths needed by
-// elimination (descending rows) and back substitution (ascending rows).
-struct CellOrder {
-  std::vector<int32_t> row_of, prow, nfar;
-  std::vector<uint8_t> far;
-  int depth = 1;
+// Split plan and row order of one cell.  The cell (local nodes 0..n-1,
+// parent[i] < i) is cut into parts (subtrees) that go to different lanes of
+// one warp: part 0 holds the root; every other part hangs from a "junction"
+// node of its parent part.  A part whose junction is at row r of a parent
+// part placed at warp row B starts at warp row B + r + 1, so its root is
+// eliminated one warp row before the junction row and back-substituted one
+// row after it.  Rows of a part follow a depth-first preorder that visits
+// children leading to junctions first, then smaller subtrees first; a row's
+// in-part parent is then the previous row except for "far" children, whose
+// contributions nest last-in-first-out on a per-lane stack.
+struct CellPart {
+  int root = 0;          // local node
+  int parent_part = -1;
+  int jnode = -1;        // local node (in the parent part) the root hangs from
+  int base = 0;          // warp row of the part's first row
+  std::vector<int32_t> nodes;  // local nodes in row order
 };
 
-CellOrder order_cell(const int32_t* parent, int n) {
-  CellOrder o;
-  std::vector<int32_t> size(n, 1), head(n, -1), next(n, -1);
-  for (int i = n - 1; i > 0; --i) size[parent[i]] += size[i];
-  // children lists sorted by (subtree size, index), built by insertion
-  for (int i = n - 1; i > 0; --i) {
-    int p = parent[i];
-    int* link = &head[p];
-    while (*link >= 0 && (size[*link] < size[i] || (size[*link] == size[i] && *link < i))) link = &next[*link];
-    next[i] = *link;
-    *link = i;
+struct CellPlan {
+  std::vector<CellPart> parts;
+  std::vector<int32_t> part_of, row_of;  // per local node: part, row within the part
+  std::vector<uint8_t> far;              // per local node
+  std::vector<int32_t> nfar;             // per local node (in-part far children)
+  int depth = 1;                         // far-stack depth needed
+  int span = 0;                          // max over parts of base + size
+};
+
+// Warp row of each part's first row: a part starts one row after the row of
+// its junction node in the parent part.  Re-parenting during the split can
+// give a part a parent with a larger index, so bases follow the part tree,
+// not the index order.
+std::vector<int> part_bases(const std::vector<CellPart>& parts, const std::vector<int32_t>& row) {
+  std::vector<int> base(parts.size(), -1);
+  base[0] = 0;
+  for (size_t q0 = 1; q0 < parts.size(); ++q0) {
+    std::vector<int> chain;
+    int q = (int)q0;
+    while (base[q] < 0) {
+      chain.push_back(q);
+      q = parts[q].parent_part;
+    }
+    for (auto it = chain.rbegin(); it != chain.rend(); ++it)
+      base[*it] = base[parts[*it].parent_part] + row[parts[*it].jnode] + 1;
   }
-  o.row_of.assign(n, -1);
-  o.prow.assign(n, -1);
-  o.nfar.assign(n, 0);
-  o.far.assign(n, 0);
-  std::vector<int32_t> stack{0};
-  int row = 0;
-  while (!stack.empty()) {
-    int u = stack.back();
-    stack.pop_back();
-    o.row_of[u] = row++;
-    // push children in reverse so the smallest subtree is visited first
-    std::vector<int32_t> ch;
-    for (int c = head[u]; c >= 0; c = next[c]) ch.push_back(c);
-    for (auto it = ch.rbegin(); it != ch.rend(); ++it) stack.push_back(*it);
+  return base;
+}
+
+CellPlan plan_cell(const int32_t* parent, int n, int target) {
+  CellPlan P;
+  std::vector<std::vector<int32_t>> ch(n);
+  for (int i = 1; i < n; ++i) ch[parent[i]].push_back(i);
+  P.part_of.assign(n, 0);
+  P.parts.push_back(CellPart{});
+  std::vector<int32_t> child_part_at(n, -1);  // junction node -> child part
+  const int want = target > 0 ? std::min(32, std::max(1, (n + target - 1) / target)) : 1;
+  std::vector<int32_t> sub(n), dep(n);
+  while ((int)P.parts.size() < want) {
+    // in-part subtree sizes and depths
+    for (int i = n - 1; i >= 0; --i) {
+      sub[i] = 1;
+      for (int c : ch[i])
+        if (P.part_of[c] == P.part_of[i]) sub[i] += sub[c];
+    }
+    std::vector<int> psize(P.parts.size(), 0);
+    for (int i = 0; i < n; ++i) {
+      psize[P.part_of[i]]++;
+      const int q = P.part_of[i];
+      dep[i] = (i == P.parts[q].root) ? 0 : dep[parent[i]] + 1;
+    }
+    // estimated bases: a child part starts at its junction depth + 1
+    const std::vector<int> base = part_bases(P.parts, dep);
+    int worst = 0;
+    for (size_t q = 1; q < P.parts.size(); ++q)
+      if (base[q] + psize[q] > base[worst] + psize[worst]) worst = (int)q;
+    const int cur = base[worst] + psize[worst];
+    int best_c = -1, best = cur;
+    for (int c = 0; c < n; ++c) {
+      if (P.part_of[c] != worst || c == P.parts[worst].root || child_part_at[parent[c]] >= 0) continue;
+      const int cost = std::max(base[worst] + psize[worst] - sub[c], base[worst] + dep[c] + sub[c]);
+      if (cost < best) {
+        best = cost;
+        best_c = c;
+      }
+    }
+    if (best_c < 0 || best >= cur) break;
+    CellPart np_;
+    np_.root = best_c;
+    np_.parent_part = worst;
+    np_.jnode = parent[best_c];
+    const int nq = (int)P.parts.size();
+    P.parts.push_back(np_);
+    child_part_at[parent[best_c]] = nq;
+    // move the in-part subtree of best_c (and re-parent child parts hanging inside it)
+    std::vector<int32_t> st{best_c};
+    while (!st.empty()) {
+      int u = st.back();
+      st.pop_back();
+      P.part_of[u] = nq;
+      for (int c : ch[u])
+        if (P.part_of[c] == worst) st.push_back(c);
+    }
+    for (size_t q = 1; q < P.parts.size(); ++q)
+      if (P.part_of[P.parts[q].jnode] == nq && (int)q != nq) P.parts[q].parent_part = nq;
   }
-  std::vector<int32_t> local_of(n);
-  for (int i = 0; i < n; ++i) local_of[o.row_of[i]] = i;
-  for (int r = 1; r < n; ++r) {
-    int pr = o.row_of[parent[local_of[r]]];
-    o.prow[r] = pr;
-    if (pr != r - 1) {
-      o.far[r] = 1;
-      o.nfar[pr]++;
+  // row order inside every part
+  for (int i = n - 1; i >= 0; --i) {
+    sub[i] = 1;
+    for (int c : ch[i])
+      if (P.part_of[c] == P.part_of[i]) sub[i] += sub[c];
+  }
+  std::vector<uint8_t> leads(n, 0);  // in-part subtree contains a junction node
+  for (int i = n - 1; i >= 0; --i) {
+    if (child_part_at[i] >= 0) leads[i] = 1;
+    for (int c : ch[i])
+      if (P.part_of[c] == P.part_of[i] && leads[c]) leads[i] = 1;
+  }
+  P.row_of.assign(n, -1);
+  P.far.assign(n, 0);
+  P.nfar.assign(n, 0);
+  for (size_t q = 0; q < P.parts.size(); ++q) {
+    CellPart& pt = P.parts[q];
+    std::vector<int32_t> st{pt.root};
+    while (!st.empty()) {
+      int u = st.back();
+      st.pop_back();
+      P.row_of[u] = (int)pt.nodes.size();
+      pt.nodes.push_back(u);
+      std::vector<int32_t> cc;
+      for (int c : ch[u])
+        if (P.part_of[c] == (int)q) cc.push_back(c);
+      std::stable_sort(cc.begin(), cc.end(), [&](int x, int y) {
+        if (leads[x] != leads[y]) return leads[x] > leads[y];
+        return sub[x] < sub[y];
+      });
+      for (auto it = cc.rbegin(); it != cc.rend(); ++it) st.push_back(*it);
+    }
+    // far flags and stack depth of this part
+    const int sz = (int)pt.nodes.size();
+    for (int r = 1; r < sz; ++r) {
+      const int u = pt.nodes[r];
+      if (P.row_of[parent[u]] != r - 1) {
+        P.far[u] = 1;
+        P.nfar[parent[u]]++;
+      }
+    }
+    int top = 0, mx = 0;
+    for (int r = sz - 1; r >= 0; --r) {
+      top -= P.nfar[pt.nodes[r]];
+      if (r > 0 && P.far[pt.nodes[r]]) mx = std::max(mx, ++top);
+    }
+    top = P.nfar[pt.nodes[0]];
+    mx = std::max(mx, top);
+    for (int r = 1; r < sz; ++r) {
+      if (P.far[pt.nodes[r]]) --top;
+      top += P.nfar[pt.nodes[r]];
+      mx = std::max(mx, top);
+    }
+    P.depth = std::max(P.depth, mx);
+  }
+  const std::vector<int> base = part_bases(P.parts, P.row_of);
+  for (size_t q = 0; q < P.parts.size(); ++q) P.parts[q].base = base[q];
+  for (const CellPart& pt : P.parts) P.span = std::max(P.span, pt.base + (int)pt.nodes.size());
+  return P;
+}
+
+// Target span (rows per lane) of a mapping value; 0 = never split.
+int map_target(int32_t mapping, int64_t n_nodes, int32_t n_cells, bool adjoint) {
+  if (mapping >= 16) return mapping;
+  if (mapping == CN_MAP_AUTO && !adjoint && n_cells > 0)
+    return (int)std::max<int64_t>(16, (n_nodes + n_cells - 1) / n_cells);
+  return 0;
+}
+
+// Checks cell_offset / parent as cn_morph requires.
+bool valid_trees(int32_t n_cells, const int32_t* off, const int32_t* parent, std::string& err) {
+  if (n_cells < 0 || !off || off[0] != 0) {
+    err = "bad cell_offset";
+    return false;
+  }
+  for (int c = 0; c < n_cells; ++c) {
+    if (off[c + 1] <= off[c]) {
+      err = "every cell needs at least one node";
+      return false;
+    }
+    for (int64_t i = off[c]; i < off[c + 1]; ++i) {
+      const int64_t li = i - off[c];
+      const int32_t p = parent[i];
+      if ((li == 0) != (p == -1) || p >= li || p < -1) {
+        err = "parent must be cell-local with parent[i] < i and one root at local index 0";
+        return false;
+      }
     }
   }
-  int top = 0, mx = 0;
-  for (int r = n - 1; r >= 0; --r) {  // elimination
-    top -= o.nfar[r];
-    if (r > 0 && o.far[r]) mx = std::max(mx, ++top);
+  return true;
+}
+
+// Placement of every cell on the lanes of the warps: cells are grouped by
+// channel set (a warp runs one set), then by part count and span, largest
+// first; a cell's parts take consecutive lanes of one warp.  node_flags holds
+// each node's topology bits (real, far, nfar, part root with its parent's
+// lane, junction with its child's lane); the mechanism-slot field is left 0.
+struct Layout {
+  std::vector<CellPlan> plans;
+  int depth = 1;
+  int n_groups = 0;
+  std::vector<int32_t> cell_lane0;            // cell -> first lane (global)
+  std::vector<int32_t> node_slot, node_row;   // global node -> lane, warp row
+  std::vector<int32_t> node_flags;            // global node -> topology bits
+};
+
+bool build_layout(int32_t n_cells, const int32_t* off, const int32_t* parent, const int32_t* cell_mask,
+                  int target, Layout& L, std::string& err) {
+  auto mask = [&](int c) { return cell_mask ? cell_mask[c] : 0; };
+  L.plans.assign(n_cells, CellPlan{});
+  L.depth = 1;
+  for (int c = 0; c < n_cells; ++c) {
+    const int n = off[c + 1] - off[c];
+    L.plans[c] = plan_cell(parent + off[c], n, target);
+    L.depth = std::max(L.depth, L.plans[c].depth);
+    for (int32_t li = 0; li < n; ++li)
+      if (L.plans[c].nfar[li] > (int)cn::kNFarMask) {
+        err = "a node has more than 8 children";
+        return false;
+      }
   }
-  top = o.nfar[0];
-  mx = std::max(mx, top);
-  for (int r = 1; r < n; ++r) {  // back substitution
-    if (o.far[r]) --top;
-    top += o.nfar[r];
-    mx = std::max(mx, top);
+  std::vector<int32_t> order(n_cells);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    if (mask(x) != mask(y)) return mask(x) < mask(y);
+    if (L.plans[x].parts.size() != L.plans[y].parts.size()) return L.plans[x].parts.size() > L.plans[y].parts.size();
+    return L.plans[x].span > L.plans[y].span;
+  });
+  L.cell_lane0.assign(n_cells, -1);
+  int fill = 0, ng = 0;
+  int32_t prev_mask = -1;
+  for (int c : order) {
+    const int P = (int)L.plans[c].parts.size();
+    if (ng == 0 || fill + P > cn::kLanes || mask(c) != prev_mask) {
+      ++ng;
+      fill = 0;
+    }
+    prev_mask = mask(c);
+    L.cell_lane0[c] = (ng - 1) * cn::kLanes + fill;
+    fill += P;
   }
-  o.depth = std::max(1, mx);
-  return o;
+  L.n_groups = ng;
+  const int64_t nn = off[n_cells];
+  L.node_slot.assign(nn, 0);
+  L.node_row.assign(nn, 0);
+  L.node_flags.assign(nn, 0);
+  for (int c = 0; c < n_cells; ++c) {
+    const CellPlan& P = L.plans[c];
+    const int l0 = L.cell_lane0[c];
+    for (int32_t li = 0; li < off[c + 1] - off[c]; ++li) {
+      const int64_t node = off[c] + li;
+      const int q = P.part_of[li];
+      L.node_slot[node] = l0 + q;
+      L.node_row[node] = P.parts[q].base + P.row_of[li];
+      int32_t f = cn::kRealBit | (P.far[li] ? cn::kFarBit : 0) | (P.nfar[li] << cn::kNFarShift);
+      if (q > 0 && li == P.parts[q].root)
+        f |= cn::kProotBit | ((l0 + P.parts[q].parent_part) % cn::kLanes) << cn::kPsrcShift;
+      for (size_t q2 = 1; q2 < P.parts.size(); ++q2)
+        if (P.parts[q2].jnode == li) f |= cn::kJuncBit | ((l0 + (int)q2) % cn::kLanes) << cn::kJsrcShift;
+      L.node_flags[node] = f;
+    }
+  }
+  return true;
 }
 
 cn_status finalize(cn_model* m) {
@@ -272,63 +513,88 @@ cn_status finalize(cn_model* m) {
   }
   m->D = (int32_t)(dmin == 0 ? cn::kMaxInterval : std::min<int64_t>(dmin, cn::kMaxInterval));
 
-  // cells sorted by size (largest first), 32 per warp
-  std::vector<int32_t> order(m->n_cells);
-  std::iota(order.begin(), order.end(), 0);
-  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-    return (m->off[x + 1] - m->off[x]) > (m->off[y + 1] - m->off[y]);
-  });
-  m->n_groups = (m->n_cells + cn::kLanes - 1) / cn::kLanes;
-  m->n_slots = m->n_groups * cn::kLanes;
-  m->cell_slot.assign(m->n_cells, -1);
-  std::vector<int32_t> slot_gid(m->n_slots, -1), slot_rows(m->n_slots, 0), slot_spike(m->n_slots, 0);
-  std::vector<double> slot_thresh(m->n_slots, 0.0);
-  // per-cell row order
-  m->node_row.assign(m->n_nodes, 0);
-  std::vector<int32_t> row_prow(m->n_nodes), row_flag(m->n_nodes);  // by global (cell offset + row)
-  int depth = 1;
-  for (int c = 0; c < m->n_cells; ++c) {
-    const int n = m->off[c + 1] - m->off[c];
-    CellOrder o = order_cell(m->parent.data() + m->off[c], n);
-    depth = std::max(depth, o.depth);
-    for (int li = 0; li < n; ++li) m->node_row[m->off[c] + li] = o.row_of[li];
-    for (int r = 0; r < n; ++r) {
-      row_prow[m->off[c] + r] = o.prow[r];
-      if (o.nfar[r] > 15) return m->fail(CN_EINVAL, "a node has more than 16 children");
-      row_flag[m->off[c] + r] = cn::kNoSlot | (o.far[r] ? cn::kFarBit : 0) | (o.nfar[r] << cn::kNFarShift);
+  // dense channel types: per-cell presence mask and per-cell kinetics (every
+  // column after gbar must be uniform within a cell for this mapping)
+  std::vector<int32_t> cell_mask(m->n_cells, 0);
+  std::vector<double> cell_kin;
+  if (m->dense) {
+    cell_kin.assign((size_t)cn::kChanParams * m->n_cells, 0.0);
+    for (int t = 0; t < cn::kChanTypes; ++t) {
+      const auto& nodes = m->ch_node[t];
+      const int np = kNParams[CN_MECH_NA3H + t];
+      const size_t n = nodes.size();
+      std::vector<int32_t> first(m->n_cells, -1);
+      std::vector<uint8_t> seen_node(m->n_nodes, 0);
+      for (size_t i = 0; i < n; ++i) {
+        if (seen_node[nodes[i]]++) return m->fail(CN_EINVAL, "two instances of one channel type on one node");
+        const int c = m->node_cell[nodes[i]];
+        if (first[c] < 0) {
+          first[c] = (int32_t)i;
+          cell_mask[c] |= 1 << t;
+          for (int q = 1; q < np; ++q)
+            cell_kin[(size_t)(cn::chan_kin0(t) + q - 1) * m->n_cells + c] = m->ch_par[t][(size_t)q * n + i];
+        } else {
+          for (int q = 1; q < np; ++q)
+            if (m->ch_par[t][(size_t)q * n + i] != m->ch_par[t][(size_t)q * n + first[c]])
+              return m->fail(CN_EINVAL, "channel kinetics must be uniform within a cell (only gbar may vary)");
+        }
+      }
     }
   }
-  for (int r = 0; r < m->n_cells; ++r) {
-    int c = order[r];
-    m->cell_slot[c] = r;
-    slot_gid[r] = c;
-    slot_rows[r] = m->off[c + 1] - m->off[c];
-    slot_spike[r] = m->node_row[m->off[c] + m->spike_node[c]];
-    slot_thresh[r] = m->thresh[c];
+  // split plans (no split when the adjoint is on or the mapping asks for
+  // one cell per lane); target span = mean cell size unless given
+  const int target = map_target(m->opt.mapping, m->n_nodes, m->n_cells, m->ck_steps > 0);
+  Layout L;
+  {
+    std::string lerr;
+    if (!build_layout(m->n_cells, m->off.data(), m->parent.data(), cell_mask.data(), target, L, lerr))
+      return m->fail(CN_EINVAL, lerr);
   }
+  const int depth = L.depth;
+  m->n_groups = L.n_groups;
+  m->n_slots = L.n_groups * cn::kLanes;
+  m->cell_slot = L.cell_lane0;
+  m->node_row = L.node_row;
+  m->node_slot = L.node_slot;
+  std::vector<int32_t> slot_gid(m->n_slots, -1), slot_rows(m->n_slots, 0), slot_spike(m->n_slots, 0),
+      slot_cell(m->n_slots, -1);
+  std::vector<double> slot_thresh(m->n_slots, 0.0);
+  for (int c = 0; c < m->n_cells; ++c) {
+    const CellPlan& P = L.plans[c];
+    for (size_t q = 0; q < P.parts.size(); ++q) {
+      const int sl = L.cell_lane0[c] + (int)q;
+      slot_cell[sl] = c;
+      slot_rows[sl] = P.parts[q].base + (int)P.parts[q].nodes.size();
+    }
+    const int64_t sn = m->off[c] + m->spike_node[c];
+    const int ss = m->node_slot[sn];
+    slot_gid[ss] = c;
+    slot_spike[ss] = m->node_row[sn];
+    slot_thresh[ss] = m->thresh[c];
+  }
+  m->slot_cell = slot_cell;
   std::vector<int32_t> g_rows(m->n_groups, 0);
   m->g_node_base.assign(m->n_groups, 0);
   for (int s = 0; s < m->n_slots; ++s) g_rows[s / cn::kLanes] = std::max(g_rows[s / cn::kLanes], slot_rows[s]);
   int64_t acc = 0;
   for (int g = 0; g < m->n_groups; ++g) {
-    g_rows[g] += g_rows[g] & 1;  // even: rows stream in pairs
+    g_rows[g] += g_rows[g] & 1;
     m->g_node_base[g] = acc;
     acc += (int64_t)g_rows[g] * cn::kLanes;
   }
   m->node_elems = acc;
-  auto row_elem = [&](int c, int row) {
-    int s = m->cell_slot[c];
-    return m->g_node_base[s / cn::kLanes] + (int64_t)row * cn::kLanes + s % cn::kLanes;
+  auto node_elem = [&](int64_t node) {
+    const int s = m->node_slot[node];
+    return m->g_node_base[s / cn::kLanes] + (int64_t)m->node_row[node] * cn::kLanes + s % cn::kLanes;
   };
-  auto node_elem = [&](int64_t node) { return row_elem(m->node_cell[node], m->node_row[node]); };
-  // mechanism slots: distinct rows carrying a point process or channel, per cell
-  std::vector<std::vector<int32_t>> cell_slot_rows(m->n_cells);
+  // mechanism slots: distinct rows carrying a point process, per lane
+  std::vector<std::vector<int32_t>> lane_slot_rows(m->n_slots);
   std::vector<int32_t> row_slot(m->n_nodes, -1);  // by global node
   auto slot_of_node = [&](int64_t node) {
     if (row_slot[node] < 0) {
-      int c = m->node_cell[node];
-      row_slot[node] = (int32_t)cell_slot_rows[c].size();
-      cell_slot_rows[c].push_back(m->node_row[node]);
+      const int sl = m->node_slot[node];
+      row_slot[node] = (int32_t)lane_slot_rows[sl].size();
+      lane_slot_rows[sl].push_back(m->node_row[node]);
     }
     return row_slot[node];
   };
@@ -337,29 +603,21 @@ cn_status finalize(cn_model* m) {
   for (size_t i = 0; i < m->hh_node.size(); ++i) hh_slotid[i] = slot_of_node(m->hh_node[i]);
   for (size_t i = 0; i < m->st_node.size(); ++i) st_slotid[i] = slot_of_node(m->st_node[i]);
   int max_slots = 1;
-  for (int c = 0; c < m->n_cells; ++c) max_slots = std::max<int>(max_slots, (int)cell_slot_rows[c].size());
-  if (max_slots >= cn::kNoSlot) return m->fail(CN_EINVAL, "too many mechanism rows in one cell");
-  const size_t smem = cn::interval_smem_bytes(depth, max_slots);
-  if (smem > 227 * 1024)
+  for (int sl = 0; sl < m->n_slots; ++sl) max_slots = std::max<int>(max_slots, (int)lane_slot_rows[sl].size());
+  if (max_slots >= cn::kNoSlot) return m->fail(CN_EINVAL, "too many mechanism rows in one cell part");
+  const size_t smem = cn::interval_smem_bytes(depth, max_slots, m->dense);
+  if (smem > kMaxSmemPerBlock)
     return m->fail(CN_EINVAL, "cell needs " + std::to_string(smem) + " bytes of shared memory (slots " +
                                   std::to_string(max_slots) + ", stack " + std::to_string(depth) + ")");
   m->smem_bytes = smem;
-  // per-row inputs, interleaved
-  std::vector<double> h_area(acc, 1.0), h_ri(acc, 1.0), h_cm(acc, 1.0), h_gp(acc, 0.0), h_ep(acc, 0.0);
-  std::vector<int32_t> h_prow(acc, -1), h_flags(acc, cn::kNoSlot);
-  for (int c = 0; c < m->n_cells; ++c) {
-    for (int32_t li = 0; li < m->off[c + 1] - m->off[c]; ++li) {
-      int64_t node = m->off[c] + li;
-      int row = m->node_row[node];
-      int64_t e = row_elem(c, row);
-      h_area[e] = m->area[node];
-      h_ri[e] = m->ri[node];
-      h_cm[e] = m->cm[node];
-      h_prow[e] = row_prow[m->off[c] + row];
-      int32_t f = row_flag[m->off[c] + row];
-      if (row_slot[node] >= 0) f = (f & ~cn::kNoSlot) | row_slot[node];
-      h_flags[e] = f;
-    }
+  // per-row flags (interleaved) and per-node geometry (node order)
+  std::vector<double> h_gp(acc, 0.0), h_ep(acc, 0.0);
+  std::vector<int32_t> h_flags(acc, cn::kNoSlot);
+  std::vector<int64_t> h_elem(m->n_nodes);
+  for (int64_t node = 0; node < m->n_nodes; ++node) {
+    const int64_t e = node_elem(node);
+    h_elem[node] = e;
+    h_flags[e] = L.node_flags[node] | (row_slot[node] >= 0 ? row_slot[node] : cn::kNoSlot);
   }
   for (size_t q = 0; q < m->pas_node.size(); ++q) {
     int64_t e = node_elem(m->pas_node[q]);
@@ -370,7 +628,7 @@ cn_status finalize(cn_model* m) {
   // slot rows, interleaved
   std::vector<int32_t> slot_n(m->n_slots, 0), g_slot_rows(m->n_groups, 0);
   std::vector<int64_t> g_slot_base(m->n_groups, 0);
-  for (int c = 0; c < m->n_cells; ++c) slot_n[m->cell_slot[c]] = (int32_t)cell_slot_rows[c].size();
+  for (int sl = 0; sl < m->n_slots; ++sl) slot_n[sl] = (int32_t)lane_slot_rows[sl].size();
   for (int s = 0; s < m->n_slots; ++s) g_slot_rows[s / cn::kLanes] = std::max(g_slot_rows[s / cn::kLanes], slot_n[s]);
   int64_t sacc = 0;
   for (int g = 0; g < m->n_groups; ++g) {
@@ -378,11 +636,9 @@ cn_status finalize(cn_model* m) {
     sacc += (int64_t)g_slot_rows[g] * cn::kLanes;
   }
   std::vector<int32_t> h_slot_row(std::max<int64_t>(sacc, 1), 0);
-  for (int c = 0; c < m->n_cells; ++c) {
-    int s = m->cell_slot[c];
-    for (size_t t = 0; t < cell_slot_rows[c].size(); ++t)
-      h_slot_row[g_slot_base[s / cn::kLanes] + (int64_t)t * cn::kLanes + s % cn::kLanes] = cell_slot_rows[c][t];
-  }
+  for (int sl = 0; sl < m->n_slots; ++sl)
+    for (size_t t = 0; t < lane_slot_rows[sl].size(); ++t)
+      h_slot_row[g_slot_base[sl / cn::kLanes] + (int64_t)t * cn::kLanes + sl % cn::kLanes] = lane_slot_rows[sl][t];
   // synapses, HH, stimuli, records
   Rows rs = interleave(m, m->syn_node), rh = interleave(m, m->hh_node), rt = interleave(m, m->st_node),
        rr = interleave(m, m->rec_node);
@@ -482,6 +738,7 @@ cn_status finalize(cn_model* m) {
 
   // ---- upload
   dm = cn::DevModel{};
+  m->gate_bytes = m->opt.precision == CN_PREC_FP64 ? 8 : (m->opt.precision == CN_PREC_GATE_FP32 ? 4 : 2);
   dm.n_groups = m->n_groups;
   dm.n_slots = m->n_slots;
   dm.n_cells = m->n_cells;
@@ -534,7 +791,6 @@ cn_status finalize(cn_model* m) {
   CN_CHECK(zeros(m, &pd, rs.elems)); dm.syn_decay = pd;
   CN_CHECK(upload(m, &p32, h_hh_slot)); dm.hh_slot = p32;
   CN_CHECK(upload(m, &p32, h_hh_row)); dm.hh_row = p32;
-  m->gate_bytes = m->opt.precision == CN_PREC_FP64 ? 8 : (m->opt.precision == CN_PREC_GATE_FP32 ? 4 : 2);
   for (void** gp : {&dm.hh_m, &dm.hh_h, &dm.hh_n}) {
     void* q = dalloc_raw(m, std::max<int64_t>(rh.elems, 1) * m->gate_bytes);
     if (!q) return m->fail(CN_ENOMEM, "device allocation failed");
@@ -548,6 +804,38 @@ cn_status finalize(cn_model* m) {
   CN_CHECK(upload(m, &pd, h_ep)); dm.pas_e = pd;
   CN_CHECK(zeros(m, &pd, acc)); dm.cdt = pd;
   CN_CHECK(zeros(m, &pd, acc)); dm.dax = pd;
+  if (m->dense) {
+    std::vector<int32_t> g_mask(m->n_groups, 0);
+    std::vector<double> h_kin((size_t)cn::kChanParams * m->n_slots, 0.0);
+    for (int sl = 0; sl < m->n_slots; ++sl) {
+      const int c = m->slot_cell[sl];
+      if (c < 0) continue;
+      g_mask[sl / cn::kLanes] |= cell_mask[c];
+      for (int q = 0; q < cn::kChanParams; ++q)
+        h_kin[(size_t)q * m->n_slots + sl] = cell_kin[(size_t)q * m->n_cells + c];
+    }
+    CN_CHECK(upload(m, &p32, g_mask)); dm.g_chmask = p32;
+    CN_CHECK(upload(m, &pd, h_kin)); dm.ch_kin = pd;
+    bool need_ca = false;
+    for (int t = 0; t < cn::kChanTypes; ++t) {
+      if (m->ch_node[t].empty()) continue;
+      if (t >= 4) need_ca = true;
+      std::vector<double> h_g(acc, 0.0);
+      for (size_t i = 0; i < m->ch_node[t].size(); ++i) h_g[node_elem(m->ch_node[t][i])] = m->ch_par[t][i];
+      CN_CHECK(upload(m, &pd, h_g)); dm.ch_gbar[t] = pd;
+      const int g0 = cn::chan_gate0(t), g1 = t + 1 < cn::kChanTypes ? cn::chan_gate0(t + 1) : cn::kChanGates;
+      for (int gi = g0; gi < g1; ++gi) {
+        void* q = dalloc_raw(m, (size_t)acc * m->gate_bytes);
+        if (!q) return m->fail(CN_ENOMEM, "device allocation failed");
+        CN_TRY_CUDA(m, cudaMemsetAsync(q, 0, (size_t)acc * m->gate_bytes, m->stream));
+        dm.ch_gate[gi] = q;
+      }
+    }
+    if (need_ca) {
+      CN_CHECK(zeros(m, &pd, acc)); dm.cai = pd;
+      CN_CHECK(zeros(m, &pd, acc)); dm.ica = pd;
+    }
+  }
   CN_CHECK(upload(m, &p32, h_st_slot)); dm.st_slot = p32;
   CN_CHECK(upload(m, &pd, h_st_del)); dm.st_del = pd;
   CN_CHECK(upload(m, &pd, h_st_dur)); dm.st_dur = pd;
@@ -570,16 +858,21 @@ cn_status finalize(cn_model* m) {
   CN_CHECK(upload(m, &p32, h_in_ds)); dm.in_dsteps = p32;
   CN_CHECK(upload(m, &pd, h_in_w)); dm.in_w = pd;
   CN_CHECK(zeros(m, &p32, 1)); dm.status = p32;
+  CN_CHECK(zeros(m, &p64, 1)); dm.jdev = p64;
+  dm.smem_warp = (int64_t)m->smem_bytes;
   dm.hist = nullptr;
   dm.trace = nullptr;
 
   // temporaries for the setup kernels
   double *d_area, *d_ri, *d_cm, *d_syn_area, *d_syn_cm, *d_syn_tau, *d_st_amp, *d_st_area, *d_st_cm;
-  int32_t* d_prow;
-  CN_CHECK(upload(m, &d_area, h_area));
-  CN_CHECK(upload(m, &d_ri, h_ri));
-  CN_CHECK(upload(m, &d_cm, h_cm));
-  CN_CHECK(upload(m, &d_prow, h_prow));
+  int32_t *d_parent, *d_off;
+  int64_t* d_elem;
+  CN_CHECK(upload(m, &d_area, m->area));
+  CN_CHECK(upload(m, &d_ri, m->ri));
+  CN_CHECK(upload(m, &d_cm, m->cm));
+  CN_CHECK(upload(m, &d_parent, m->parent));
+  CN_CHECK(upload(m, &d_off, m->off));
+  CN_CHECK(upload(m, &d_elem, h_elem));
   CN_CHECK(upload(m, &d_syn_area, h_syn_area));
   CN_CHECK(upload(m, &d_syn_cm, h_syn_cm));
   CN_CHECK(upload(m, &d_syn_tau, h_syn_tau));
@@ -588,20 +881,35 @@ cn_status finalize(cn_model* m) {
   CN_CHECK(upload(m, &d_st_cm, h_st_cm));
   const int tb = 128, nb = (m->n_slots + tb - 1) / tb;
   cudaStream_t st = m->stream;
-  CN_CHECK(launch_checked(m, [&] { cn::k_setup_nodes<<<nb, tb, 0, st>>>(dm, d_area, d_ri, d_cm, d_prow); }));
+  const int nbe = (int)((acc + 255) / 256), nbc = (m->n_cells + tb - 1) / tb;
+  CN_CHECK(launch_checked(m, [&] { cn::k_setup_pad<<<nbe, 256, 0, st>>>(dm); }));
+  CN_CHECK(launch_checked(m, [&] { cn::k_setup_geom<<<nbc, tb, 0, st>>>(dm, m->n_cells, d_off, d_parent, d_area, d_ri, d_cm, d_elem); }));
   CN_CHECK(launch_checked(m, [&] { cn::k_pas_apply<<<nb, tb, 0, st>>>(dm); }));
   CN_CHECK(launch_checked(m, [&] { cn::k_setup_slots<<<nb, tb, 0, st>>>(dm); }));
   CN_CHECK(launch_checked(m, [&] { cn::k_setup_syn<<<nb, tb, 0, st>>>(dm, d_syn_area, d_syn_cm, d_syn_tau); }));
   CN_CHECK(launch_checked(m, [&] { cn::k_hh_params<<<nb, tb, 0, st>>>(dm); }));
   CN_CHECK(launch_checked(m, [&] { cn::k_setup_stim<<<nb, tb, 0, st>>>(dm, d_st_amp, d_st_area, d_st_cm); }));
+  if (m->dense) {
+    const double v0 = m->opt.v_init_mV;
+    switch (m->opt.precision) {
+      case CN_PREC_FP64: CN_CHECK(launch_checked(m, [&] { cn::k_setup_dense<0><<<nb, tb, 0, st>>>(dm, v0, true); })); break;
+      case CN_PREC_GATE_FP32: CN_CHECK(launch_checked(m, [&] { cn::k_setup_dense<1><<<nb, tb, 0, st>>>(dm, v0, true); })); break;
+      default: CN_CHECK(launch_checked(m, [&] { cn::k_setup_dense<2><<<nb, tb, 0, st>>>(dm, v0, true); })); break;
+    }
+  }
   CN_CHECK(state_init(m));
   CN_TRY_CUDA(m, cudaStreamSynchronize(st));
   for (double* p : {d_area, d_ri, d_cm, d_syn_area, d_syn_cm, d_syn_tau, d_st_amp, d_st_area, d_st_cm}) dfree_raw(m, p);
-  dfree_raw(m, d_prow);
+  dfree_raw(m, d_parent);
+  dfree_raw(m, d_off);
+  dfree_raw(m, d_elem);
   m->x_pos0 = x_pos;
-  for (auto fn : {(const void*)cn::k_interval<0, false>, (const void*)cn::k_interval<1, false>,
-                  (const void*)cn::k_interval<2, false>, (const void*)cn::k_interval<0, true>})
-    CN_TRY_CUDA(m, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m->smem_bytes));
+  for (auto fn : {(const void*)cn::k_interval<0, false, false>, (const void*)cn::k_interval<1, false, false>,
+                  (const void*)cn::k_interval<2, false, false>, (const void*)cn::k_interval<0, true, false>,
+                  (const void*)cn::k_interval<0, false, true>, (const void*)cn::k_interval<1, false, true>,
+                  (const void*)cn::k_interval<2, false, true>})
+    CN_TRY_CUDA(m, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemPerBlock));
+  m->wpb = std::max(1, std::min<int>(m->wpb, (int)(kMaxSmemPerBlock / m->smem_bytes)));
   m->finalized = true;
   m->cells_nodes = m->n_nodes;
   return CN_OK;
@@ -656,48 +964,241 @@ cudaEvent_t take_event(cn_model* m) {
   return e;
 }
 
-cn_status launch_interval(cn_model* m, int64_t J, int s0, int s1) {
+// Queue one interval (steps [s0, s1) of interval J) on stream st: the event
+// pull at the interval start, the interval kernel, and the device-side
+// interval index bump once the interval is complete.  ev, when given, holds
+// four events recorded around the pull and the interval kernel.
+cn_status enqueue_interval(cn_model* m, cudaStream_t st, int64_t J, int s0, int s1, cudaEvent_t* ev) {
   cn::DevModel dm = m->dm;
-  cudaStream_t st = m->stream;
-  const int wpb = 1;
+  const int64_t* Jp = dm.jdev;
+  const int wpb = m->wpb;
   const int blocks = (m->n_groups + wpb - 1) / wpb;
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  const size_t smem = (size_t)wpb * m->smem_bytes;
   if (s0 == 0) {
     const int tb = 128, nb = (m->n_slots + tb - 1) / tb;
-    if (m->profiling) {
-      e0 = take_event(m);
-      e1 = take_event(m);
-      CN_TRY_CUDA(m, cudaEventRecord(e0, st));
-    }
-    CN_CHECK(launch_checked(m, [&] { cn::k_pull_events<<<nb, tb, 0, st>>>(dm, J); }));
-    if (m->profiling) {
-      CN_TRY_CUDA(m, cudaEventRecord(e1, st));
-      m->ev_pull.emplace_back(e0, e1);
-    }
+    if (ev) CN_TRY_CUDA(m, cudaEventRecord(ev[0], st));
+    CN_CHECK(launch_checked(m, [&] { cn::k_pull_events<<<nb, tb, 0, st>>>(dm, J, Jp); }));
+    if (ev) CN_TRY_CUDA(m, cudaEventRecord(ev[1], st));
   }
-  if (m->profiling) {
-    e0 = take_event(m);
-    e1 = take_event(m);
-    CN_TRY_CUDA(m, cudaEventRecord(e0, st));
-  }
+  if (ev) CN_TRY_CUDA(m, cudaEventRecord(ev[2], st));
   switch (m->opt.precision) {
     case CN_PREC_FP64:
-      CN_CHECK(launch_checked(m, [&] { cn::k_interval<0, false><<<blocks, 32 * wpb, m->smem_bytes, st>>>(dm, J, s0, s1); }));
+      if (m->dense) CN_CHECK(launch_checked(m, [&] { cn::k_interval<0, false, true><<<blocks, 32 * wpb, smem, st>>>(dm, J, s0, s1, Jp); }));
+      else CN_CHECK(launch_checked(m, [&] { cn::k_interval<0, false, false><<<blocks, 32 * wpb, smem, st>>>(dm, J, s0, s1, Jp); }));
       break;
     case CN_PREC_GATE_FP32:
-      CN_CHECK(launch_checked(m, [&] { cn::k_interval<1, false><<<blocks, 32 * wpb, m->smem_bytes, st>>>(dm, J, s0, s1); }));
+      if (m->dense) CN_CHECK(launch_checked(m, [&] { cn::k_interval<1, false, true><<<blocks, 32 * wpb, smem, st>>>(dm, J, s0, s1, Jp); }));
+      else CN_CHECK(launch_checked(m, [&] { cn::k_interval<1, false, false><<<blocks, 32 * wpb, smem, st>>>(dm, J, s0, s1, Jp); }));
       break;
     default:
-      CN_CHECK(launch_checked(m, [&] { cn::k_interval<2, false><<<blocks, 32 * wpb, m->smem_bytes, st>>>(dm, J, s0, s1); }));
+      if (m->dense) CN_CHECK(launch_checked(m, [&] { cn::k_interval<2, false, true><<<blocks, 32 * wpb, smem, st>>>(dm, J, s0, s1, Jp); }));
+      else CN_CHECK(launch_checked(m, [&] { cn::k_interval<2, false, false><<<blocks, 32 * wpb, smem, st>>>(dm, J, s0, s1, Jp); }));
       break;
   }
-  if (m->profiling) {
-    CN_TRY_CUDA(m, cudaEventRecord(e1, st));
-    m->ev_interval.emplace_back(e0, e1);
-  }
+  if (ev) CN_TRY_CUDA(m, cudaEventRecord(ev[3], st));
+  if (s1 == m->D) CN_CHECK(launch_checked(m, [&] { cn::k_next_interval<<<1, 1, 0, st>>>(dm.jdev); }));
   return CN_OK;
 }
 
+// Direct launch of one interval on the model's stream (events from the pool
+// when profiling).
+cn_status launch_interval(cn_model* m, int64_t J, int s0, int s1) {
+  if (!m->profiling) return enqueue_interval(m, m->stream, J, s0, s1, nullptr);
+  cudaEvent_t ev[4];
+  for (auto& e : ev) e = take_event(m);
+  CN_CHECK(enqueue_interval(m, m->stream, J, s0, s1, ev));
+  if (s0 == 0) m->ev_pull.emplace_back(ev[0], ev[1]);
+  else {
+    m->ev_pool.push_back(ev[0]);
+    m->ev_pool.push_back(ev[1]);
+  }
+  m->ev_interval.emplace_back(ev[2], ev[3]);
+  return CN_OK;
+}
+
+// ---- CUDA graph replay of whole intervals.  A chunk of kGraphIntervals
+// complete intervals is captured once (the interval index lives on the
+// device, so the same graph serves every chunk) and replayed on the model's
+// stream.  Two chunk graphs alternate so that, when profiling, the events of
+// one can be read while the other runs.
+constexpr int kGraphIntervals = 8;
+
+cn_status fold_chunk_events(cn_model* m, int c) {
+  GraphChunk& g = m->gchunk[c];
+  if (!g.pending) return CN_OK;
+  CN_TRY_CUDA(m, cudaEventSynchronize(g.ev.back()));
+  for (size_t i = 0; i + 3 < g.ev.size(); i += 4) {
+    float a = 0.f, b = 0.f;
+    CN_TRY_CUDA(m, cudaEventElapsedTime(&a, g.ev[i], g.ev[i + 1]));
+    CN_TRY_CUDA(m, cudaEventElapsedTime(&b, g.ev[i + 2], g.ev[i + 3]));
+    m->acc_pull_ms += a;
+    m->acc_int_ms += b;
+    m->acc_pull_n++;
+    m->acc_int_n++;
+  }
+  g.pending = false;
+  return CN_OK;
+}
+
+void drop_graphs(cn_model* m) {
+  for (GraphChunk& g : m->gchunk) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    for (cudaEvent_t e : g.ev) cudaEventDestroy(e);
+    g = GraphChunk{};
+  }
+}
+
+cn_status capture_chunk(cn_model* m, int c) {
+  GraphChunk& g = m->gchunk[c];
+  if (!m->cap_stream) CN_TRY_CUDA(m, cudaStreamCreateWithFlags(&m->cap_stream, cudaStreamNonBlocking));
+  if (m->profiling && g.ev.empty()) {
+    g.ev.resize(4 * kGraphIntervals);
+    for (auto& e : g.ev) CN_TRY_CUDA(m, cudaEventCreate(&e));
+  }
+  cudaGraph_t graph = nullptr;
+  CN_TRY_CUDA(m, cudaStreamBeginCapture(m->cap_stream, cudaStreamCaptureModeThreadLocal));
+  cn_status st = CN_OK;
+  const int64_t launches = m->launches;
+  for (int i = 0; i < kGraphIntervals && st == CN_OK; ++i)
+    st = enqueue_interval(m, m->cap_stream, 0, 0, m->D, m->profiling ? g.ev.data() + 4 * i : nullptr);
+  m->launches = launches;  // captured, not launched
+  cudaError_t e = cudaStreamEndCapture(m->cap_stream, &graph);
+  if (st != CN_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  CN_TRY_CUDA(m, e);
+  e = cudaGraphInstantiate(&g.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  CN_TRY_CUDA(m, e);
+  g.key_hist = m->dm.hist;
+  g.key_trace = m->dm.trace;
+  g.key_prof = m->profiling;
+  g.key_wpb = m->wpb;
+  return CN_OK;
+}
+
+// Replays one chunk of kGraphIntervals complete intervals.
+cn_status replay_chunk(cn_model* m) {
+  const int c = m->gnext;
+  m->gnext ^= 1;
+  GraphChunk& g = m->gchunk[c];
+  CN_CHECK(fold_chunk_events(m, c));
+  if (g.exec && (g.key_hist != m->dm.hist || g.key_trace != m->dm.trace || g.key_prof != m->profiling ||
+                 g.key_wpb != m->wpb)) {
+    cudaGraphExecDestroy(g.exec);
+    g.exec = nullptr;
+  }
+  if (!g.exec) CN_CHECK(capture_chunk(m, c));
+  CN_TRY_CUDA(m, cudaGraphLaunch(g.exec, m->stream));
+  // the graph's kernels: per interval the pull, the interval kernel and the bump
+  m->launches += 3 * kGraphIntervals;
+  g.pending = m->profiling;
+  return CN_OK;
+}
+
+
+// Back to step 0: initial state, event cursors, spike history, interval
+// index, status word and the step-0 trace sample.
+cn_status reset_state(cn_model* m) {
+  CN_CHECK(state_init(m));
+  if (!m->x_pos0.empty())
+    CN_TRY_CUDA(m, cudaMemcpyAsync(m->dm.x_pos, m->x_pos0.data(), m->x_pos0.size() * sizeof(int64_t),
+                                   cudaMemcpyHostToDevice, m->stream));
+  if (m->dm.hist) CN_TRY_CUDA(m, cudaMemsetAsync(m->dm.hist, 0, (size_t)m->hist_cap * m->n_cells * 8, m->stream));
+  CN_TRY_CUDA(m, cudaMemsetAsync(m->dm.status, 0, sizeof(int32_t), m->stream));
+  CN_TRY_CUDA(m, cudaMemsetAsync(m->dm.jdev, 0, sizeof(int64_t), m->stream));
+  m->step = 0;
+  if (m->dm.trace) {
+    const int tb = 128, nb = (m->n_slots + tb - 1) / tb;
+    cn::DevModel dm = m->dm;
+    CN_CHECK(launch_checked(m, [&] { cn::k_record0<<<nb, tb, 0, m->stream>>>(dm, 0); }));
+  }
+  CN_TRY_CUDA(m, cudaStreamSynchronize(m->stream));
+  return CN_OK;
+}
+
+// Frees every device buffer of the model and forgets the layout, so that
+// finalize can lay the model out again (used by the autotuner).
+cn_status release_device(cn_model* m) {
+  CN_TRY_CUDA(m, cudaStreamSynchronize(m->stream));
+  drop_graphs(m);
+  for (auto* v : {&m->ev_interval, &m->ev_pull})
+    for (auto& pr : *v) {
+      m->ev_pool.push_back(pr.first);
+      m->ev_pool.push_back(pr.second);
+    }
+  m->ev_interval.clear();
+  m->ev_pull.clear();
+  std::vector<void*> all = m->allocs;
+  for (void* p : all) dfree_raw(m, p);
+  m->ck_buf.clear();
+  m->dm = cn::DevModel{};
+  m->finalized = false;
+  m->hist_cap = m->trace_cap = 0;
+  m->step = 0;
+  m->acc_int_ms = m->acc_pull_ms = 0.0;
+  m->acc_int_n = m->acc_pull_n = 0;
+  return CN_OK;
+}
+
+// Mapping autotuner: lays the model out for each candidate target span (one
+// cell per lane, and spans of 1/4, 1/2, 1 and 2 mean cell sizes), and for
+// each runs one warm-up and one timed interval from the initial state with
+// 1, 2 and 4 warps per block; keeps the fastest and lays the model out
+// again with it.  Results do not depend on the choice beyond rounding.
+cn_status autotune(cn_model* m) {
+  const int64_t mean = std::max<int64_t>(1, (m->n_nodes + m->n_cells - 1) / std::max(1, m->n_cells));
+  std::vector<int32_t> cand{CN_MAP_THREAD};
+  if (m->ck_steps <= 0)
+    for (int64_t t : {mean / 4, mean / 2, mean, 2 * mean}) {
+      const int32_t v = (int32_t)std::max<int64_t>(16, t);
+      if (v < mean * 4 && std::find(cand.begin(), cand.end(), v) == cand.end()) cand.push_back(v);
+    }
+  float best = 0.f;
+  int32_t best_map = CN_MAP_THREAD, best_wpb = 1;
+  const bool prof = m->profiling;
+  m->profiling = false;
+  cudaEvent_t e0 = take_event(m), e1 = take_event(m);
+  for (int32_t c : cand) {
+    m->opt.mapping = c;
+    CN_CHECK(finalize(m));
+    CN_CHECK(ensure_capacity(m, 2 * (int64_t)m->D));
+    for (int w = 1; w <= cn::kMaxWarpsPerBlock; w *= 2) {
+      if ((size_t)w * m->smem_bytes > (size_t)kMaxSmemPerBlock) break;
+      m->wpb = w;
+      CN_CHECK(reset_state(m));
+      CN_CHECK(enqueue_interval(m, m->stream, 0, 0, m->D, nullptr));
+      CN_TRY_CUDA(m, cudaEventRecord(e0, m->stream));
+      CN_CHECK(enqueue_interval(m, m->stream, 1, 0, m->D, nullptr));
+      CN_TRY_CUDA(m, cudaEventRecord(e1, m->stream));
+      CN_TRY_CUDA(m, cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CN_TRY_CUDA(m, cudaEventElapsedTime(&ms, e0, e1));
+      if (best == 0.f || ms < best) {
+        best = ms;
+        best_map = c;
+        best_wpb = w;
+      }
+    }
+    CN_CHECK(release_device(m));
+  }
+  m->ev_pool.push_back(e0);
+  m->ev_pool.push_back(e1);
+  m->profiling = prof;
+  m->opt.mapping = best_map;
+  m->wpb = best_wpb;
+  m->tuned_ms = best;
+  m->launches = 0;
+  return finalize(m);
+}
+
+// Lays the model out on first use (through the autotuner when asked).
+cn_status prepare(cn_model* m) {
+  if (m->finalized) return CN_OK;
+  if (m->opt.mapping == CN_MAP_TUNE) return autotune(m);
+  return finalize(m);
+}
 
 // State snapshot (v, HH gates, synaptic g) into / out of a device buffer.
 size_t snapshot_bytes(const cn_model* m) {
@@ -729,8 +1230,12 @@ cn_status advance(cn_model* m, int64_t K, bool traj) {
     if (traj) {
       cn::DevModel dm = m->dm;
       CN_CHECK(launch_checked(m, [&] {
-        cn::k_interval<0, true><<<m->n_groups, 32, m->smem_bytes, m->stream>>>(dm, J, s0, s1);
+        cn::k_interval<0, true, false><<<m->n_groups, 32, m->smem_bytes, m->stream>>>(dm, J, s0, s1, nullptr);
       }));
+    } else if (m->opt.use_graph && s0 == 0 && K - m->step >= (int64_t)kGraphIntervals * m->D) {
+      CN_CHECK(replay_chunk(m));
+      m->step += (int64_t)kGraphIntervals * m->D;
+      continue;
     } else {
       CN_CHECK(launch_interval(m, J, s0, s1));
     }
@@ -783,6 +1288,40 @@ cn_status cn_geometry(int32_t n_cells, const int32_t* cell_offset, const int32_t
   return CN_OK;
 }
 
+cn_status cn_get_mapping(cn_model* m, int32_t* mapping, int32_t* warps_per_block, int32_t* n_warps,
+                         float* tuned_interval_ms) {
+  if (!m) return CN_EINVAL;
+  CN_TRY_CUDA(m, cudaSetDevice(m->opt.device));
+  CN_CHECK(prepare(m));
+  if (mapping) *mapping = m->opt.mapping;
+  if (warps_per_block) *warps_per_block = m->wpb;
+  if (n_warps) *n_warps = m->n_groups;
+  if (tuned_interval_ms) *tuned_interval_ms = m->tuned_ms;
+  return CN_OK;
+}
+
+cn_status cn_plan_layout(int32_t n_cells, const int32_t* cell_offset, const int32_t* parent, int32_t mapping,
+                         int32_t* node_lane, int32_t* node_row, int32_t* node_flags, int32_t* n_warps,
+                         int32_t* stack_depth) {
+  g_create_error.clear();
+  if (n_cells < 0 || !cell_offset || (n_cells > 0 && !parent)) {
+    g_create_error = "null argument";
+    return CN_EINVAL;
+  }
+  if (!valid_trees(n_cells, cell_offset, parent, g_create_error)) return CN_EINVAL;
+  const int64_t nn = cell_offset[n_cells];
+  Layout L;
+  if (!build_layout(n_cells, cell_offset, parent, nullptr, map_target(mapping, nn, n_cells, false), L,
+                    g_create_error))
+    return CN_EINVAL;
+  if (node_lane) std::copy(L.node_slot.begin(), L.node_slot.end(), node_lane);
+  if (node_row) std::copy(L.node_row.begin(), L.node_row.end(), node_row);
+  if (node_flags) std::copy(L.node_flags.begin(), L.node_flags.end(), node_flags);
+  if (n_warps) *n_warps = L.n_groups;
+  if (stack_depth) *stack_depth = L.depth;
+  return CN_OK;
+}
+
 cn_status cn_model_create(const cn_morph* morph, const cn_mech_table* mechs, int32_t n_mechs,
                           const cn_options* opt, cn_model** out) {
   g_create_error.clear();
@@ -798,6 +1337,8 @@ cn_status cn_model_create(const cn_morph* morph, const cn_mech_table* mechs, int
   if (!(o.dt_ms > 0) || !std::isfinite(o.v_init_mV)) return bad("bad dt or v_init");
   if (o.precision < 0 || o.precision > 2) return bad("bad precision");
   if ((o.alloc == nullptr) != (o.free == nullptr)) return bad("alloc and free must be given together");
+  if (o.warps_per_block < 0 || o.warps_per_block > cn::kMaxWarpsPerBlock) return bad("warps_per_block must be 0..4");
+  if (o.mapping < 0 || (o.mapping > CN_MAP_TUNE && o.mapping < 16)) return bad("mapping must be 0, 1, 2 or >= 16");
   const int32_t nc = morph->n_cells;
   if (nc <= 0 || !morph->cell_offset || !morph->parent || !morph->area_um2 || !morph->cm_uF_cm2 ||
       !morph->ri_MOhm || !morph->spike_node || !morph->threshold_mV)
@@ -824,6 +1365,7 @@ cn_status cn_model_create(const cn_morph* morph, const cn_mech_table* mechs, int
     return CN_ENOMEM;
   }
   m->opt = o;
+  m->wpb = std::max(1, o.warps_per_block);
   m->stream = static_cast<cudaStream_t>(o.stream);
   m->n_cells = nc;
   m->n_nodes = nn;
@@ -870,8 +1412,13 @@ cn_status cn_model_create(const cn_morph* morph, const cn_mech_table* mechs, int
         m->syn_tau.assign(mt.param, mt.param + mt.n);
         m->syn_e.assign(mt.param + mt.n, mt.param + 2 * (int64_t)mt.n);
         break;
-      default:
-        if (mt.n > 0) { delete m; return bad("mechanism type not supported by this mapping"); }
+      default: {
+        const int t = mt.type - CN_MECH_NA3H;
+        m->ch_node[t].assign(mt.node, mt.node + mt.n);
+        m->ch_par[t].assign(mt.param, mt.param + (int64_t)np * mt.n);
+        if (mt.n > 0) m->dense = true;
+        break;
+      }
     }
   }
   cudaError_t e = cudaSetDevice(o.device);
@@ -948,7 +1495,7 @@ cn_status cn_run(cn_model* m, double tstop_ms) {
   const int64_t K = round_half_away(tstop_ms / m->opt.dt_ms);
   if (K < m->step) return m->fail(CN_EINVAL, "tstop is behind the current time");
   CN_TRY_CUDA(m, cudaSetDevice(m->opt.device));
-  if (!m->finalized) CN_CHECK(finalize(m));
+  CN_CHECK(prepare(m));
   CN_CHECK(ensure_capacity(m, K));
   if (m->ck_steps <= 0) return advance(m, K, false);
   // with adjoint checkpoints: snapshot the state at every multiple of S
@@ -1041,8 +1588,7 @@ cn_status cn_get_v(cn_model* m, double* out, size_t cap) {
   std::vector<double> h(m->node_elems);
   CN_TRY_CUDA(m, cudaMemcpy(h.data(), m->dm.v, h.size() * sizeof(double), cudaMemcpyDeviceToHost));
   for (int64_t i = 0; i < m->n_nodes; ++i) {
-    int c = m->node_cell[i];
-    int s = m->cell_slot[c];
+    const int s = m->node_slot[i];
     out[i] = h[m->g_node_base[s / cn::kLanes] + (int64_t)m->node_row[i] * cn::kLanes + s % cn::kLanes];
   }
   return CN_OK;
@@ -1086,6 +1632,25 @@ cn_status cn_get_state(cn_model* m, int32_t type, int32_t col, double* out, size
     }
     return CN_OK;
   }
+  if (type >= CN_MECH_NA3H && type <= CN_MECH_KCA) {
+    const int t = type - CN_MECH_NA3H;
+    const int ngates = (t + 1 < cn::kChanTypes ? cn::chan_gate0(t + 1) : cn::kChanGates) - cn::chan_gate0(t);
+    const size_t n = m->ch_node[t].size();
+    if (cap < n) return m->fail(CN_ERANGE, "buffer too small");
+    const bool want_cai = type == CN_MECH_CAHVA && col == ngates;
+    if (col < 0 || (col >= ngates && !want_cai)) return m->fail(CN_EINVAL, "no such state column");
+    const void* src = want_cai ? (const void*)m->dm.cai : m->dm.ch_gate[cn::chan_gate0(t) + col];
+    const int bytes = want_cai ? 8 : m->gate_bytes;
+    std::vector<uint8_t> h((size_t)m->node_elems * bytes);
+    CN_TRY_CUDA(m, cudaMemcpy(h.data(), src, h.size(), cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < n; ++i) {
+      const int32_t node = m->ch_node[t][i];
+      const int sl = m->node_slot[node];
+      const int64_t e = m->g_node_base[sl / cn::kLanes] + (int64_t)m->node_row[node] * cn::kLanes + sl % cn::kLanes;
+      out[i] = gate_to_double(h.data(), e, bytes);
+    }
+    return CN_OK;
+  }
   return m->fail(CN_EINVAL, "no such state column");
 }
 
@@ -1099,22 +1664,28 @@ cn_status cn_profile_read(cn_model* m, double* interval_ms, int64_t* interval_la
                           int64_t* pull_launches) {
   if (!m) return CN_EINVAL;
   CN_TRY_CUDA(m, cudaStreamSynchronize(m->stream));
-  auto sum = [&](std::vector<std::pair<cudaEvent_t, cudaEvent_t>>& v, double* ms, int64_t* cnt) -> cn_status {
-    double t = 0.0;
+  auto sum = [&](std::vector<std::pair<cudaEvent_t, cudaEvent_t>>& v, double& ms, int64_t& cnt) -> cn_status {
     for (auto& pr : v) {
       float x = 0.f;
       CN_TRY_CUDA(m, cudaEventElapsedTime(&x, pr.first, pr.second));
-      t += x;
+      ms += x;
+      ++cnt;
       m->ev_pool.push_back(pr.first);
       m->ev_pool.push_back(pr.second);
     }
-    if (ms) *ms = t;
-    if (cnt) *cnt = (int64_t)v.size();
     v.clear();
     return CN_OK;
   };
-  CN_CHECK(sum(m->ev_interval, interval_ms, interval_launches));
-  CN_CHECK(sum(m->ev_pull, pull_ms, pull_launches));
+  CN_CHECK(sum(m->ev_interval, m->acc_int_ms, m->acc_int_n));
+  CN_CHECK(sum(m->ev_pull, m->acc_pull_ms, m->acc_pull_n));
+  CN_CHECK(fold_chunk_events(m, 0));
+  CN_CHECK(fold_chunk_events(m, 1));
+  if (interval_ms) *interval_ms = m->acc_int_ms;
+  if (interval_launches) *interval_launches = m->acc_int_n;
+  if (pull_ms) *pull_ms = m->acc_pull_ms;
+  if (pull_launches) *pull_launches = m->acc_pull_n;
+  m->acc_int_ms = m->acc_pull_ms = 0.0;
+  m->acc_int_n = m->acc_pull_n = 0;
   return CN_OK;
 }
 
@@ -1122,35 +1693,22 @@ cn_status cn_reset(cn_model* m) {
   if (!m) return CN_EINVAL;
   if (!m->finalized) return CN_OK;
   CN_TRY_CUDA(m, cudaSetDevice(m->opt.device));
-  CN_CHECK(state_init(m));
-  if (!m->x_pos0.empty())
-    CN_TRY_CUDA(m, cudaMemcpyAsync(m->dm.x_pos, m->x_pos0.data(), m->x_pos0.size() * sizeof(int64_t),
-                                   cudaMemcpyHostToDevice, m->stream));
-  if (m->dm.hist) CN_TRY_CUDA(m, cudaMemsetAsync(m->dm.hist, 0, (size_t)m->hist_cap * m->n_cells * 8, m->stream));
-  CN_TRY_CUDA(m, cudaMemsetAsync(m->dm.status, 0, sizeof(int32_t), m->stream));
-  m->step = 0;
-  if (m->dm.trace) {
-    const int tb = 128, nb = (m->n_slots + tb - 1) / tb;
-    cn::DevModel dm = m->dm;
-    CN_CHECK(launch_checked(m, [&] { cn::k_record0<<<nb, tb, 0, m->stream>>>(dm, 0); }));
-  }
-  CN_TRY_CUDA(m, cudaStreamSynchronize(m->stream));
-  return CN_OK;
+  return reset_state(m);
 }
 
 static cn_status cell_values_to_slots(cn_model* m, const double* values, double** d_out) {
   std::vector<double> h(m->n_slots, 0.0);
-  for (int c = 0; c < m->n_cells; ++c) {
+  for (int c = 0; c < m->n_cells; ++c)
     if (!std::isfinite(values[c])) return m->fail(CN_EINVAL, "non-finite parameter value");
-    h[m->cell_slot[c]] = values[c];
-  }
+  for (int sl = 0; sl < m->n_slots; ++sl)
+    if (m->slot_cell[sl] >= 0) h[sl] = values[m->slot_cell[sl]];
   return upload(m, d_out, h);
 }
 
 cn_status cn_set_cell_param(cn_model* m, int32_t param, const double* values) {
   if (!m || !values || param < 0 || param > 2) return m ? m->fail(CN_EINVAL, "bad parameter id") : CN_EINVAL;
   CN_TRY_CUDA(m, cudaSetDevice(m->opt.device));
-  if (!m->finalized) CN_CHECK(finalize(m));
+  CN_CHECK(prepare(m));
   CN_CHECK(ensure_capacity(m, m->step));
   double* d = nullptr;
   CN_CHECK(cell_values_to_slots(m, values, &d));
@@ -1168,7 +1726,7 @@ cn_status cn_set_cell_param(cn_model* m, int32_t param, const double* values) {
 cn_status cn_get_cell_param(cn_model* m, int32_t param, double* values) {
   if (!m || !values || param < 0 || param > 2) return m ? m->fail(CN_EINVAL, "bad parameter id") : CN_EINVAL;
   CN_TRY_CUDA(m, cudaSetDevice(m->opt.device));
-  if (!m->finalized) CN_CHECK(finalize(m));
+  CN_CHECK(prepare(m));
   double* d = nullptr;
   CN_CHECK(zeros(m, &d, m->n_slots));
   const int tb = 128, nb = (m->n_slots + tb - 1) / tb;
@@ -1188,12 +1746,13 @@ cn_status cn_enable_adjoint(cn_model* m, int32_t checkpoint_steps) {
   if (m->opt.precision != CN_PREC_FP64) return m->fail(CN_ESTATE, "the adjoint is defined for the FP64 path");
   if (!m->nc_src.empty() || !m->ev_syn.empty())
     return m->fail(CN_ESTATE, "the adjoint needs a model without NetCons or external events");
+  if (m->dense) return m->fail(CN_ESTATE, "the adjoint covers HH, pas and IClamp models");
   std::vector<int> nh(m->n_cells, 0);
   for (int32_t node : m->hh_node)
     if (++nh[m->node_cell[node]] > 1) return m->fail(CN_EINVAL, "the adjoint supports one HH instance per cell");
   m->ck_steps = checkpoint_steps;
   CN_TRY_CUDA(m, cudaSetDevice(m->opt.device));
-  if (!m->finalized) CN_CHECK(finalize(m));
+  CN_CHECK(prepare(m));
   m->ck_bytes = snapshot_bytes(m);
   return CN_OK;
 }
@@ -1254,8 +1813,10 @@ cn_status cn_run_adjoint(cn_model* m, const double* dj, double* grad) {
   std::vector<double> h_g(3 * (size_t)m->n_slots);
   CN_TRY_CUDA(m, cudaMemcpyAsync(h_g.data(), A.grad, h_g.size() * 8, cudaMemcpyDeviceToHost, m->stream));
   CN_TRY_CUDA(m, cudaStreamSynchronize(m->stream));
-  for (int c = 0; c < m->n_cells; ++c)
-    for (int q = 0; q < 3; ++q) grad[(size_t)q * m->n_cells + c] = h_g[(size_t)q * m->n_slots + m->cell_slot[c]];
+  for (size_t i = 0; i < 3 * (size_t)m->n_cells; ++i) grad[i] = 0.0;
+  for (int sl = 0; sl < m->n_slots; ++sl)
+    if (m->slot_cell[sl] >= 0)
+      for (int q = 0; q < 3; ++q) grad[(size_t)q * m->n_cells + m->slot_cell[sl]] += h_g[(size_t)q * m->n_slots + sl];
   for (void* b : {(void*)A.dj, (void*)A.lam, (void*)A.ytmp, (void*)A.qtmp, (void*)A.xi, (void*)A.grad, (void*)tv,
                   (void*)tg, fin})
     dfree_raw(m, b);
@@ -1275,6 +1836,8 @@ void cn_model_destroy(cn_model* m) {
   for (auto& pr : m->ev_interval) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
   for (auto& pr : m->ev_pull) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
   for (cudaEvent_t e : m->ev_pool) cudaEventDestroy(e);
+  drop_graphs(m);
+  if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
   delete m;
 }
 

@@ -5,38 +5,39 @@
 namespace cn {
 
 // ------------------------------------------------------------------ setup
+// Every element starts as an identity row (padding): cdt 1, no couplings.
+__global__ void k_setup_pad(DevModel M) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= M.node_elems) return;
+  M.cdt[e] = 1.0;
+  M.dax[e] = 0.0;
+  const_cast<double*>(M.a)[e] = 0.0;
+  const_cast<double*>(M.b)[e] = 0.0;
+}
+
 // Geometry part of every row (Eq. 1 discretised on the tree), rows scaled by
 // 1/cdt_i, cdt_i = 1e-3 cm_i/dt:
 //   b_i  = -100/(ri_i area_i) / cdt_i          (row i, column parent)
 //   a_i  = -100/(ri_i area_p) / cdt_p          (row parent, column i)
 //   dax_i = sum of the unscaled axial couplings of row i
-// One thread per cell; prow holds parent rows.  Rows past the cell's end
-// (the group's rows are those of its largest cell) get zero couplings.
-__global__ void k_setup_nodes(DevModel M, const double* area, const double* ri, const double* cm,
-                              const int32_t* prow) {
-  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
-  if (slot >= M.n_slots) return;
-  const int g = slot / kLanes, lane = slot % kLanes;
-  const int N = M.s_rows[slot];
-  const int64_t nb = M.g_node_base[g] + lane;
+// One thread per cell (a cell's parts may sit in different lanes); elem
+// maps a global node to its element.
+__global__ void k_setup_geom(DevModel M, int n_cells, const int32_t* off, const int32_t* parent, const double* area,
+                             const double* ri, const double* cm, const int64_t* elem) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_cells) return;
   double* a = const_cast<double*>(M.a);
   double* b = const_cast<double*>(M.b);
-  for (int j = 0; j < M.g_rows[g]; ++j) {
-    const int64_t i = nb + (int64_t)j * kLanes;
-    M.cdt[i] = j < N ? 1e-3 * cm[i] / M.dt : 1.0;
-    M.dax[i] = 0.0;
-    a[i] = 0.0;
-    b[i] = 0.0;
-  }
-  for (int j = 1; j < N; ++j) {
-    const int64_t i = nb + (int64_t)j * kLanes;
-    const int64_t ip = nb + (int64_t)prow[i] * kLanes;
+  for (int32_t i = off[c]; i < off[c + 1]; ++i) M.cdt[elem[i]] = 1e-3 * cm[i] / M.dt;
+  for (int32_t i = off[c] + 1; i < off[c + 1]; ++i) {
+    const int32_t ip = off[c] + parent[i];
+    const int64_t e = elem[i], ep = elem[ip];
     const double bb = -100.0 / (ri[i] * area[i]);
     const double aa = -100.0 / (ri[i] * area[ip]);
-    M.dax[i] -= bb;
-    M.dax[ip] -= aa;
-    b[i] = bb / M.cdt[i];
-    a[i] = aa / M.cdt[ip];
+    M.dax[e] -= bb;
+    M.dax[ep] -= aa;
+    b[e] = bb / M.cdt[e];
+    a[e] = aa / M.cdt[ep];
   }
 }
 
@@ -47,13 +48,12 @@ __global__ void k_pas_apply(DevModel M) {
   const int slot = blockIdx.x * blockDim.x + threadIdx.x;
   if (slot >= M.n_slots) return;
   const int g = slot / kLanes, lane = slot % kLanes;
-  const int N = M.s_rows[slot];
   const int64_t nb = M.g_node_base[g] + lane;
   double* d0 = const_cast<double*>(M.d0);
   double* ge = const_cast<double*>(M.ge);
   for (int j = 0; j < M.g_rows[g]; ++j) {
     const int64_t i = nb + (int64_t)j * kLanes;
-    if (j < N) {
+    if (M.flags[i] & kRealBit) {
       const double c = M.cdt[i];
       d0[i] = (c + M.pas_g[i] + M.dax[i]) / c;
       ge[i] = M.pas_g[i] * M.pas_e[i] / c;
@@ -95,9 +95,8 @@ __global__ void k_set_cell_param(DevModel M, int32_t param, const double* value)
     const int64_t base = M.g_hh_base[g] + lane;
     for (int q = 0; q < n; ++q) M.hh_raw[param * M.hh_elems + base + (int64_t)q * kLanes] = x;
   } else {
-    const int N = M.s_rows[slot];
     const int64_t nb = M.g_node_base[g] + lane;
-    for (int j = 0; j < N; ++j) {
+    for (int j = 0; j < M.g_rows[g]; ++j) {
       const int64_t i = nb + (int64_t)j * kLanes;
       if (M.flags[i] & kHasPasBit) M.pas_g[i] = x;
     }
@@ -134,7 +133,7 @@ __global__ void k_state_init(DevModel M, double v_init) {
   const int64_t nb = M.g_node_base[g] + lane;
   for (int j = 0; j < M.g_rows[g]; ++j) {
     const int64_t i = nb + (int64_t)j * kLanes;
-    M.v[i] = j < N ? v_init : 0.0;
+    M.v[i] = (M.flags[i] & kRealBit) ? v_init : 0.0;
     M.bp[i] = 0.0;
   }
   const int nh = M.s_nhh[slot];
@@ -150,7 +149,7 @@ __global__ void k_state_init(DevModel M, double v_init) {
   const int ns = M.s_nsyn[slot];
   const int64_t sb = M.g_syn_base[g] + lane;
   for (int q = 0; q < ns; ++q) M.syn_g[sb + (int64_t)q * kLanes] = 0.0;
-  M.s_above[slot] = N > 0 && v_init > M.s_thresh[slot];
+  M.s_above[slot] = M.s_gid[slot] >= 0 && N > 0 && v_init > M.s_thresh[slot];
   M.ev_count[slot] = 0;
 }
 
@@ -206,14 +205,11 @@ __global__ void k_setup_stim(DevModel M, const double* amp, const double* node_a
 // events for the same window, into its event buffer ordered by (step,
 // external-before-NetCon, input index | source gid, NetCon index).  No
 // atomics: the result is deterministic.
-__global__ void k_pull_events(DevModel M, int64_t J) {
+__global__ void k_pull_events(DevModel M, int64_t J, const int64_t* Jp) {
   const int slot = blockIdx.x * blockDim.x + threadIdx.x;
   if (slot >= M.n_slots) return;
+  if (Jp) J = *Jp;
   EvRec* out = M.ev_buf + (int64_t)slot * kEvCap;
-  if (M.s_gid[slot] < 0) {
-    M.ev_count[slot] = 0;
-    return;
-  }
   const int D = M.D;
   const int64_t T = J * D;
   int n = 0;
@@ -273,6 +269,151 @@ __global__ void k_pull_events(DevModel M, int64_t J) {
   M.ev_count[slot] = m;
 }
 
+// Advances the device-side interval index after a complete interval.
+__global__ void k_next_interval(int64_t* Jp) { *Jp += 1; }
+
+
+// ------------------------------------------------------- dense channel types
+// Channel types of the batched workload, present on every row of a cell
+// (I_ion of Eq. 1).  Gate x of a type obeys alpha = A (v-vh)/(1-exp(-(v-vh)/k)),
+// beta = B exp(-(v-vh2)/k2) (KCa: alpha = A cai/(cai+kd), beta = B) and
+// is updated by cnexp at v_{k+1}; the conductance gbar * prod(x^p) enters
+// the matrix in FP64 whatever the gate precision.  kin points at the lane's
+// kinetics in shared memory ([param][32]).
+template <typename T>
+__device__ __forceinline__ void gate_ab(const double* kin, T v, T& al, T& be) {
+  const T A = (T)kin[0], vh = (T)kin[kLanes], k = (T)kin[2 * kLanes];
+  const T B = (T)kin[3 * kLanes], vh2 = (T)kin[4 * kLanes], k2 = (T)kin[5 * kLanes];
+  al = vtrap<T>(A, vh, k, v);
+  be = B * dexp_(-(v - vh2) / k2);
+}
+
+template <int PREC>
+__device__ __forceinline__ void dense_cur(const DevModel& M, int mask, int64_t e, double v, const double* kin,
+                                          double& G, double& GE) {
+  using S = typename GateT<PREC>::S;
+  auto x = [&](int gi) { return (double)g_load(static_cast<const S*>(M.ch_gate[gi]) + e); };
+  double g = 0.0, ge = 0.0;
+  if (mask & 1) {  // NA3H: m^3 h
+    const double m = x(0), c = M.ch_gbar[0][e] * (m * m * m * x(1));
+    g += c;
+    ge = fma(c, kin[chan_kin0(0) * kLanes], ge);
+  }
+  if (mask & 2) {  // KDR4: n^4
+    const double n = x(2), c = M.ch_gbar[1][e] * ((n * n) * (n * n));
+    g += c;
+    ge = fma(c, kin[chan_kin0(1) * kLanes], ge);
+  }
+  if (mask & 4) {  // KA: a^3 b
+    const double a = x(3), c = M.ch_gbar[2][e] * (a * a * a * x(4));
+    g += c;
+    ge = fma(c, kin[chan_kin0(2) * kLanes], ge);
+  }
+  if (mask & 8) {  // IH: q
+    const double c = M.ch_gbar[3][e] * x(5);
+    g += c;
+    ge = fma(c, kin[chan_kin0(3) * kLanes], ge);
+  }
+  if (mask & 16) {  // CAHVA: m^2 h; its current drives [Ca]i
+    const double m = x(6), c = M.ch_gbar[4][e] * (m * m * x(7));
+    const double eca = kin[chan_kin0(4) * kLanes];
+    g += c;
+    ge = fma(c, eca, ge);
+    M.ica[e] = c * M.cdt[e] * (v - eca);
+  }
+  if (mask & 32) {  // KCA: c
+    const double c = M.ch_gbar[5][e] * x(8);
+    g += c;
+    ge = fma(c, kin[chan_kin0(5) * kLanes], ge);
+  }
+  G = g;
+  GE = ge;
+}
+
+template <int PREC>
+__device__ __forceinline__ void dense_state(const DevModel& M, int mask, int64_t e, double vnew, const double* kin) {
+  using S = typename GateT<PREC>::S;
+  using T = typename GateT<PREC>::M;
+  const T v = (T)vnew, tdt = (T)M.dt;
+  auto upd = [&](int gi, const double* k6) {
+    T al, be;
+    gate_ab<T>(k6, v, al, be);
+    S* p = static_cast<S*>(M.ch_gate[gi]) + e;
+    g_store(p, cnexp_step<T>(g_load(p), al, be, tdt));
+  };
+  if (mask & 1) {
+    upd(0, kin + (chan_kin0(0) + 1) * kLanes);
+    upd(1, kin + (chan_kin0(0) + 7) * kLanes);
+  }
+  if (mask & 2) upd(2, kin + (chan_kin0(1) + 1) * kLanes);
+  if (mask & 4) {
+    upd(3, kin + (chan_kin0(2) + 1) * kLanes);
+    upd(4, kin + (chan_kin0(2) + 7) * kLanes);
+  }
+  if (mask & 8) upd(5, kin + (chan_kin0(3) + 1) * kLanes);
+  if (mask & 16) {
+    upd(6, kin + (chan_kin0(4) + 1) * kLanes);
+    upd(7, kin + (chan_kin0(4) + 7) * kLanes);
+    const double* kc = kin + chan_kin0(4) * kLanes;
+    const T depth = (T)kc[13 * kLanes], taur = (T)kc[14 * kLanes], cainf = (T)kc[15 * kLanes];
+    T drive = T(-1e4) * (T)M.ica[e] / (T(2.0 * 96485.3321) * depth);
+    if (drive < T(0)) drive = T(0);
+    const T cai = (T)M.cai[e];
+    M.cai[e] = (double)(cai + (T(1) - dexp_(-tdt / taur)) * (cainf + drive * taur - cai));
+  }
+  if (mask & 32) {
+    const double* kk = kin + chan_kin0(5) * kLanes;
+    const T cai = (T)M.cai[e];
+    const T al = (T)kk[1 * kLanes] * cai / (cai + (T)kk[2 * kLanes]);
+    S* p = static_cast<S*>(M.ch_gate[8]) + e;
+    g_store(p, cnexp_step<T>(g_load(p), al, (T)kk[3 * kLanes], tdt));
+  }
+}
+
+// Dense-channel constants and initial state: gbar divided by cdt of the row,
+// gates at their steady state of v_init, [Ca]i at cainf (5e-5 mM without
+// CAHVA).
+template <int PREC>
+__global__ void k_setup_dense(DevModel M, double v_init, bool scale_gbar) {
+  using S = typename GateT<PREC>::S;
+  using T = typename GateT<PREC>::M;
+  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot >= M.n_slots) return;
+  const int g = slot / kLanes, lane = slot % kLanes;
+  const int N = M.s_rows[slot];
+  const int mask = M.g_chmask[g];
+  const int64_t nb = M.g_node_base[g] + lane;
+  const double* kin = M.ch_kin + slot;  // [param][n_slots]
+  const int64_t ks = M.n_slots;
+  const T v = (T)v_init;
+  for (int j = 0; j < N; ++j) {
+    const int64_t e = nb + (int64_t)j * kLanes;
+    if (!(M.flags[e] & kRealBit)) continue;
+    if (scale_gbar)
+      for (int t = 0; t < kChanTypes; ++t)
+        if ((mask >> t) & 1) M.ch_gbar[t][e] /= M.cdt[e];
+    auto init = [&](int gi, int k0) {
+      const T A = (T)kin[k0 * ks], vh = (T)kin[(k0 + 1) * ks], k = (T)kin[(k0 + 2) * ks];
+      const T B = (T)kin[(k0 + 3) * ks], vh2 = (T)kin[(k0 + 4) * ks], k2 = (T)kin[(k0 + 5) * ks];
+      const T al = vtrap<T>(A, vh, k, v), be = B * dexp_(-(v - vh2) / k2);
+      g_store(static_cast<S*>(M.ch_gate[gi]) + e, al / (al + be));
+    };
+    if (mask & 1) { init(0, chan_kin0(0) + 1); init(1, chan_kin0(0) + 7); }
+    if (mask & 2) init(2, chan_kin0(1) + 1);
+    if (mask & 4) { init(3, chan_kin0(2) + 1); init(4, chan_kin0(2) + 7); }
+    if (mask & 8) init(5, chan_kin0(3) + 1);
+    if (mask & 16) { init(6, chan_kin0(4) + 1); init(7, chan_kin0(4) + 7); }
+    if (M.cai) M.cai[e] = (mask & 16) ? kin[(chan_kin0(4) + 15) * ks] : 5e-5;
+    if (mask & 32) {
+      const T cai = (T)M.cai[e];
+      const T al = (T)kin[(chan_kin0(5) + 1) * ks] * cai / (cai + (T)kin[(chan_kin0(5) + 2) * ks]);
+      const T be = (T)kin[(chan_kin0(5) + 3) * ks];
+      g_store(static_cast<S*>(M.ch_gate[8]) + e, al / (al + be));
+    }
+    if (M.ica) M.ica[e] = 0.0;
+  }
+}
+
 // ---------------------------------------------------------- interval kernel
 // Advances the 32 cells of one warp (one block) by steps [s_begin, s_end) of
 // interval J, one cell per lane.  Per step k = J D + s (Section 2's list):
@@ -294,14 +435,18 @@ __global__ void k_pull_events(DevModel M, int64_t J) {
 // TRAJ: adjoint recompute -- also store v and the HH gates of every step
 // into the trajectory buffers, and leave spikes, threshold flags and traces
 // untouched.
-template <int PREC, bool TRAJ>
-__global__ void __launch_bounds__(32) k_interval(DevModel M, int64_t J, int s_begin, int s_end) {
+template <int PREC, bool TRAJ, bool DENSE>
+__global__ void __launch_bounds__(kMaxWarpsPerBlock * 32)
+    k_interval(DevModel M, int64_t J, int s_begin, int s_end, const int64_t* Jp) {
   using S = typename GateT<PREC>::S;
   using T = typename GateT<PREC>::M;
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int g = blockIdx.x;
+  extern __shared__ __align__(16) unsigned char smem_all[];
+  if (Jp) J = *Jp;  // interval index kept on the device (graph replay)
+  const int wib = threadIdx.x >> 5;  // warp in block: each warp runs one group
+  const int g = blockIdx.x * (blockDim.x >> 5) + wib;
   if (g >= M.n_groups) return;
-  const int lane = threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  unsigned char* const smem = smem_all + (size_t)wib * M.smem_warp;
   const int slot = g * kLanes + lane;
   const int N = M.s_rows[slot];
   const int R = M.g_rows[g];
@@ -324,6 +469,10 @@ __global__ void __launch_bounds__(32) k_interval(DevModel M, int64_t J, int s_be
   double* const st_y = st_x + DS * kLanes;
   double* const sl_ge = st_y + DS * kLanes;  // slot buffer [max_slots][32]
   double* const sl_d = sl_ge + M.max_slots * kLanes;
+  double* const kin = sl_d + M.max_slots * kLanes;  // dense kinetics [kChanParams][32]
+  const int chmask = DENSE ? M.g_chmask[g] : 0;
+  if (DENSE)
+    for (int q = 0; q < kChanParams; ++q) kin[q * kLanes] = M.ch_kin[(int64_t)q * M.n_slots + slot];
 
   // this lane's column of every per-row array
   double* const gv = M.v + nb;
@@ -457,6 +606,7 @@ __global__ void __launch_bounds__(32) k_interval(DevModel M, int64_t J, int s_be
     //     pops it into two FMAs (zero coefficients on rows that pop
     //     nothing); the previous row's carry enters the same way.
     double ca = 0.0, cx = 0.0, cb = 0.0, x = 0.0;
+    double pub_a = 0.0, pub_x = 0.0, pub_b = 0.0;
     int top = 0;
     for (int jb = R - 1; jb >= 0; jb -= kElimRows) {
 #pragma unroll
@@ -483,12 +633,33 @@ __global__ void __launch_bounds__(32) k_interval(DevModel M, int64_t J, int s_be
           const double fx = np > 0 ? st_x[ti] : 0.0;
           const double fb = np > 0 ? st_y[ti] : 0.0;
           top = tp;
-          double rhs = fma(fa, fx, e_v[ro] + (hs ? sg : g0));
-          double d = fma(fa, fb, hs ? sd : d00);
+          double base = e_v[ro] + (hs ? sg : g0);
+          double dd0 = hs ? sd : d00;
+          if (DENSE) {
+            double Gc, GEc;
+            dense_cur<PREC>(M, chmask, nb + (int64_t)j * kLanes, e_v[ro], kin, Gc, GEc);
+            base += GEc;
+            dd0 += Gc;
+          }
+          double rhs = fma(fa, fx, base);
+          double d = fma(fa, fb, dd0);
           for (int q = 1; q < np; ++q) {  // third and further children (rare)
             --top;
             rhs = fma(st_a[top * kLanes], st_x[top * kLanes], rhs);
             d = fma(st_a[top * kLanes], st_y[top * kLanes], d);
+          }
+          // a part of this cell in another lane hangs from this row: its root
+          // was eliminated one warp row earlier and published (-a, x, b/d)
+          const bool jn = (f & kJuncBit) != 0;
+          if (__any_sync(0xffffffffu, jn)) {
+            const int src = (f >> kJsrcShift) & 31;
+            const double qa = __shfl_sync(0xffffffffu, pub_a, src);
+            const double qx = __shfl_sync(0xffffffffu, pub_x, src);
+            const double qb = __shfl_sync(0xffffffffu, pub_b, src);
+            if (jn) {
+              rhs = fma(qa, qx, rhs);
+              d = fma(qa, qb, d);
+            }
           }
           rhs = fma(ca, cx, rhs);
           d = fma(ca, cb, d);
@@ -504,8 +675,13 @@ __global__ void __launch_bounds__(32) k_interval(DevModel M, int64_t J, int s_be
             st_x[top * kLanes] = x;
             st_y[top * kLanes] = bp;
           }
+          if (f & kProotBit) {  // the parent row lives in another lane
+            pub_a = na;
+            pub_x = x;
+            pub_b = bp;
+          }
           top += far ? 1 : 0;
-          ca = far ? 0.0 : na;
+          ca = (far || (f & kProotBit)) ? 0.0 : na;
           cx = x;
           cb = bp;
         }
@@ -529,8 +705,16 @@ __global__ void __launch_bounds__(32) k_interval(DevModel M, int64_t J, int s_be
           const bool far = (f & kFarBit) != 0;
           const int tp = far ? top - 1 : top;
           const double pv = st_x[(tp < DS ? tp : DS - 1) * kLanes];
-          const double vj = fma(-b_bp[ro], far ? pv : vprev, b_x[ro]);
+          double vp = far ? pv : vprev;
+          // root of a part whose parent row (one warp row down) is in another lane
+          const bool pr = (f & kProotBit) != 0;
+          if (__any_sync(0xffffffffu, pr)) {
+            const double qv = __shfl_sync(0xffffffffu, vprev, (f >> kPsrcShift) & 31);
+            if (pr) vp = qv;
+          }
+          const double vj = fma(-b_bp[ro], vp, b_x[ro]);
           gv[(int64_t)j * kLanes] = vj;
+          if (DENSE && (f & kRealBit)) dense_state<PREC>(M, chmask, nb + (int64_t)j * kLanes, vj, kin);
           if (TRAJ) M.traj_v[(k + 1 - M.traj_k0) * M.node_elems + nb + (int64_t)j * kLanes] = vj;
           const int np = (f >> kNFarShift) & kNFarMask;
           if (np > 0) st_x[tp * kLanes] = vj;
@@ -653,7 +837,6 @@ __global__ void __launch_bounds__(32) k_adjoint(DevModel M, AdjView A, int64_t k
   if (g >= M.n_groups) return;
   const int lane = threadIdx.x;
   const int slot = g * kLanes + lane;
-  const int N = M.s_rows[slot];
   const int R = M.g_rows[g];
   const int64_t nb = M.g_node_base[g] + lane;
   const int DS = M.stack_depth;
@@ -729,7 +912,7 @@ __global__ void __launch_bounds__(32) k_adjoint(DevModel M, AdjView A, int64_t k
       const int np = (f >> kNFarShift) & kNFarMask;
       for (int q = 0; q < np; ++q) st_x[top++ * kLanes] = yj;
       yprev = yj;
-      if (j < N) {
+      if (f & kRealBit) {
         const double mu = yj / M.cdt[e];
         const double v1 = M.traj_v[tv1 + e];
         if (f & kHasPasBit) gpas = fma(mu, M.pas_e[e] - v1, gpas);

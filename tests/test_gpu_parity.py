@@ -26,8 +26,8 @@ def cn():
     return _cn
 
 
-def run_gpu(cn, sc, precision="fp64", tstop=None, chunks=None):
-    md = cn.from_scenario(sc, precision=precision)
+def run_gpu(cn, sc, precision="fp64", tstop=None, chunks=None, **kw):
+    md = cn.from_scenario(sc, precision=precision, **kw)
     tstop = sc.tstop if tstop is None else tstop
     if chunks:
         for t in chunks:
@@ -195,3 +195,76 @@ def test_event_buffer_overflow_reported(cn):
     with pytest.raises(cn.CNError) as e:
         md.cn_sync()
     assert e.value.status == cn.CN_ERANGE
+
+
+@pytest.mark.parametrize("mapping", [1, 40, 100])
+def test_split_cells_over_lanes(cn, mapping):
+    """The same driven network with one cell per lane (mapping 1) and with
+    cells cut into parts of about 40 or 100 rows spread over lanes of one
+    warp: the raster, voltages and states must match the oracle in every
+    layout."""
+    sc = network(n_cells=96, tstop=30.0, w_median=0.03, bg_w=0.03, bg_rate_hz=30.0)
+    ref = run_oracle(sc)
+    assert len(ref["g"]) > 10
+    assert_parity(run_gpu(cn, sc, mapping=mapping), ref)
+
+
+def test_split_cells_batched_big(cn):
+    """Cells of up to 5,000 compartments with channels everywhere, cut into
+    parts of about 300 rows (up to 17 lanes per cell)."""
+    from scenarios import batched
+    sc = batched(n_cells=40, tstop=8.0, n_in=20)
+    ref = run_oracle(sc)
+    assert_parity(run_gpu(cn, sc, mapping=300), ref)
+
+
+def _same(a, b):
+    for key in ("g", "k", "v", "tr"):
+        assert np.array_equal(a[key], b[key]), key
+
+
+def test_graph_replay_matches_direct_launches(cn):
+    """Whole intervals replayed from the captured graph (8 per chunk, the
+    interval index kept on the device) give bit-identical results to one
+    launch per interval, including a run that stops mid-interval."""
+    sc = network(n_cells=200, tstop=41.3, w_median=0.03, bg_w=0.03, bg_rate_hz=30.0)
+    a = run_gpu(cn, sc, use_graph=False)
+    b = run_gpu(cn, sc, use_graph=True)
+    c = run_gpu(cn, sc, use_graph=True, chunks=[2.5, 11.0, 30.0])
+    assert len(a["g"]) > 10
+    _same(a, b)
+    _same(a, c)
+
+
+@pytest.mark.parametrize("wpb", [2, 4])
+def test_warps_per_block_bit_identical(cn, wpb):
+    """Several groups per block change only the launch shape: results are
+    bit-identical to one warp per block."""
+    sc = network(n_cells=300, tstop=20.0, w_median=0.03, bg_w=0.03, bg_rate_hz=30.0)
+    a = run_gpu(cn, sc, warps_per_block=1)
+    b = run_gpu(cn, sc, warps_per_block=wpb)
+    assert b["model"].cn_get_mapping()[1] == wpb
+    _same(a, b)
+
+
+def test_autotuned_mapping_parity(cn):
+    """CN_MAP_TUNE times every candidate layout, keeps the fastest, starts
+    from the initial state again: the run still matches the oracle."""
+    sc = network(n_cells=96, tstop=30.0, w_median=0.03, bg_w=0.03, bg_rate_hz=30.0)
+    ref = run_oracle(sc)
+    gpu = run_gpu(cn, sc, mapping=cn.CN_MAP_TUNE)
+    mp, wpb, nw, ms = gpu["model"].cn_get_mapping()
+    assert (mp == cn.CN_MAP_THREAD or mp >= 16) and 1 <= wpb <= 4 and nw >= 1 and ms > 0
+    assert_parity(gpu, ref)
+
+
+def test_profile_counts_graph_launches(cn):
+    """Per-launch CUDA-event timing also covers graph-replayed intervals."""
+    sc = network(n_cells=64, tstop=30.0)
+    md = cn.from_scenario(sc, record=False)
+    md.cn_profile(True)
+    md.cn_run(27.0)
+    k_ms, k_n, p_ms, p_n = md.cn_profile_read()
+    assert k_n == 27 and p_n == 27 and k_ms > 0 and p_ms > 0
+    md.cn_run(30.0)
+    assert md.cn_profile_read()[1] == 3

@@ -1,0 +1,223 @@
+"""Host checks of the cell-to-lane placement (no GPU needed).
+
+cn_plan_layout returns, for every node, the lane and warp row the engine
+gives it and the topology bits the interval kernel reads.  These tests check
+the invariants the kernel relies on (Hines order inside every part, a part
+root exactly one warp row after its junction row in another lane of the same
+warp, far-child stack discipline within the reported depth), and then run the
+kernel's elimination schedule on random tree systems in NumPy, following only
+the placement: the solution must equal a direct sparse solve."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from scenarios import network, batched, passive_cable, ring16
+
+FAR, REAL, JUNC, PROOT = 1 << 12, 1 << 17, 1 << 18, 1 << 24
+
+
+@pytest.fixture(scope="module")
+def cn():
+    from paper_1901_10975_gb300 import build
+    build.build()
+    from paper_1901_10975_gb300 import cn as _cn
+    return _cn
+
+
+def cells_of(sc):
+    off = np.asarray(sc.cell_offset, np.int64)
+    return off, np.asarray(sc.parent, np.int32)
+
+
+def check_invariants(off, parent, L):
+    lane, row, fl = L["lane"], L["row"], L["flags"]
+    n = parent.shape[0]
+    assert np.all(fl & REAL)
+    # one node per (lane, row)
+    key = lane.astype(np.int64) * (1 << 32) + row
+    assert np.unique(key).shape[0] == n
+    nfar_seen = np.zeros(n, np.int64)
+    for c in range(len(off) - 1):
+        lo, hi = off[c], off[c + 1]
+        lanes = np.unique(lane[lo:hi])
+        assert np.all(lanes // 32 == lanes[0] // 32), "a cell spans two warps"
+        # each lane of the cell holds one contiguous run of rows
+        for l in lanes:
+            r = np.sort(row[lo:hi][lane[lo:hi] == l])
+            assert np.all(np.diff(r) == 1)
+        for i in range(lo + 1, hi):
+            p = lo + parent[i]
+            if lane[i] == lane[p]:
+                assert not (fl[i] & PROOT)
+                if fl[i] & FAR:
+                    assert row[p] < row[i] - 1
+                    nfar_seen[p] += 1
+                else:
+                    assert row[p] == row[i] - 1
+            else:
+                assert fl[i] & PROOT and ((fl[i] >> 25) & 31) == lane[p] % 32
+                assert fl[p] & JUNC and ((fl[p] >> 19) & 31) == lane[i] % 32
+                assert row[i] == row[p] + 1
+        root_lane = lane[lo]
+        assert not (fl[lo] & PROOT) and row[lo] == row[lo:hi][lane[lo:hi] == root_lane].min()
+    assert np.array_equal((fl >> 13) & 7, nfar_seen)
+    # every lane is used by at most one cell
+    owner = {}
+    for c in range(len(off) - 1):
+        for l in np.unique(lane[off[c]:off[c + 1]]):
+            assert owner.setdefault(int(l), c) == c
+
+
+def emulate_solve(off, parent, L, a, b, d, rhs):
+    """The interval kernel's elimination and back substitution, warp row by
+    warp row, driven only by the placement and its flags."""
+    lane, row, fl = L["lane"], L["row"], L["flags"]
+    n = parent.shape[0]
+    at = {}
+    for i in range(n):
+        at[(int(lane[i]), int(row[i]))] = i
+    depth = L["stack_depth"]
+    x = np.zeros(n)
+    bp = np.zeros(n)
+    v = np.zeros(n)
+    span = np.zeros(L["n_warps"], np.int64)
+    np.maximum.at(span, lane // 32, row.astype(np.int64) + 1)
+    for w in range(L["n_warps"]):
+        lanes = range(32 * w, 32 * w + 32)
+        R = int(span[w])
+        if R == 0:
+            continue
+        stack = {l: [] for l in lanes}
+        carry = {l: None for l in lanes}
+        pub = {l: None for l in lanes}
+        maxtop = 0
+        for j in range(R - 1, -1, -1):
+            new_pub = {}
+            for l in lanes:
+                i = at.get((l, j))
+                if i is None:
+                    carry[l] = None
+                    continue
+                f = int(fl[i])
+                r_, d_ = rhs[i], d[i]
+                nf = (f >> 13) & 7
+                for _ in range(nf):
+                    na, xx, bb = stack[l].pop()
+                    r_ += na * xx
+                    d_ += na * bb
+                if f & JUNC:
+                    na, xx, bb = pub[(l // 32) * 32 + ((f >> 19) & 31)]
+                    r_ += na * xx
+                    d_ += na * bb
+                if carry[l] is not None:
+                    na, xx, bb = carry[l]
+                    r_ += na * xx
+                    d_ += na * bb
+                x[i] = r_ / d_
+                bp[i] = b[i] / d_
+                ent = (-a[i], x[i], bp[i])
+                carry[l] = None
+                if f & FAR:
+                    stack[l].append(ent)
+                    maxtop = max(maxtop, len(stack[l]))
+                elif f & PROOT:
+                    new_pub[l] = ent
+                else:
+                    carry[l] = ent
+            pub.update(new_pub)
+        assert all(len(s) == 0 for s in stack.values())
+        assert maxtop <= depth
+        # back substitution, root to leaves
+        vstack = {l: [] for l in lanes}
+        vprev = {l: 0.0 for l in lanes}
+        for j in range(R):
+            cur = {}
+            for l in lanes:
+                i = at.get((l, j))
+                if i is None:
+                    continue
+                f = int(fl[i])
+                if f & FAR:
+                    vp = vstack[l].pop()
+                elif f & PROOT:
+                    vp = vprev[(l // 32) * 32 + ((f >> 25) & 31)]
+                else:
+                    vp = vprev[l]
+                v[i] = x[i] - bp[i] * vp
+                vstack[l].extend([v[i]] * ((f >> 13) & 7))
+                cur[l] = v[i]
+            vprev.update(cur)
+    return v
+
+
+def random_system(off, parent, rng):
+    n = parent.shape[0]
+    a = -rng.uniform(0.1, 1.0, n)
+    b = -rng.uniform(0.1, 1.0, n)
+    d = np.zeros(n)
+    rows, cols, vals = [], [], []
+    for c in range(len(off) - 1):
+        for i in range(off[c], off[c + 1]):
+            p = parent[i]
+            if p < 0:
+                a[i] = b[i] = 0.0
+                continue
+            p += off[c]
+            rows += [i, p]
+            cols += [p, i]
+            vals += [b[i], a[i]]
+            d[i] += -b[i]
+            d[p] += -a[i]
+    d += rng.uniform(0.05, 1.0, n)
+    A = sp.csr_matrix((np.concatenate([vals, d]), (np.concatenate([rows, np.arange(n)]),
+                                                    np.concatenate([cols, np.arange(n)]))), shape=(n, n))
+    rhs = rng.normal(size=n)
+    return a, b, d, rhs, A
+
+
+CASES = {
+    "network": lambda: network(n_cells=60, tstop=1.0),
+    "batched": lambda: batched(n_cells=24, tstop=1.0, n_in=4),
+    "cable": lambda: passive_cable(700, L=1400.0, tstop=1.0),
+    "ring": lambda: ring16(),
+}
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+@pytest.mark.parametrize("mapping", [1, 16, 40, 100, 300, 0])
+def test_layout_invariants_and_emulated_solve(cn, case, mapping):
+    off, parent = cells_of(CASES[case]())
+    L = cn.cn_plan_layout(off, parent, mapping)
+    check_invariants(off, parent, L)
+    rng = np.random.default_rng(7)
+    a, b, d, rhs, A = random_system(off, parent, rng)
+    v = emulate_solve(off, parent, L, a, b, d, rhs)
+    ref = spla.spsolve(A.tocsc(), rhs)
+    assert np.max(np.abs(v - ref)) <= 1e-12 * max(1.0, np.max(np.abs(ref)))
+
+
+def test_split_spreads_large_cells(cn):
+    """The largest cell of the batched workload (a branched tree) with a
+    100-row target occupies several lanes and its span (warp rows) drops well
+    below its size; an unbranched cable cannot be shortened (its depth is
+    its size) and stays on one lane."""
+    off, parent = cells_of(batched(n_cells=24, tstop=1.0, n_in=4))
+    sizes = np.diff(off)
+    c = int(np.argmax(sizes))
+    sub_off = np.array([0, sizes[c]])
+    sub_par = parent[off[c]:off[c + 1]]
+    one = cn.cn_plan_layout(sub_off, sub_par, 1)
+    split = cn.cn_plan_layout(sub_off, sub_par, 100)
+    assert np.unique(one["lane"]).shape[0] == 1 and one["row"].max() == sizes[c] - 1
+    assert np.unique(split["lane"]).shape[0] >= 4 and split["row"].max() < sizes[c] // 2
+    off, parent = cells_of(passive_cable(700, L=1400.0, tstop=1.0))
+    assert np.unique(cn.cn_plan_layout(off, parent, 40)["lane"]).shape[0] == 1
+
+
+def test_plan_layout_rejects_bad_trees(cn):
+    with pytest.raises(cn.CNError) as e:
+        cn.cn_plan_layout(np.array([0, 3]), np.array([-1, 0, 2]), 0)
+    assert e.value.status == cn.CN_EINVAL
+    with pytest.raises(cn.CNError):
+        cn.cn_plan_layout(np.array([0, 2]), np.array([0, -1]), 0)
