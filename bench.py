@@ -144,16 +144,32 @@ def max_over_ranks(x, world):
 
 
 def workload(args, intervals):
+    if args.workload == "batched":
+        from scenarios import batched
+        return batched(n_cells=args.cells or 50000, tstop=float(intervals) + 1.0, seed=1903)
     from scenarios import network
-    return network(n_cells=args.cells, tstop=float(intervals) + 1.0, seed=1902)
+    return network(n_cells=args.cells or 16384, tstop=float(intervals) + 1.0, seed=1902)
 
 
-def config_dict(args, sc):
-    return {"workload": f"network {args.cells} cells x 200-600 compartments (HH soma, pas dendrites), "
-                        f"50 ExpSyn/cell, 100 NetCons/cell, 5 Hz background, dt 0.025 ms, FP64",
-            "cells": args.cells, "compartments": int(sc.n_nodes), "step": "one 1 ms min-delay interval (40 dt)",
-            "l2": "working set > L2 (no flush needed)", "precision": args.precision,
-            "mapping": getattr(args, "mapping", 0)}
+def config_dict(args, sc, layout=None):
+    cells = int(len(sc.cell_offset) - 1)
+    if args.workload == "batched":
+        name = (f"batched {cells} cells x lognormal(400, 0.8) compartments in [50, 5000], random subset of "
+                f"6 channel types per cell on every node, network as the plain workload, dt 0.025 ms")
+    else:
+        name = (f"network {cells} cells x 200-600 compartments (HH soma, pas dendrites), "
+                f"50 ExpSyn/cell, 100 NetCons/cell, 5 Hz background, dt 0.025 ms")
+    d = {"workload": name, "cells": cells, "compartments": int(sc.n_nodes),
+         "step": "one 1 ms min-delay interval (40 dt)", "l2": "working set > L2 (no flush needed)",
+         "precision": args.precision}
+    if layout is not None:
+        mp, wpb, nw, tuned = layout
+        span, tall = mp & ~(1 << 20), bool(mp & (1 << 20))
+        d["layout"] = {"mapping": "one cell per lane" if mp == 1 else
+                       f"cells split to ~{span} rows per lane" + (", tall warps" if tall else ""),
+                       "warps_per_block": wpb, "warps": nw,
+                       "chosen_by": "autotuner" if args.mapping == 2 else "fixed"}
+    return d
 
 
 def cpu_oracle_rate(sc, intervals, warm=0):
@@ -183,7 +199,7 @@ def run_reference(args):
             "data": "synthetic", "config": config_dict(args, sc),
             "cpu_baseline": {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": f"{args.steps} intervals ({args.steps * 40} steps) of the full "
-                                       f"{args.cells}-cell network after {args.warmup} warm-up intervals"},
+                                       f"{args.workload} workload after {args.warmup} warm-up intervals"},
             "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -205,7 +221,8 @@ def run_ours(args):
     sc = workload(args, W + K)
     md = cn.from_scenario(sc, precision=args.precision, device=local, record=False, mapping=args.mapping)
     md.cn_profile(True)
-    md.cn_run(float(W))                       # warm-up intervals (includes the one-time upload)
+    layout = md.cn_get_mapping()              # lays the model out (autotuned by default)
+    md.cn_run(float(W))                       # warm-up intervals
     md.cn_sync()
     md.cn_profile_read()
     launches0 = md.launches
@@ -237,7 +254,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.precision == "fp64" else f"f64 (gates {args.precision[5:]})",
-        "data": "synthetic", "config": config_dict(args, sc),
+        "data": "synthetic", "config": config_dict(args, sc, layout),
         "gpu_launches": int(launches),
         "roofline": {"bound": "alu", "pipe": "fp64", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": traffic,
@@ -250,13 +267,13 @@ def run_ours(args):
         "clocks": clocks,
     }
     if rank == 0 and world == 1 and not args.no_e2e:
-        line["e2e"] = e2e_measure(args, cn, K)
+        line["e2e"] = e2e_measure(args, cn, K, layout)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         sc_cpu = workload(args, args.cpu_intervals)
         rate, threads, dt = cpu_oracle_rate(sc_cpu, args.cpu_intervals)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
                                 "sample": f"first {args.cpu_intervals} intervals ({args.cpu_intervals * 40} steps) "
-                                          f"of the full {args.cells}-cell network, {dt:.1f} s"}
+                                          f"of the full {args.workload} workload, {dt:.1f} s"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     md.close()
@@ -266,7 +283,7 @@ def run_ours(args):
     return 0
 
 
-def e2e_measure(args, cn, K):
+def e2e_measure(args, cn, K, layout):
     """Same metric through the public API from host buffers: model creation
     from pinned host arrays (geometry, tables, NetCons, events: the H2D
     copies), K intervals, then the spike raster and soma traces back to the
@@ -285,7 +302,8 @@ def e2e_measure(args, cn, K):
     h2d += sum(m.node.nbytes + m.param_matrix().nbytes for m in sc.mechs)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    md = cn.from_scenario(sc, precision=args.precision, record=True, mapping=args.mapping)
+    md = cn.from_scenario(sc, precision=args.precision, record=True, mapping=layout[0],
+                          warps_per_block=layout[1])
     md.cn_run(float(K))
     g, k = md.cn_get_spikes()
     tr = [md.cn_get_trace(r) for r in range(len(sc.rec_node))]
@@ -294,7 +312,8 @@ def e2e_measure(args, cn, K):
     md.close()
     return {"value": sc.n_nodes * 40 * K / dt, "unit": UNIT, "h2d_bytes_per_step": h2d / K,
             "d2h_bytes_per_step": d2h / K, "seconds": dt,
-            "region": "cn_geometry + cn_model_create + cn_add_* + cn_run + cn_get_spikes + cn_get_trace"}
+            "region": "cn_geometry + cn_model_create + cn_add_* + cn_run + cn_get_spikes + cn_get_trace "
+                      "(with the layout the autotuner chose for the device-timed run)"}
 
 
 def main():
@@ -303,13 +322,15 @@ def main():
     ap.add_argument("--steps", type=int, default=100, help="timed 1 ms intervals")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--cells", type=int, default=16384)
+    ap.add_argument("--cells", type=int, default=0, help="0: the workload's full size")
+    ap.add_argument("--workload", choices=["network", "batched"], default="network")
     ap.add_argument("--precision", choices=["fp64", "gate_fp32", "gate_bf16"], default="fp64")
     ap.add_argument("--cpu-intervals", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--mapping", type=int, default=0,
-                    help="0: automatic cell split, 1: one cell per lane, >=16: target rows per lane")
+    ap.add_argument("--mapping", type=int, default=2,
+                    help="2: autotuned, 0: split to the mean cell size, 1: one cell per lane, "
+                         ">=16: target rows per lane")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -40,16 +40,18 @@ struct EvRec {
 // the lane holding that part, 24 part root (the parent is in another lane),
 // 25-29 the lane holding the parent.
 constexpr int kMaxWarpsPerBlock = 4;  // warps (groups) per block of the interval kernel
-constexpr int32_t kNoSlot = 0xfff;
-constexpr int32_t kFarBit = 1 << 12;
-constexpr int kNFarShift = 13;
+// Per-row flag word of the interval kernel.
+constexpr int32_t kNoSlot = 0x3f;          // bits 0-5: mechanism slot of the row (HH, IClamp); 63 = none
+constexpr int32_t kFarBit = 1 << 6;        // the in-part parent is not the previous row
+constexpr int kNFarShift = 7;              // bits 7-9: number of far children
 constexpr int32_t kNFarMask = 7;
-constexpr int32_t kHasPasBit = 1 << 16;
-constexpr int32_t kRealBit = 1 << 17;
-constexpr int32_t kJuncBit = 1 << 18;
-constexpr int kJsrcShift = 19;
-constexpr int32_t kProotBit = 1 << 24;
-constexpr int kPsrcShift = 25;
+constexpr int32_t kHasPasBit = 1 << 10;
+constexpr int32_t kRealBit = 1 << 11;      // a compartment (else an identity padding row)
+constexpr int32_t kJuncBit = 1 << 12;      // a child part hangs from this row
+constexpr int32_t kProotBit = 1 << 13;     // root of a child part (its parent row is elsewhere)
+constexpr int kJmailShift = 14;            // bits 14-22: mailbox entry of the hanging part
+constexpr int kPmailShift = 23;            // bits 23-31: mailbox entry of this part root
+constexpr int32_t kMailMask = 511;
 
 // Channel types of the batched workload (CN_MECH_NA3H .. CN_MECH_KCA), their
 // gate-state arrays and their per-cell kinetic parameters (the table columns
@@ -67,7 +69,7 @@ __host__ __device__ constexpr int chan_kin0(int t) {
 // Plain-old-data view of a model's device buffers, passed by value.
 struct DevModel {
   int32_t n_groups, n_slots, n_cells, D, n_rec;
-  int32_t max_slots, stack_depth;
+  int32_t max_slots, stack_depth, n_mail;
   int64_t node_elems;
   double dt;
   int64_t smem_warp;           // dynamic shared memory of one warp (multiple of 16 bytes)
@@ -109,7 +111,7 @@ struct DevModel {
   const double* slot_ge0;   // ge of the slot's row
   const double* slot_d00;   // d0 of the slot's row
   // synapses (ExpSyn)
-  const int32_t* syn_slot;
+  const int32_t* syn_row;      // warp row of the synapse (a lane's synapses by row, descending)
   double* syn_g;
   const double* syn_s;      // 100 / (area cdt) of the synapse row
   const double* syn_e;
@@ -175,17 +177,18 @@ struct DevModel {
 // back substitution streams two arrays and the flags and spends one, so its
 // ring is deeper.  Each lane copies and reads only its own elements, so the
 // rings need no warp synchronisation.  The two rings share memory.
-constexpr int kElimRows = 8;
-constexpr int kBackRows = 24;
+constexpr int kElimRows = 4;
+constexpr int kBackRows = 8;
 
 __host__ __device__ inline size_t ring_bytes() {
   const size_t elim = (size_t)kElimRows * kLanes * (5 * sizeof(double) + sizeof(int32_t));
   const size_t back = (size_t)kBackRows * kLanes * (2 * sizeof(double) + sizeof(int32_t));
   return ((elim > back ? elim : back) + 15) / 16 * 16;
 }
-__host__ __device__ inline size_t interval_smem_bytes(int stack_depth, int max_slots, bool dense) {
+__host__ __device__ inline size_t interval_smem_bytes(int stack_depth, int max_slots, bool dense, int n_mail) {
   return ring_bytes() + (size_t)stack_depth * kLanes * 3 * sizeof(double) +
-         (size_t)max_slots * kLanes * 2 * sizeof(double) + (dense ? (size_t)kChanParams * kLanes * sizeof(double) : 0);
+         (size_t)max_slots * kLanes * 2 * sizeof(double) +
+         (dense ? (size_t)kChanParams * kLanes * sizeof(double) : 0) + (size_t)n_mail * 4 * sizeof(double);
 }
 
 // Per-thread asynchronous global->shared copies (through L1, so a lane's own

@@ -64,6 +64,8 @@ struct cn_model {
   std::vector<int32_t> node_cell;
   std::vector<int32_t> node_row;   // global node -> warp row of its lane
   std::vector<int32_t> node_slot;  // global node -> lane (slot) holding it
+  std::vector<int64_t> node_elem;  // global node -> element of the interleaved row arrays
+  std::vector<int64_t> hh_elem;    // HH instance -> element of the interleaved HH arrays
   std::vector<int32_t> slot_cell;  // lane -> cell (-1 when empty)
   size_t smem_bytes = 0;
   std::vector<int64_t> x_pos0;     // initial external-event cursors
@@ -172,12 +174,18 @@ struct Rows {
   int64_t elems = 0;
 };
 
-Rows interleave(const cn_model* m, const std::vector<int32_t>& inst_node) {
+Rows interleave(const cn_model* m, const std::vector<int32_t>& inst_node, bool rows_descending = false) {
   Rows r;
   r.slot_n.assign(m->n_slots, 0);
   r.inst_slot.resize(inst_node.size());
   r.inst_q.resize(inst_node.size());
-  for (size_t i = 0; i < inst_node.size(); ++i) {
+  std::vector<int64_t> order(inst_node.size());
+  std::iota(order.begin(), order.end(), 0);
+  if (rows_descending)  // a lane's instances in elimination order (stable for equal rows)
+    std::stable_sort(order.begin(), order.end(), [&](int64_t x, int64_t y) {
+      return m->node_row[inst_node[x]] > m->node_row[inst_node[y]];
+    });
+  for (int64_t i : order) {
     int s = m->node_slot[inst_node[i]];
     r.inst_slot[i] = s;
     r.inst_q[i] = r.slot_n[s]++;
@@ -396,6 +404,7 @@ CellPlan plan_cell(const int32_t* parent, int n, int target) {
 
 // Target span (rows per lane) of a mapping value; 0 = never split.
 int map_target(int32_t mapping, int64_t n_nodes, int32_t n_cells, bool adjoint) {
+  mapping &= ~CN_MAP_TALL;
   if (mapping >= 16) return mapping;
   if (mapping == CN_MAP_AUTO && !adjoint && n_cells > 0)
     return (int)std::max<int64_t>(16, (n_nodes + n_cells - 1) / n_cells);
@@ -425,73 +434,193 @@ bool valid_trees(int32_t n_cells, const int32_t* off, const int32_t* parent, std
   return true;
 }
 
-// Placement of every cell on the lanes of the warps: cells are grouped by
-// channel set (a warp runs one set), then by part count and span, largest
-// first; a cell's parts take consecutive lanes of one warp.  node_flags holds
-// each node's topology bits (real, far, nfar, part root with its parent's
-// lane, junction with its child's lane); the mechanism-slot field is left 0.
+// Placement of every cell on the lanes of the warps.  Each warp is a grid
+// of 32 lanes x H rows: H is the span of the cell that opened the warp, or,
+// with "tall" warps, the largest span of all cells.  Cells are taken largest
+// span first and placed, part by part in part-tree order, into the first
+// warp where they fit (among the last few warps, or any warp when tall): the root part into a lane that holds no other spike
+// source, each child part into the lane whose free row is closest to (at or
+// below) the row after its junction, so that it starts there or, failing
+// that, as early as possible above it.  A child part may start anywhere
+// above its junction row: its eliminated (-a, x, b/d) and the junction's
+// back-substituted v pass through a per-warp mailbox in shared memory.
+// With stacking on, a lane holds parts of several cells one above the
+// other; without it (channel kinetics are per lane; the adjoint sums per
+// lane) a lane holds parts of one cell only.  Channel sets never share a
+// warp.  node_flags holds each node's topology bits (real, far, nfar,
+// junction and part root with their mailbox entries); the mechanism-slot
+// field is left 0.
 struct Layout {
   std::vector<CellPlan> plans;
   int depth = 1;
   int n_groups = 0;
-  std::vector<int32_t> cell_lane0;            // cell -> first lane (global)
+  int n_mail = 1;                             // mailbox entries per warp (max over warps)
+  std::vector<int32_t> cell_lane0;            // cell -> lane of its root part (global)
+  std::vector<int32_t> lane_rows;             // lane -> rows used
+  std::vector<int32_t> lane_cell;             // lane -> its only cell (-1: none or several)
   std::vector<int32_t> node_slot, node_row;   // global node -> lane, warp row
   std::vector<int32_t> node_flags;            // global node -> topology bits
 };
 
+constexpr size_t kPackWindow = 4;
+
 bool build_layout(int32_t n_cells, const int32_t* off, const int32_t* parent, const int32_t* cell_mask,
-                  int target, Layout& L, std::string& err) {
+                  const int32_t* spike_node, int target, bool stack, bool tall, Layout& L, std::string& err) {
   auto mask = [&](int c) { return cell_mask ? cell_mask[c] : 0; };
   L.plans.assign(n_cells, CellPlan{});
   L.depth = 1;
+  int H = 1;
   for (int c = 0; c < n_cells; ++c) {
     const int n = off[c + 1] - off[c];
     L.plans[c] = plan_cell(parent + off[c], n, target);
     L.depth = std::max(L.depth, L.plans[c].depth);
+    H = std::max(H, L.plans[c].span);
     for (int32_t li = 0; li < n; ++li)
       if (L.plans[c].nfar[li] > (int)cn::kNFarMask) {
         err = "a node has more than 8 children";
         return false;
       }
+    if ((int)L.plans[c].parts.size() - 1 > cn::kMailMask + 1) {
+      err = "a cell was cut into too many parts";
+      return false;
+    }
   }
   std::vector<int32_t> order(n_cells);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
     if (mask(x) != mask(y)) return mask(x) < mask(y);
-    if (L.plans[x].parts.size() != L.plans[y].parts.size()) return L.plans[x].parts.size() > L.plans[y].parts.size();
     return L.plans[x].span > L.plans[y].span;
   });
-  L.cell_lane0.assign(n_cells, -1);
-  int fill = 0, ng = 0;
-  int32_t prev_mask = -1;
-  for (int c : order) {
-    const int P = (int)L.plans[c].parts.size();
-    if (ng == 0 || fill + P > cn::kLanes || mask(c) != prev_mask) {
-      ++ng;
-      fill = 0;
+  struct Warp {
+    int lev[cn::kLanes];
+    int owner[cn::kLanes];   // -1 free, >= 0 the only cell, -2 several
+    bool root[cn::kLanes];
+    int n_mail = 0;
+    int32_t mask = 0;
+    int min_lev = 0;
+    int H = 0;               // rows of this warp: the span of the cell that opened it
+  };
+  std::vector<Warp> warps;
+  // per cell: part order (parents first), and the placement found
+  std::vector<int> porder, pstart, plane;
+  std::vector<std::vector<int>> kids;
+  std::vector<int32_t> part_lane_of_cell, part_start_of_cell;  // flattened by cell
+  std::vector<int64_t> cell_part0(n_cells + 1, 0);
+  for (int c = 0; c < n_cells; ++c) cell_part0[c + 1] = cell_part0[c] + (int64_t)L.plans[c].parts.size();
+  part_lane_of_cell.assign(cell_part0[n_cells], -1);
+  part_start_of_cell.assign(cell_part0[n_cells], 0);
+  std::vector<int> cell_warp(n_cells, -1), warp_mail0(n_cells, 0);
+  auto try_place = [&](int c, Warp& w, int wi) -> bool {
+    const CellPlan& P = L.plans[c];
+    const int np = (int)P.parts.size();
+    if (w.n_mail + np - 1 > cn::kMailMask + 1) return false;
+    const int qsp = P.part_of[spike_node ? spike_node[c] : 0];  // the part holding the spike source
+    int lev[cn::kLanes], own[cn::kLanes];
+    std::copy(w.lev, w.lev + cn::kLanes, lev);
+    std::copy(w.owner, w.owner + cn::kLanes, own);
+    pstart.assign(np, 0);
+    plane.assign(np, -1);
+    for (int q : porder) {
+      const int size = (int)P.parts[q].nodes.size();
+      int best = -1, bstart = 0, bgap = 0;
+      const int release = q == 0 ? 0 : pstart[P.parts[q].parent_part] + P.row_of[P.parts[q].jnode] + 1;
+      for (int l = 0; l < cn::kLanes; ++l) {
+        if (q == qsp && w.root[l]) continue;
+        if (!stack && own[l] != -1 && own[l] != c) continue;
+        const int st = std::max(lev[l], release);
+        const int gap = st - lev[l];
+        if (st + size > w.H) continue;
+        if (best < 0 || st < bstart || (st == bstart && gap < bgap)) {
+          best = l;
+          bstart = st;
+          bgap = gap;
+        }
+      }
+      if (best < 0) return false;
+      plane[q] = best;
+      pstart[q] = bstart;
+      lev[best] = bstart + size;
+      own[best] = (own[best] == -1 || own[best] == c) ? c : -2;
     }
-    prev_mask = mask(c);
-    L.cell_lane0[c] = (ng - 1) * cn::kLanes + fill;
-    fill += P;
+    std::copy(lev, lev + cn::kLanes, w.lev);
+    std::copy(own, own + cn::kLanes, w.owner);
+    w.root[plane[qsp]] = true;
+    w.min_lev = *std::min_element(w.lev, w.lev + cn::kLanes);
+    warp_mail0[c] = w.n_mail;
+    w.n_mail += np - 1;
+    cell_warp[c] = wi;
+    for (int q = 0; q < np; ++q) {
+      part_lane_of_cell[cell_part0[c] + q] = wi * cn::kLanes + plane[q];
+      part_start_of_cell[cell_part0[c] + q] = pstart[q];
+    }
+    return true;
+  };
+  size_t group_first = 0;  // first warp of the current channel set
+  for (int c : order) {
+    const CellPlan& P = L.plans[c];
+    const int np = (int)P.parts.size();
+    kids.assign(np, {});
+    for (int q = 1; q < np; ++q) kids[P.parts[q].parent_part].push_back(q);
+    porder.clear();
+    porder.push_back(0);
+    for (size_t h = 0; h < porder.size(); ++h)
+      for (int k : kids[porder[h]]) porder.push_back(k);
+    if (!warps.empty() && warps.back().mask != mask(c)) group_first = warps.size();
+    bool placed = false;
+    const int size0 = (int)P.parts[0].nodes.size();
+    // first fit among the most recent warps of this channel set, so that a
+    // warp holds cells of similar span
+    const size_t window = tall ? warps.size() : kPackWindow;
+    const size_t from = std::max(group_first, warps.size() > window ? warps.size() - window : 0);
+    for (size_t wi = from; wi < warps.size() && !placed; ++wi) {
+      if (warps[wi].min_lev + size0 > warps[wi].H) continue;
+      placed = try_place(c, warps[wi], (int)wi);
+    }
+    if (!placed) {
+      Warp w;
+      std::fill(w.lev, w.lev + cn::kLanes, 0);
+      std::fill(w.owner, w.owner + cn::kLanes, -1);
+      std::fill(w.root, w.root + cn::kLanes, false);
+      w.mask = mask(c);
+      w.H = tall ? H : P.span;
+      warps.push_back(w);
+      if (!try_place(c, warps.back(), (int)warps.size() - 1)) {
+        err = "internal: a cell does not fit an empty warp";
+        return false;
+      }
+    }
   }
-  L.n_groups = ng;
+  L.n_groups = (int)warps.size();
+  L.n_mail = 1;
+  L.lane_rows.assign((size_t)L.n_groups * cn::kLanes, 0);
+  L.lane_cell.assign((size_t)L.n_groups * cn::kLanes, -1);
+  for (int wi = 0; wi < L.n_groups; ++wi) {
+    L.n_mail = std::max(L.n_mail, warps[wi].n_mail);
+    for (int l = 0; l < cn::kLanes; ++l) {
+      L.lane_rows[(size_t)wi * cn::kLanes + l] = warps[wi].lev[l];
+      L.lane_cell[(size_t)wi * cn::kLanes + l] = warps[wi].owner[l] >= 0 ? warps[wi].owner[l] : -1;
+    }
+  }
+  L.cell_lane0.assign(n_cells, -1);
   const int64_t nn = off[n_cells];
   L.node_slot.assign(nn, 0);
   L.node_row.assign(nn, 0);
   L.node_flags.assign(nn, 0);
   for (int c = 0; c < n_cells; ++c) {
     const CellPlan& P = L.plans[c];
-    const int l0 = L.cell_lane0[c];
+    const int64_t p0 = cell_part0[c];
+    L.cell_lane0[c] = part_lane_of_cell[p0];
     for (int32_t li = 0; li < off[c + 1] - off[c]; ++li) {
       const int64_t node = off[c] + li;
       const int q = P.part_of[li];
-      L.node_slot[node] = l0 + q;
-      L.node_row[node] = P.parts[q].base + P.row_of[li];
+      L.node_slot[node] = part_lane_of_cell[p0 + q];
+      L.node_row[node] = part_start_of_cell[p0 + q] + P.row_of[li];
       int32_t f = cn::kRealBit | (P.far[li] ? cn::kFarBit : 0) | (P.nfar[li] << cn::kNFarShift);
+      // mailbox entry of part q (q >= 1): warp_mail0 + q - 1
       if (q > 0 && li == P.parts[q].root)
-        f |= cn::kProotBit | ((l0 + P.parts[q].parent_part) % cn::kLanes) << cn::kPsrcShift;
+        f |= cn::kProotBit | (int32_t)((uint32_t)(warp_mail0[c] + q - 1) << cn::kPmailShift);
       for (size_t q2 = 1; q2 < P.parts.size(); ++q2)
-        if (P.parts[q2].jnode == li) f |= cn::kJuncBit | ((l0 + (int)q2) % cn::kLanes) << cn::kJsrcShift;
+        if (P.parts[q2].jnode == li) f |= cn::kJuncBit | ((warp_mail0[c] + (int)q2 - 1) << cn::kJmailShift);
       L.node_flags[node] = f;
     }
   }
@@ -547,7 +676,8 @@ cn_status finalize(cn_model* m) {
   Layout L;
   {
     std::string lerr;
-    if (!build_layout(m->n_cells, m->off.data(), m->parent.data(), cell_mask.data(), target, L, lerr))
+    if (!build_layout(m->n_cells, m->off.data(), m->parent.data(), cell_mask.data(), m->spike_node.data(), target,
+                      !m->dense && m->ck_steps <= 0, (m->opt.mapping & CN_MAP_TALL) != 0, L, lerr))
       return m->fail(CN_EINVAL, lerr);
   }
   const int depth = L.depth;
@@ -559,13 +689,11 @@ cn_status finalize(cn_model* m) {
   std::vector<int32_t> slot_gid(m->n_slots, -1), slot_rows(m->n_slots, 0), slot_spike(m->n_slots, 0),
       slot_cell(m->n_slots, -1);
   std::vector<double> slot_thresh(m->n_slots, 0.0);
+  for (int sl = 0; sl < m->n_slots; ++sl) {
+    slot_cell[sl] = L.lane_cell[sl];
+    slot_rows[sl] = L.lane_rows[sl];
+  }
   for (int c = 0; c < m->n_cells; ++c) {
-    const CellPlan& P = L.plans[c];
-    for (size_t q = 0; q < P.parts.size(); ++q) {
-      const int sl = L.cell_lane0[c] + (int)q;
-      slot_cell[sl] = c;
-      slot_rows[sl] = P.parts[q].base + (int)P.parts[q].nodes.size();
-    }
     const int64_t sn = m->off[c] + m->spike_node[c];
     const int ss = m->node_slot[sn];
     slot_gid[ss] = c;
@@ -598,14 +726,13 @@ cn_status finalize(cn_model* m) {
     }
     return row_slot[node];
   };
-  std::vector<int32_t> syn_slotid(m->syn_node.size()), hh_slotid(m->hh_node.size()), st_slotid(m->st_node.size());
-  for (size_t i = 0; i < m->syn_node.size(); ++i) syn_slotid[i] = slot_of_node(m->syn_node[i]);
+  std::vector<int32_t> hh_slotid(m->hh_node.size()), st_slotid(m->st_node.size());
   for (size_t i = 0; i < m->hh_node.size(); ++i) hh_slotid[i] = slot_of_node(m->hh_node[i]);
   for (size_t i = 0; i < m->st_node.size(); ++i) st_slotid[i] = slot_of_node(m->st_node[i]);
   int max_slots = 1;
   for (int sl = 0; sl < m->n_slots; ++sl) max_slots = std::max<int>(max_slots, (int)lane_slot_rows[sl].size());
   if (max_slots >= cn::kNoSlot) return m->fail(CN_EINVAL, "too many mechanism rows in one cell part");
-  const size_t smem = cn::interval_smem_bytes(depth, max_slots, m->dense);
+  const size_t smem = cn::interval_smem_bytes(depth, max_slots, m->dense, L.n_mail);
   if (smem > kMaxSmemPerBlock)
     return m->fail(CN_EINVAL, "cell needs " + std::to_string(smem) + " bytes of shared memory (slots " +
                                   std::to_string(max_slots) + ", stack " + std::to_string(depth) + ")");
@@ -619,6 +746,7 @@ cn_status finalize(cn_model* m) {
     h_elem[node] = e;
     h_flags[e] = L.node_flags[node] | (row_slot[node] >= 0 ? row_slot[node] : cn::kNoSlot);
   }
+  m->node_elem = h_elem;
   for (size_t q = 0; q < m->pas_node.size(); ++q) {
     int64_t e = node_elem(m->pas_node[q]);
     h_gp[e] = m->pas_g[q];
@@ -640,19 +768,19 @@ cn_status finalize(cn_model* m) {
     for (size_t t = 0; t < lane_slot_rows[sl].size(); ++t)
       h_slot_row[g_slot_base[sl / cn::kLanes] + (int64_t)t * cn::kLanes + sl % cn::kLanes] = lane_slot_rows[sl][t];
   // synapses, HH, stimuli, records
-  Rows rs = interleave(m, m->syn_node), rh = interleave(m, m->hh_node), rt = interleave(m, m->st_node),
+  Rows rs = interleave(m, m->syn_node, true), rh = interleave(m, m->hh_node), rt = interleave(m, m->st_node),
        rr = interleave(m, m->rec_node);
   m->syn_slot = rs.inst_slot; m->syn_q = rs.inst_q;
   m->hh_slot = rh.inst_slot; m->hh_q = rh.inst_q;
   m->g_syn_base = rs.g_base;
   m->g_hh_base = rh.g_base;
   m->syn_elems = rs.elems; m->hh_elems = rh.elems; m->st_elems = rt.elems; m->rec_elems = rr.elems;
-  std::vector<int32_t> h_syn_slot(rs.elems, 0);
+  std::vector<int32_t> h_syn_row(rs.elems, -1);
   std::vector<double> h_syn_tau(rs.elems, 1.0), h_syn_e(rs.elems, 0.0), h_syn_area(rs.elems, 1.0),
       h_syn_cm(rs.elems, 1.0);
   for (size_t i = 0; i < m->syn_node.size(); ++i) {
     int64_t e = elem_of(rs, i);
-    h_syn_slot[e] = syn_slotid[i];
+    h_syn_row[e] = m->node_row[m->syn_node[i]];
     h_syn_tau[e] = m->syn_tau[i];
     h_syn_e[e] = m->syn_e[i];
     h_syn_area[e] = m->area[m->syn_node[i]];
@@ -661,8 +789,10 @@ cn_status finalize(cn_model* m) {
   std::vector<int32_t> h_hh_row(rh.elems, 0), h_hh_slot(rh.elems, 0);
   std::vector<double> h_hh_p(6 * rh.elems, 0.0), h_hh_cm(rh.elems, 1.0);
   size_t nhh = m->hh_node.size();
+  m->hh_elem.assign(nhh, 0);
   for (size_t i = 0; i < nhh; ++i) {
     int64_t e = elem_of(rh, i);
+    m->hh_elem[i] = e;
     h_hh_row[e] = m->node_row[m->hh_node[i]];
     h_hh_slot[e] = hh_slotid[i];
     h_hh_cm[e] = m->cm[m->hh_node[i]];
@@ -746,6 +876,7 @@ cn_status finalize(cn_model* m) {
   dm.n_rec = (int32_t)m->rec_node.size();
   dm.max_slots = max_slots;
   dm.stack_depth = depth;
+  dm.n_mail = L.n_mail;
   dm.node_elems = acc;
   dm.dt = dt;
   int64_t* p64;
@@ -784,7 +915,7 @@ cn_status finalize(cn_model* m) {
   CN_CHECK(upload(m, &p32, h_slot_row)); dm.slot_row = p32;
   CN_CHECK(zeros(m, &pd, std::max<int64_t>(sacc, 1))); dm.slot_ge0 = pd;
   CN_CHECK(zeros(m, &pd, std::max<int64_t>(sacc, 1))); dm.slot_d00 = pd;
-  CN_CHECK(upload(m, &p32, h_syn_slot)); dm.syn_slot = p32;
+  CN_CHECK(upload(m, &p32, h_syn_row)); dm.syn_row = p32;
   CN_CHECK(zeros(m, &pd, rs.elems)); dm.syn_g = pd;
   CN_CHECK(zeros(m, &pd, rs.elems)); dm.syn_s = pd;
   CN_CHECK(upload(m, &pd, h_syn_e)); dm.syn_e = pd;
@@ -968,7 +1099,10 @@ cudaEvent_t take_event(cn_model* m) {
 // pull at the interval start, the interval kernel, and the device-side
 // interval index bump once the interval is complete.  ev, when given, holds
 // four events recorded around the pull and the interval kernel.
-cn_status enqueue_interval(cn_model* m, cudaStream_t st, int64_t J, int s0, int s1, cudaEvent_t* ev) {
+cn_status enqueue_interval(cn_model* m, cudaStream_t st, int64_t J, int s0, int s1, cudaEvent_t* ev,
+                           bool capturing = false) {
+  // inside a capture an event becomes a record node only when marked external
+  const unsigned rec_flags = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
   cn::DevModel dm = m->dm;
   const int64_t* Jp = dm.jdev;
   const int wpb = m->wpb;
@@ -976,11 +1110,11 @@ cn_status enqueue_interval(cn_model* m, cudaStream_t st, int64_t J, int s0, int 
   const size_t smem = (size_t)wpb * m->smem_bytes;
   if (s0 == 0) {
     const int tb = 128, nb = (m->n_slots + tb - 1) / tb;
-    if (ev) CN_TRY_CUDA(m, cudaEventRecord(ev[0], st));
+    if (ev) CN_TRY_CUDA(m, cudaEventRecordWithFlags(ev[0], st, rec_flags));
     CN_CHECK(launch_checked(m, [&] { cn::k_pull_events<<<nb, tb, 0, st>>>(dm, J, Jp); }));
-    if (ev) CN_TRY_CUDA(m, cudaEventRecord(ev[1], st));
+    if (ev) CN_TRY_CUDA(m, cudaEventRecordWithFlags(ev[1], st, rec_flags));
   }
-  if (ev) CN_TRY_CUDA(m, cudaEventRecord(ev[2], st));
+  if (ev) CN_TRY_CUDA(m, cudaEventRecordWithFlags(ev[2], st, rec_flags));
   switch (m->opt.precision) {
     case CN_PREC_FP64:
       if (m->dense) CN_CHECK(launch_checked(m, [&] { cn::k_interval<0, false, true><<<blocks, 32 * wpb, smem, st>>>(dm, J, s0, s1, Jp); }));
@@ -995,7 +1129,7 @@ cn_status enqueue_interval(cn_model* m, cudaStream_t st, int64_t J, int s0, int 
       else CN_CHECK(launch_checked(m, [&] { cn::k_interval<2, false, false><<<blocks, 32 * wpb, smem, st>>>(dm, J, s0, s1, Jp); }));
       break;
   }
-  if (ev) CN_TRY_CUDA(m, cudaEventRecord(ev[3], st));
+  if (ev) CN_TRY_CUDA(m, cudaEventRecordWithFlags(ev[3], st, rec_flags));
   if (s1 == m->D) CN_CHECK(launch_checked(m, [&] { cn::k_next_interval<<<1, 1, 0, st>>>(dm.jdev); }));
   return CN_OK;
 }
@@ -1060,7 +1194,7 @@ cn_status capture_chunk(cn_model* m, int c) {
   cn_status st = CN_OK;
   const int64_t launches = m->launches;
   for (int i = 0; i < kGraphIntervals && st == CN_OK; ++i)
-    st = enqueue_interval(m, m->cap_stream, 0, 0, m->D, m->profiling ? g.ev.data() + 4 * i : nullptr);
+    st = enqueue_interval(m, m->cap_stream, 0, 0, m->D, m->profiling ? g.ev.data() + 4 * i : nullptr, true);
   m->launches = launches;  // captured, not launched
   cudaError_t e = cudaStreamEndCapture(m->cap_stream, &graph);
   if (st != CN_OK) {
@@ -1151,9 +1285,12 @@ cn_status autotune(cn_model* m) {
   const int64_t mean = std::max<int64_t>(1, (m->n_nodes + m->n_cells - 1) / std::max(1, m->n_cells));
   std::vector<int32_t> cand{CN_MAP_THREAD};
   if (m->ck_steps <= 0)
-    for (int64_t t : {mean / 4, mean / 2, mean, 2 * mean}) {
+    for (int64_t t : {mean / 8, mean / 4, mean / 2, mean}) {
       const int32_t v = (int32_t)std::max<int64_t>(16, t);
-      if (v < mean * 4 && std::find(cand.begin(), cand.end(), v) == cand.end()) cand.push_back(v);
+      if (std::find(cand.begin(), cand.end(), v) == cand.end()) {
+        cand.push_back(v);
+        if (!m->dense) cand.push_back(v | CN_MAP_TALL);
+      }
     }
   float best = 0.f;
   int32_t best_map = CN_MAP_THREAD, best_wpb = 1;
@@ -1311,8 +1448,8 @@ cn_status cn_plan_layout(int32_t n_cells, const int32_t* cell_offset, const int3
   if (!valid_trees(n_cells, cell_offset, parent, g_create_error)) return CN_EINVAL;
   const int64_t nn = cell_offset[n_cells];
   Layout L;
-  if (!build_layout(n_cells, cell_offset, parent, nullptr, map_target(mapping, nn, n_cells, false), L,
-                    g_create_error))
+  if (!build_layout(n_cells, cell_offset, parent, nullptr, nullptr, map_target(mapping, nn, n_cells, false), true,
+                    (mapping & CN_MAP_TALL) != 0, L, g_create_error))
     return CN_EINVAL;
   if (node_lane) std::copy(L.node_slot.begin(), L.node_slot.end(), node_lane);
   if (node_row) std::copy(L.node_row.begin(), L.node_row.end(), node_row);
@@ -1338,7 +1475,11 @@ cn_status cn_model_create(const cn_morph* morph, const cn_mech_table* mechs, int
   if (o.precision < 0 || o.precision > 2) return bad("bad precision");
   if ((o.alloc == nullptr) != (o.free == nullptr)) return bad("alloc and free must be given together");
   if (o.warps_per_block < 0 || o.warps_per_block > cn::kMaxWarpsPerBlock) return bad("warps_per_block must be 0..4");
-  if (o.mapping < 0 || (o.mapping > CN_MAP_TUNE && o.mapping < 16)) return bad("mapping must be 0, 1, 2 or >= 16");
+  {
+    const int32_t mv = o.mapping & ~CN_MAP_TALL;
+    if (o.mapping < 0 || (mv > CN_MAP_TUNE && mv < 16) || ((o.mapping & CN_MAP_TALL) && mv < 16))
+      return bad("mapping must be 0, 1, 2, or a span >= 16 (optionally with CN_MAP_TALL)");
+  }
   const int32_t nc = morph->n_cells;
   if (nc <= 0 || !morph->cell_offset || !morph->parent || !morph->area_um2 || !morph->cm_uF_cm2 ||
       !morph->ri_MOhm || !morph->spike_node || !morph->threshold_mV)
@@ -1696,30 +1837,54 @@ cn_status cn_reset(cn_model* m) {
   return reset_state(m);
 }
 
-static cn_status cell_values_to_slots(cn_model* m, const double* values, double** d_out) {
-  std::vector<double> h(m->n_slots, 0.0);
-  for (int c = 0; c < m->n_cells; ++c)
-    if (!std::isfinite(values[c])) return m->fail(CN_EINVAL, "non-finite parameter value");
-  for (int sl = 0; sl < m->n_slots; ++sl)
-    if (m->slot_cell[sl] >= 0) h[sl] = values[m->slot_cell[sl]];
-  return upload(m, d_out, h);
+// Element indices and cells of the instances a per-cell parameter covers:
+// HH instances (gnabar, gkbar) or rows carrying pas (g).
+static void param_targets(const cn_model* m, int32_t param, std::vector<int64_t>& idx, std::vector<int32_t>& cell) {
+  idx.clear();
+  cell.clear();
+  if (param < 2) {
+    for (size_t i = 0; i < m->hh_node.size(); ++i) {
+      idx.push_back((int64_t)param * m->hh_elems + m->hh_elem[i]);
+      cell.push_back(m->node_cell[m->hh_node[i]]);
+    }
+  } else {
+    for (size_t i = 0; i < m->pas_node.size(); ++i) {
+      idx.push_back(m->node_elem[m->pas_node[i]]);
+      cell.push_back(m->node_cell[m->pas_node[i]]);
+    }
+  }
 }
 
 cn_status cn_set_cell_param(cn_model* m, int32_t param, const double* values) {
   if (!m || !values || param < 0 || param > 2) return m ? m->fail(CN_EINVAL, "bad parameter id") : CN_EINVAL;
+  for (int c = 0; c < m->n_cells; ++c)
+    if (!std::isfinite(values[c])) return m->fail(CN_EINVAL, "non-finite parameter value");
   CN_TRY_CUDA(m, cudaSetDevice(m->opt.device));
   CN_CHECK(prepare(m));
   CN_CHECK(ensure_capacity(m, m->step));
-  double* d = nullptr;
-  CN_CHECK(cell_values_to_slots(m, values, &d));
+  std::vector<int64_t> idx;
+  std::vector<int32_t> cell;
+  param_targets(m, param, idx, cell);
   const int tb = 128, nb = (m->n_slots + tb - 1) / tb;
   cn::DevModel dm = m->dm;
-  CN_CHECK(launch_checked(m, [&] { cn::k_set_cell_param<<<nb, tb, 0, m->stream>>>(dm, param, d); }));
+  if (!idx.empty()) {
+    std::vector<double> val(idx.size());
+    for (size_t i = 0; i < idx.size(); ++i) val[i] = values[cell[i]];
+    int64_t* d_idx;
+    double* d_val;
+    CN_CHECK(upload(m, &d_idx, idx));
+    CN_CHECK(upload(m, &d_val, val));
+    double* dst = param < 2 ? const_cast<double*>(dm.hh_raw) : const_cast<double*>(dm.pas_g);
+    const int64_t n = (int64_t)idx.size();
+    CN_CHECK(launch_checked(m, [&] { cn::k_scatter<<<(unsigned)((n + 255) / 256), 256, 0, m->stream>>>(dst, d_idx, d_val, n); }));
+    CN_TRY_CUDA(m, cudaStreamSynchronize(m->stream));
+    dfree_raw(m, d_idx);
+    dfree_raw(m, d_val);
+  }
   if (param < 2) CN_CHECK(launch_checked(m, [&] { cn::k_hh_params<<<nb, tb, 0, m->stream>>>(dm); }));
   else CN_CHECK(launch_checked(m, [&] { cn::k_pas_apply<<<nb, tb, 0, m->stream>>>(dm); }));
   CN_CHECK(launch_checked(m, [&] { cn::k_setup_slots<<<nb, tb, 0, m->stream>>>(dm); }));
   CN_TRY_CUDA(m, cudaStreamSynchronize(m->stream));
-  dfree_raw(m, d);
   return CN_OK;
 }
 
@@ -1727,16 +1892,27 @@ cn_status cn_get_cell_param(cn_model* m, int32_t param, double* values) {
   if (!m || !values || param < 0 || param > 2) return m ? m->fail(CN_EINVAL, "bad parameter id") : CN_EINVAL;
   CN_TRY_CUDA(m, cudaSetDevice(m->opt.device));
   CN_CHECK(prepare(m));
-  double* d = nullptr;
-  CN_CHECK(zeros(m, &d, m->n_slots));
-  const int tb = 128, nb = (m->n_slots + tb - 1) / tb;
-  cn::DevModel dm = m->dm;
-  CN_CHECK(launch_checked(m, [&] { cn::k_get_cell_param<<<nb, tb, 0, m->stream>>>(dm, param, d); }));
-  std::vector<double> h(m->n_slots);
-  CN_TRY_CUDA(m, cudaMemcpyAsync(h.data(), d, h.size() * 8, cudaMemcpyDeviceToHost, m->stream));
+  std::vector<int64_t> idx;
+  std::vector<int32_t> cell;
+  param_targets(m, param, idx, cell);
+  for (int c = 0; c < m->n_cells; ++c) values[c] = 0.0;
+  if (idx.empty()) return CN_OK;
+  int64_t* d_idx;
+  double* d_out;
+  CN_CHECK(upload(m, &d_idx, idx));
+  CN_CHECK(zeros(m, &d_out, idx.size()));
+  const double* src = param < 2 ? m->dm.hh_raw : m->dm.pas_g;
+  const int64_t n = (int64_t)idx.size();
+  CN_CHECK(launch_checked(m, [&] { cn::k_gather<<<(unsigned)((n + 255) / 256), 256, 0, m->stream>>>(src, d_idx, d_out, n); }));
+  std::vector<double> h(idx.size());
+  CN_TRY_CUDA(m, cudaMemcpyAsync(h.data(), d_out, h.size() * 8, cudaMemcpyDeviceToHost, m->stream));
   CN_TRY_CUDA(m, cudaStreamSynchronize(m->stream));
-  dfree_raw(m, d);
-  for (int c = 0; c < m->n_cells; ++c) values[c] = h[m->cell_slot[c]];
+  dfree_raw(m, d_idx);
+  dfree_raw(m, d_out);
+  // the value of a cell's first instance (the engine keeps them equal)
+  std::vector<uint8_t> seen(m->n_cells, 0);
+  for (size_t i = 0; i < idx.size(); ++i)
+    if (!seen[cell[i]]++) values[cell[i]] = h[i];
   return CN_OK;
 }
 

@@ -83,41 +83,16 @@ __global__ void k_hh_params(DevModel M) {
   }
 }
 
-// Per-cell parameter update: HH gnabar (0) or gkbar (1) of every HH instance
-// of the cell, or pas g (2) of every row carrying pas.  value[slot].
-__global__ void k_set_cell_param(DevModel M, int32_t param, const double* value) {
-  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
-  if (slot >= M.n_slots || M.s_gid[slot] < 0) return;
-  const int g = slot / kLanes, lane = slot % kLanes;
-  const double x = value[slot];
-  if (param < 2) {
-    const int n = M.s_nhh[slot];
-    const int64_t base = M.g_hh_base[g] + lane;
-    for (int q = 0; q < n; ++q) M.hh_raw[param * M.hh_elems + base + (int64_t)q * kLanes] = x;
-  } else {
-    const int64_t nb = M.g_node_base[g] + lane;
-    for (int j = 0; j < M.g_rows[g]; ++j) {
-      const int64_t i = nb + (int64_t)j * kLanes;
-      if (M.flags[i] & kHasPasBit) M.pas_g[i] = x;
-    }
-  }
+// Parameter scatter / gather by element index (per-cell conductances are
+// expanded to their instances on the host): dst[idx[i]] = val[i] and
+// out[i] = src[idx[i]].
+__global__ void k_scatter(double* dst, const int64_t* idx, const double* val, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[idx[i]] = val[i];
 }
-
-// Per-cell parameter read-back (value[slot]).
-__global__ void k_get_cell_param(DevModel M, int32_t param, double* value) {
-  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
-  if (slot >= M.n_slots) return;
-  const int g = slot / kLanes, lane = slot % kLanes;
-  double x = 0.0;
-  if (param < 2) {
-    if (M.s_nhh[slot] > 0) x = M.hh_raw[param * M.hh_elems + M.g_hh_base[g] + lane];
-  } else {
-    const int N = M.s_rows[slot];
-    const int64_t nb = M.g_node_base[g] + lane;
-    for (int j = N - 1; j >= 0; --j)
-      if (M.flags[nb + (int64_t)j * kLanes] & kHasPasBit) x = M.pas_g[nb + (int64_t)j * kLanes];
-  }
-  value[slot] = x;
+__global__ void k_gather(const double* src, const int64_t* idx, double* out, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = src[idx[i]];
 }
 
 // Initial state: v = v_init (0 on rows past the cell's end), HH gates at
@@ -436,7 +411,7 @@ __global__ void k_setup_dense(DevModel M, double v_init, bool scale_gbar) {
 // into the trajectory buffers, and leave spikes, threshold flags and traces
 // untouched.
 template <int PREC, bool TRAJ, bool DENSE>
-__global__ void __launch_bounds__(kMaxWarpsPerBlock * 32)
+__global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 4)
     k_interval(DevModel M, int64_t J, int s_begin, int s_end, const int64_t* Jp) {
   using S = typename GateT<PREC>::S;
   using T = typename GateT<PREC>::M;
@@ -464,12 +439,16 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32)
   double* const b_x = reinterpret_cast<double*>(smem) + lane;
   double* const b_bp = b_x + kBackRows * kLanes;
   int32_t* const b_fl = reinterpret_cast<int32_t*>(reinterpret_cast<double*>(smem) + 2 * kBackRows * kLanes) + lane;
-  double* const st_a = reinterpret_cast<double*>(smem + ring_bytes()) + lane;  // far stack [DS][32] each
+  double* const wsm = reinterpret_cast<double*>(smem + ring_bytes());
+  double* const st_a = wsm + lane;  // far stack [DS][32] each
   double* const st_x = st_a + DS * kLanes;
   double* const st_y = st_x + DS * kLanes;
   double* const sl_ge = st_y + DS * kLanes;  // slot buffer [max_slots][32]
   double* const sl_d = sl_ge + M.max_slots * kLanes;
   double* const kin = sl_d + M.max_slots * kLanes;  // dense kinetics [kChanParams][32]
+  // mailbox [n_mail][4] shared by the warp: a part root leaves (-a, x, b/d)
+  // for its junction row, the junction row leaves v for the part root
+  double* const mail = wsm + (3 * DS + 2 * M.max_slots + (DENSE ? kChanParams : 0)) * kLanes;
   const int chmask = DENSE ? M.g_chmask[g] : 0;
   if (DENSE)
     for (int q = 0; q < kChanParams; ++q) kin[q * kLanes] = M.ch_kin[(int64_t)q * M.n_slots + slot];
@@ -485,7 +464,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32)
 
   const int SLR = M.g_slot_rows[g], nslot = M.s_nslot[slot];
   const int64_t slb = M.g_slot_base[g] + lane;
-  const int SR = M.g_syn_rows[g], nsyn = M.s_nsyn[slot];
+  const int nsyn = M.s_nsyn[slot];
   const int64_t sb = M.g_syn_base[g] + lane;
   const int HR = M.g_hh_rows[g], nhh = M.s_nhh[slot];
   const int64_t hb = M.g_hh_base[g] + lane;
@@ -549,36 +528,33 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32)
       M.syn_g[sb + (int64_t)ev[ei].syn * kLanes] += ev[ei].w;
       ++ei;
     }
-    // (2) nrn_cur into the slot buffer; synapses in batches of 8 so that
-    //     their loads are in flight together
-    constexpr int kSynBatch = 8;
-    for (int q0 = 0; q0 < SR; q0 += kSynBatch) {
-      double gs[kSynBatch], ss[kSynBatch], se[kSynBatch], sd[kSynBatch];
-      int st[kSynBatch];
-#pragma unroll
-      for (int u = 0; u < kSynBatch; ++u) {
-        const int q = q0 + u;
-        if (q < nsyn) {
-          const int64_t i = sb + (int64_t)q * kLanes;
-          gs[u] = M.syn_g[i];
-          ss[u] = M.syn_s[i];
-          se[u] = M.syn_e[i];
-          sd[u] = M.syn_decay[i];
-          st[u] = M.syn_slot[i];
-        }
+    // (2) nrn_cur: HH and IClamp into the slot buffer; the synapses of the
+    //     lane are merged into the elimination below, in row order
+    // Two synapses are kept in registers (the current one and the next) so
+    // that a synapse's loads are issued one synapse ahead of its row.
+    int sq = 0, srow = -1, srow2 = -1;
+    int64_t si_ = 0, si2 = 0;
+    double ng = 0.0, ns_ = 0.0, ne_ = 0.0, nd_ = 0.0;
+    double ng2 = 0.0, ns2 = 0.0, ne2 = 0.0, nd2 = 0.0;
+    auto load_syn = [&]() {  // the lane's synapse sq (rows descending) into the second stage
+      if (sq < nsyn) {
+        si2 = sb + (int64_t)sq * kLanes;
+        srow2 = M.syn_row[si2];
+        ng2 = M.syn_g[si2];
+        ns2 = M.syn_s[si2];
+        ne2 = M.syn_e[si2];
+        nd2 = M.syn_decay[si2];
+        ++sq;
+      } else {
+        srow2 = -1;
       }
-#pragma unroll
-      for (int u = 0; u < kSynBatch; ++u) {
-        const int q = q0 + u;
-        if (q < nsyn) {
-          const double G = gs[u] * ss[u];
-          const int t = st[u] * kLanes;
-          sl_ge[t] = fma(G, se[u], sl_ge[t]);
-          sl_d[t] += G;
-          M.syn_g[sb + (int64_t)q * kLanes] = gs[u] * sd[u];  // ExpSyn state update: v-independent
-        }
-      }
-    }
+    };
+    auto next_syn = [&]() {
+      srow = srow2; si_ = si2; ng = ng2; ns_ = ns2; ne_ = ne2; nd_ = nd2;
+      load_syn();
+    };
+    load_syn();
+    next_syn();
     for (int q = 0; q < HR; ++q) {
       if (q < nhh) {
         const int64_t i = hb + (int64_t)q * kLanes;
@@ -606,7 +582,6 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32)
     //     pops it into two FMAs (zero coefficients on rows that pop
     //     nothing); the previous row's carry enters the same way.
     double ca = 0.0, cx = 0.0, cb = 0.0, x = 0.0;
-    double pub_a = 0.0, pub_x = 0.0, pub_b = 0.0;
     int top = 0;
     for (int jb = R - 1; jb >= 0; jb -= kElimRows) {
 #pragma unroll
@@ -633,8 +608,16 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32)
           const double fx = np > 0 ? st_x[ti] : 0.0;
           const double fb = np > 0 ? st_y[ti] : 0.0;
           top = tp;
-          double base = e_v[ro] + (hs ? sg : g0);
+          double acc_ge = hs ? sg : g0;
           double dd0 = hs ? sd : d00;
+          while (srow == j) {  // ExpSyn G and G E at this row; then its decay (v-independent)
+            const double G = ng * ns_;
+            acc_ge = fma(G, ne_, acc_ge);
+            dd0 += G;
+            M.syn_g[si_] = ng * nd_;
+            next_syn();
+          }
+          double base = e_v[ro] + acc_ge;
           if (DENSE) {
             double Gc, GEc;
             dense_cur<PREC>(M, chmask, nb + (int64_t)j * kLanes, e_v[ro], kin, Gc, GEc);
@@ -648,17 +631,15 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32)
             rhs = fma(st_a[top * kLanes], st_x[top * kLanes], rhs);
             d = fma(st_a[top * kLanes], st_y[top * kLanes], d);
           }
-          // a part of this cell in another lane hangs from this row: its root
-          // was eliminated one warp row earlier and published (-a, x, b/d)
+          // a part of this cell hangs from this row: its root was eliminated
+          // at a higher warp row and left (-a, x, b/d) in the mailbox
           const bool jn = (f & kJuncBit) != 0;
           if (__any_sync(0xffffffffu, jn)) {
-            const int src = (f >> kJsrcShift) & 31;
-            const double qa = __shfl_sync(0xffffffffu, pub_a, src);
-            const double qx = __shfl_sync(0xffffffffu, pub_x, src);
-            const double qb = __shfl_sync(0xffffffffu, pub_b, src);
+            __syncwarp();
             if (jn) {
-              rhs = fma(qa, qx, rhs);
-              d = fma(qa, qb, d);
+              const double* q = mail + 4 * ((f >> kJmailShift) & kMailMask);
+              rhs = fma(q[0], q[1], rhs);
+              d = fma(q[0], q[2], d);
             }
           }
           rhs = fma(ca, cx, rhs);
@@ -675,10 +656,11 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32)
             st_x[top * kLanes] = x;
             st_y[top * kLanes] = bp;
           }
-          if (f & kProotBit) {  // the parent row lives in another lane
-            pub_a = na;
-            pub_x = x;
-            pub_b = bp;
+          if (f & kProotBit) {  // the parent row lies below, possibly in another lane
+            double* q = mail + 4 * (((uint32_t)f >> kPmailShift) & kMailMask);
+            q[0] = na;
+            q[1] = x;
+            q[2] = bp;
           }
           top += far ? 1 : 0;
           ca = (far || (f & kProotBit)) ? 0.0 : na;
@@ -706,14 +688,16 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32)
           const int tp = far ? top - 1 : top;
           const double pv = st_x[(tp < DS ? tp : DS - 1) * kLanes];
           double vp = far ? pv : vprev;
-          // root of a part whose parent row (one warp row down) is in another lane
+          // root of a part: its parent row was back-substituted at a lower
+          // warp row and left v in the mailbox
           const bool pr = (f & kProotBit) != 0;
           if (__any_sync(0xffffffffu, pr)) {
-            const double qv = __shfl_sync(0xffffffffu, vprev, (f >> kPsrcShift) & 31);
-            if (pr) vp = qv;
+            __syncwarp();
+            if (pr) vp = mail[4 * (((uint32_t)f >> kPmailShift) & kMailMask) + 3];
           }
           const double vj = fma(-b_bp[ro], vp, b_x[ro]);
           gv[(int64_t)j * kLanes] = vj;
+          if (f & kJuncBit) mail[4 * ((f >> kJmailShift) & kMailMask) + 3] = vj;
           if (DENSE && (f & kRealBit)) dense_state<PREC>(M, chmask, nb + (int64_t)j * kLanes, vj, kin);
           if (TRAJ) M.traj_v[(k + 1 - M.traj_k0) * M.node_elems + nb + (int64_t)j * kLanes] = vj;
           const int np = (f >> kNFarShift) & kNFarMask;

@@ -197,7 +197,7 @@ def test_event_buffer_overflow_reported(cn):
     assert e.value.status == cn.CN_ERANGE
 
 
-@pytest.mark.parametrize("mapping", [1, 40, 100])
+@pytest.mark.parametrize("mapping", [1, 40, 100, 16 | (1 << 20), 64 | (1 << 20)])
 def test_split_cells_over_lanes(cn, mapping):
     """The same driven network with one cell per lane (mapping 1) and with
     cells cut into parts of about 40 or 100 rows spread over lanes of one

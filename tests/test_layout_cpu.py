@@ -3,10 +3,11 @@
 cn_plan_layout returns, for every node, the lane and warp row the engine
 gives it and the topology bits the interval kernel reads.  These tests check
 the invariants the kernel relies on (Hines order inside every part, a part
-root exactly one warp row after its junction row in another lane of the same
-warp, far-child stack discipline within the reported depth), and then run the
-kernel's elimination schedule on random tree systems in NumPy, following only
-the placement: the solution must equal a direct sparse solve."""
+root above its junction row in the same warp with matching mailbox entries,
+one spike source per lane, far-child stack discipline within the reported
+depth), and then run the kernel's elimination schedule on random tree
+systems in NumPy, following only the placement: the solution must equal a
+direct sparse solve."""
 import numpy as np
 import pytest
 import scipy.sparse as sp
@@ -14,7 +15,19 @@ import scipy.sparse.linalg as spla
 
 from scenarios import network, batched, passive_cable, ring16
 
-FAR, REAL, JUNC, PROOT = 1 << 12, 1 << 17, 1 << 18, 1 << 24
+FAR, REAL, JUNC, PROOT = 1 << 6, 1 << 11, 1 << 12, 1 << 13
+
+
+def nfar(f):
+    return (f >> 7) & 7
+
+
+def jmail(f):
+    return (int(f) >> 14) & 511
+
+
+def pmail(f):
+    return (int(f) & 0xffffffff) >> 23
 
 
 @pytest.fixture(scope="module")
@@ -42,31 +55,27 @@ def check_invariants(off, parent, L):
         lo, hi = off[c], off[c + 1]
         lanes = np.unique(lane[lo:hi])
         assert np.all(lanes // 32 == lanes[0] // 32), "a cell spans two warps"
-        # each lane of the cell holds one contiguous run of rows
-        for l in lanes:
-            r = np.sort(row[lo:hi][lane[lo:hi] == l])
-            assert np.all(np.diff(r) == 1)
+        assert not (fl[lo] & PROOT)
         for i in range(lo + 1, hi):
             p = lo + parent[i]
-            if lane[i] == lane[p]:
-                assert not (fl[i] & PROOT)
-                if fl[i] & FAR:
-                    assert row[p] < row[i] - 1
-                    nfar_seen[p] += 1
-                else:
-                    assert row[p] == row[i] - 1
+            if fl[i] & PROOT:
+                assert fl[p] & JUNC and jmail(fl[p]) == pmail(fl[i])
+                assert row[i] > row[p]
+            elif fl[i] & FAR:
+                assert lane[i] == lane[p] and row[p] < row[i] - 1
+                nfar_seen[p] += 1
             else:
-                assert fl[i] & PROOT and ((fl[i] >> 25) & 31) == lane[p] % 32
-                assert fl[p] & JUNC and ((fl[p] >> 19) & 31) == lane[i] % 32
-                assert row[i] == row[p] + 1
-        root_lane = lane[lo]
-        assert not (fl[lo] & PROOT) and row[lo] == row[lo:hi][lane[lo:hi] == root_lane].min()
-    assert np.array_equal((fl >> 13) & 7, nfar_seen)
-    # every lane is used by at most one cell
-    owner = {}
-    for c in range(len(off) - 1):
-        for l in np.unique(lane[off[c]:off[c + 1]]):
-            assert owner.setdefault(int(l), c) == c
+                assert lane[i] == lane[p] and row[p] == row[i] - 1
+    assert np.array_equal(nfar(fl), nfar_seen)
+    # a mailbox entry joins exactly one junction and one part root per warp
+    for w in range(L["n_warps"]):
+        sel = lane // 32 == w
+        js = sorted(jmail(f) for f in fl[sel] if f & JUNC)
+        ps = sorted(pmail(f) for f in fl[sel] if f & PROOT)
+        assert js == ps and len(set(js)) == len(js)
+    # one spike source (the cell's first node) per lane
+    roots = lane[off[:-1]]
+    assert np.unique(roots).shape[0] == roots.shape[0]
 
 
 def emulate_solve(off, parent, L, a, b, d, rhs):
@@ -90,10 +99,9 @@ def emulate_solve(off, parent, L, a, b, d, rhs):
             continue
         stack = {l: [] for l in lanes}
         carry = {l: None for l in lanes}
-        pub = {l: None for l in lanes}
+        mail = {}
         maxtop = 0
         for j in range(R - 1, -1, -1):
-            new_pub = {}
             for l in lanes:
                 i = at.get((l, j))
                 if i is None:
@@ -101,13 +109,12 @@ def emulate_solve(off, parent, L, a, b, d, rhs):
                     continue
                 f = int(fl[i])
                 r_, d_ = rhs[i], d[i]
-                nf = (f >> 13) & 7
-                for _ in range(nf):
+                for _ in range(nfar(f)):
                     na, xx, bb = stack[l].pop()
                     r_ += na * xx
                     d_ += na * bb
                 if f & JUNC:
-                    na, xx, bb = pub[(l // 32) * 32 + ((f >> 19) & 31)]
+                    na, xx, bb = mail.pop(jmail(f))
                     r_ += na * xx
                     d_ += na * bb
                 if carry[l] is not None:
@@ -122,17 +129,17 @@ def emulate_solve(off, parent, L, a, b, d, rhs):
                     stack[l].append(ent)
                     maxtop = max(maxtop, len(stack[l]))
                 elif f & PROOT:
-                    new_pub[l] = ent
+                    assert pmail(f) not in mail
+                    mail[pmail(f)] = ent
                 else:
                     carry[l] = ent
-            pub.update(new_pub)
-        assert all(len(s) == 0 for s in stack.values())
+        assert all(len(s) == 0 for s in stack.values()) and not mail
         assert maxtop <= depth
         # back substitution, root to leaves
         vstack = {l: [] for l in lanes}
         vprev = {l: 0.0 for l in lanes}
+        vmail = {}
         for j in range(R):
-            cur = {}
             for l in lanes:
                 i = at.get((l, j))
                 if i is None:
@@ -141,13 +148,14 @@ def emulate_solve(off, parent, L, a, b, d, rhs):
                 if f & FAR:
                     vp = vstack[l].pop()
                 elif f & PROOT:
-                    vp = vprev[(l // 32) * 32 + ((f >> 25) & 31)]
+                    vp = vmail.pop(pmail(f))
                 else:
                     vp = vprev[l]
                 v[i] = x[i] - bp[i] * vp
-                vstack[l].extend([v[i]] * ((f >> 13) & 7))
-                cur[l] = v[i]
-            vprev.update(cur)
+                if f & JUNC:
+                    vmail[jmail(f)] = v[i]
+                vstack[l].extend([v[i]] * nfar(f))
+                vprev[l] = v[i]
     return v
 
 
@@ -185,7 +193,7 @@ CASES = {
 
 
 @pytest.mark.parametrize("case", sorted(CASES))
-@pytest.mark.parametrize("mapping", [1, 16, 40, 100, 300, 0])
+@pytest.mark.parametrize("mapping", [1, 16, 40, 100, 300, 0, 16 | (1 << 20), 100 | (1 << 20)])
 def test_layout_invariants_and_emulated_solve(cn, case, mapping):
     off, parent = cells_of(CASES[case]())
     L = cn.cn_plan_layout(off, parent, mapping)
