@@ -252,6 +252,28 @@ int64_t cn_launch_count(const cn_model* m);
  * Parameters set with cn_set_cell_param are kept.                          */
 cn_status cn_reset(cn_model* m);
 
+/* Checkpoint / restart of the network (Section 3.4).  A checkpoint holds,
+ * in the model's input order (so it restores under any mapping), the state
+ * at the current step: every node voltage, every gating state and synaptic
+ * conductance, [Ca]i, the threshold flags, and, in place of the undelivered
+ * NetCon events, the spike history of the intervals that can still deliver
+ * (each delivery is re-derived from its source spike, as the paper collapses
+ * pending messages back into the firing event).
+ * cn_checkpoint_save: the step must be an interval boundary (a multiple of
+ * the minimum NetCon delay).  Two-call: with buf NULL, *n = bytes needed;
+ * otherwise writes *n bytes to the HOST buffer buf (cap >= *n).  Errors:
+ * CN_ESTATE (not at a boundary), CN_ERANGE (cap too small).
+ * cn_checkpoint_load: restores into a model built from the same morphology,
+ * mechanism placement and NetCons (checked by a fingerprint; parameters,
+ * stimuli and external events may differ), before or after its first run.
+ * The model continues from the checkpoint step with its OWN external events
+ * and stimuli at and after that step, so a restored network can be driven
+ * by new inputs.  Its raster reports spikes after the checkpoint step only;
+ * recorded traces start at that step.  Errors: CN_EINVAL (not a checkpoint,
+ * another network).                                                        */
+cn_status cn_checkpoint_save(cn_model* m, void* buf, size_t cap, size_t* n);
+cn_status cn_checkpoint_load(cn_model* m, const void* buf, size_t n);
+
 /* Per-cell maximal conductances (the adjoint's parameters): */
 typedef enum {
   CN_PARAM_GNABAR = 0,  /* gnabar of every HH instance of the cell (S/cm2) */
@@ -264,8 +286,8 @@ typedef enum {
 cn_status cn_set_cell_param(cn_model* m, int32_t param, const double* values);
 cn_status cn_get_cell_param(cn_model* m, int32_t param, double* values);
 
-/* Prepare the discrete adjoint of the FP64 run (the benchmark spec's
- * differentiation pattern; the paper has no adjoint): from step 0, cn_run
+/* Prepare the discrete adjoint of the FP64 run (an extension: the paper has
+ * no adjoint): from step 0, cn_run
  * stores the state (v, HH gates, synaptic g) every checkpoint_steps steps.
  * Needs FP64, no NetCons, no external events, at most one HH instance per
  * cell.  Errors: CN_ESTATE, CN_EINVAL.                                     */

@@ -74,6 +74,10 @@ def lib():
         L.cn_plan_layout.restype = st
         L.cn_get_mapping.argtypes = [C.c_void_p, _P_I32, _P_I32, _P_I32, C.POINTER(C.c_float)]
         L.cn_get_mapping.restype = st
+        L.cn_checkpoint_save.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t, C.POINTER(C.c_size_t)]
+        L.cn_checkpoint_save.restype = st
+        L.cn_checkpoint_load.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t]
+        L.cn_checkpoint_load.restype = st
         L.cn_model_create.argtypes = [C.POINTER(cn_morph), C.POINTER(cn_mech_table), C.c_int32,
                                       C.POINTER(cn_options), C.POINTER(C.c_void_p)]
         L.cn_model_create.restype = st
@@ -344,6 +348,17 @@ class Model:
 
     def cn_profile(self, enable=True):
         _check(lib().cn_profile(self._h, int(bool(enable))), self._h)
+
+    def cn_checkpoint_save(self) -> bytes:
+        """The network state at the current (interval-boundary) step."""
+        n = C.c_size_t(0)
+        _check(lib().cn_checkpoint_save(self._h, None, 0, C.byref(n)), self._h)
+        buf = C.create_string_buffer(n.value)
+        _check(lib().cn_checkpoint_save(self._h, buf, n.value, C.byref(n)), self._h)
+        return buf.raw[:n.value]
+
+    def cn_checkpoint_load(self, data: bytes):
+        _check(lib().cn_checkpoint_load(self._h, data, len(data)), self._h)
 
     def cn_get_mapping(self):
         """(mapping, warps per block, warps, autotuner's interval ms) of the layout in use."""

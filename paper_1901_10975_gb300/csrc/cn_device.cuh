@@ -138,6 +138,8 @@ struct DevModel {
   void* ch_gate[kChanGates];
   const double* ch_kin;
   double* cai;
+  double* ch_g;    // channel conductance of the row for the coming step, / cdt
+  double* ch_ge;   // its sum of g E, / cdt
   double* ica;
   // adjoint trajectory (recompute only)
   double* traj_v;           // [step - traj_k0][node_elems]
@@ -180,13 +182,14 @@ struct DevModel {
 constexpr int kElimRows = 4;
 constexpr int kBackRows = 8;
 
-__host__ __device__ inline size_t ring_bytes() {
-  const size_t elim = (size_t)kElimRows * kLanes * (5 * sizeof(double) + sizeof(int32_t));
+__host__ __device__ inline size_t ring_bytes(bool dense) {
+  // elimination: v, ge, d0, a, b (+ the channel G, G E) and flags per row
+  const size_t elim = (size_t)kElimRows * kLanes * ((dense ? 7 : 5) * sizeof(double) + sizeof(int32_t));
   const size_t back = (size_t)kBackRows * kLanes * (2 * sizeof(double) + sizeof(int32_t));
   return ((elim > back ? elim : back) + 15) / 16 * 16;
 }
 __host__ __device__ inline size_t interval_smem_bytes(int stack_depth, int max_slots, bool dense, int n_mail) {
-  return ring_bytes() + (size_t)stack_depth * kLanes * 3 * sizeof(double) +
+  return ring_bytes(dense) + (size_t)stack_depth * kLanes * 3 * sizeof(double) +
          (size_t)max_slots * kLanes * 2 * sizeof(double) +
          (dense ? (size_t)kChanParams * kLanes * sizeof(double) : 0) + (size_t)n_mail * 4 * sizeof(double);
 }
@@ -276,5 +279,13 @@ __device__ __forceinline__ float g_load(const __nv_bfloat16* p) { return __bfloa
 __device__ __forceinline__ void g_store(double* p, double x) { *p = x; }
 __device__ __forceinline__ void g_store(float* p, float x) { *p = x; }
 __device__ __forceinline__ void g_store(__nv_bfloat16* p, float x) { *p = __float2bfloat16_rn(x); }
+// Stores x and returns the value as stored (rounded for bfloat16).
+__device__ __forceinline__ double g_store_ret(double* p, double x) { *p = x; return x; }
+__device__ __forceinline__ float g_store_ret(float* p, float x) { *p = x; return x; }
+__device__ __forceinline__ float g_store_ret(__nv_bfloat16* p, float x) {
+  const __nv_bfloat16 b = __float2bfloat16_rn(x);
+  *p = b;
+  return __bfloat162float(b);
+}
 
 }  // namespace cn

@@ -66,6 +66,10 @@ struct cn_model {
   std::vector<int32_t> node_slot;  // global node -> lane (slot) holding it
   std::vector<int64_t> node_elem;  // global node -> element of the interleaved row arrays
   std::vector<int64_t> hh_elem;    // HH instance -> element of the interleaved HH arrays
+  std::vector<int64_t> syn_elem;   // ExpSyn instance -> element of the interleaved synapse arrays
+  std::vector<int64_t> x_off_h, x_step_h;  // external events per lane (offsets, steps sorted per lane)
+  int64_t max_ds = 0;              // longest NetCon delay in steps
+  int64_t raster_from = 0;         // spikes at or before this step are not reported (restored runs)
   std::vector<int32_t> slot_cell;  // lane -> cell (-1 when empty)
   size_t smem_bytes = 0;
   std::vector<int64_t> x_pos0;     // initial external-event cursors
@@ -638,6 +642,7 @@ cn_status finalize(cn_model* m) {
     if (ds < 1) return m->fail(CN_EINVAL, "NetCon delay rounds to less than one step");
     if (ds > (int64_t)1 << 30) return m->fail(CN_EINVAL, "NetCon delay too long");
     nc_ds[j] = (int32_t)ds;
+    m->max_ds = std::max<int64_t>(m->max_ds, ds);
     if (dmin == 0 || ds < dmin) dmin = ds;
   }
   m->D = (int32_t)(dmin == 0 ? cn::kMaxInterval : std::min<int64_t>(dmin, cn::kMaxInterval));
@@ -771,6 +776,8 @@ cn_status finalize(cn_model* m) {
   Rows rs = interleave(m, m->syn_node, true), rh = interleave(m, m->hh_node), rt = interleave(m, m->st_node),
        rr = interleave(m, m->rec_node);
   m->syn_slot = rs.inst_slot; m->syn_q = rs.inst_q;
+  m->syn_elem.resize(m->syn_node.size());
+  for (size_t i = 0; i < m->syn_node.size(); ++i) m->syn_elem[i] = elem_of(rs, i);
   m->hh_slot = rh.inst_slot; m->hh_q = rh.inst_q;
   m->g_syn_base = rs.g_base;
   m->g_hh_base = rh.g_base;
@@ -966,6 +973,8 @@ cn_status finalize(cn_model* m) {
       CN_CHECK(zeros(m, &pd, acc)); dm.cai = pd;
       CN_CHECK(zeros(m, &pd, acc)); dm.ica = pd;
     }
+    CN_CHECK(zeros(m, &pd, acc)); dm.ch_g = pd;
+    CN_CHECK(zeros(m, &pd, acc)); dm.ch_ge = pd;
   }
   CN_CHECK(upload(m, &p32, h_st_slot)); dm.st_slot = p32;
   CN_CHECK(upload(m, &pd, h_st_del)); dm.st_del = pd;
@@ -981,6 +990,8 @@ cn_status finalize(cn_model* m) {
   std::vector<int64_t> x_pos(x_off.begin(), x_off.end() - 1);
   CN_CHECK(upload(m, &p64, x_pos)); dm.x_pos = p64;
   CN_CHECK(upload(m, &p64, h_x_step)); dm.x_step = p64;
+  m->x_off_h = x_off;
+  m->x_step_h = h_x_step;
   CN_CHECK(upload(m, &p32, h_x_syn)); dm.x_syn = p32;
   CN_CHECK(upload(m, &pd, h_x_w)); dm.x_w = pd;
   CN_CHECK(upload(m, &p64, in_off)); dm.in_off = p64;
@@ -1243,6 +1254,7 @@ cn_status reset_state(cn_model* m) {
   CN_TRY_CUDA(m, cudaMemsetAsync(m->dm.status, 0, sizeof(int32_t), m->stream));
   CN_TRY_CUDA(m, cudaMemsetAsync(m->dm.jdev, 0, sizeof(int64_t), m->stream));
   m->step = 0;
+  m->raster_from = 0;
   if (m->dm.trace) {
     const int tb = 128, nb = (m->n_slots + tb - 1) / tb;
     cn::DevModel dm = m->dm;
@@ -1384,6 +1396,112 @@ cn_status advance(cn_model* m, int64_t K, bool traj) {
 }  // namespace
 
 // ====================================================================== ABI
+namespace {
+constexpr uint64_t kCkMagic = 0x314b434e43ull;  // "CNCK1"
+
+uint64_t fnv(uint64_t h, const void* p, size_t n) {
+  const unsigned char* b = static_cast<const unsigned char*>(p);
+  for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
+  return h;
+}
+template <class T>
+uint64_t fnv_vec(uint64_t h, const std::vector<T>& v) {
+  return fnv(h, v.data(), v.size() * sizeof(T));
+}
+
+// Identity of the network a checkpoint belongs to: morphology, mechanism
+// placement, NetCons and the step.
+uint64_t network_fingerprint(const cn_model* m) {
+  uint64_t h = 1469598103934665603ull;
+  h = fnv(h, &m->n_cells, sizeof(m->n_cells));
+  h = fnv_vec(h, m->off);
+  h = fnv_vec(h, m->parent);
+  h = fnv_vec(h, m->pas_node);
+  h = fnv_vec(h, m->hh_node);
+  h = fnv_vec(h, m->syn_node);
+  for (int t = 0; t < cn::kChanTypes; ++t) h = fnv_vec(h, m->ch_node[t]);
+  h = fnv_vec(h, m->nc_src);
+  h = fnv_vec(h, m->nc_syn);
+  h = fnv_vec(h, m->nc_delay);
+  h = fnv_vec(h, m->nc_w);
+  h = fnv(h, &m->opt.dt_ms, sizeof(double));
+  return h;
+}
+
+struct CkHeader {
+  uint64_t magic, fingerprint;
+  int64_t step, window0, n_nodes, n_hh, n_syn, n_ch[cn::kChanTypes];
+  int32_t n_cells, D, has_cai, pad;
+};
+
+double gate_load(const void* base, int64_t e, int bytes) {
+  if (bytes == 8) return static_cast<const double*>(base)[e];
+  if (bytes == 4) return static_cast<const float*>(base)[e];
+  uint32_t fb = (uint32_t) static_cast<const uint16_t*>(base)[e] << 16;
+  float f;
+  std::memcpy(&f, &fb, 4);
+  return f;
+}
+
+// Stores x in the gate format (bfloat16 by round-to-nearest-even of its
+// single-precision value).
+void gate_store(void* base, int64_t e, int bytes, double x) {
+  if (bytes == 8) {
+    static_cast<double*>(base)[e] = x;
+    return;
+  }
+  const float f = (float)x;
+  if (bytes == 4) {
+    static_cast<float*>(base)[e] = f;
+    return;
+  }
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  if ((u & 0x7f800000u) != 0x7f800000u) u += 0x7fffu + ((u >> 16) & 1u);
+  static_cast<uint16_t*>(base)[e] = (uint16_t)(u >> 16);
+}
+
+// Everything a checkpoint moves, as (device buffer, bytes per element,
+// element map from input order) triples, plus the flat host image.
+struct CkPlan {
+  std::vector<void*> dev;
+  std::vector<int64_t> dev_elems;
+  std::vector<int> bytes;
+  std::vector<const std::vector<int64_t>*> map;
+  std::vector<std::vector<int64_t>> owned_maps;
+};
+
+void ck_plan(cn_model* m, CkPlan& P) {
+  P.owned_maps.reserve(2 * cn::kChanTypes + 2);
+  auto add = [&](void* d, int64_t elems, int bytes, const std::vector<int64_t>* mp) {
+    P.dev.push_back(d);
+    P.dev_elems.push_back(elems);
+    P.bytes.push_back(bytes);
+    P.map.push_back(mp);
+  };
+  add(m->dm.v, m->node_elems, 8, &m->node_elem);
+  for (void* g : {m->dm.hh_m, m->dm.hh_h, m->dm.hh_n}) add(g, m->hh_elems, m->gate_bytes, &m->hh_elem);
+  add(m->dm.syn_g, m->syn_elems, 8, &m->syn_elem);
+  for (int t = 0; t < cn::kChanTypes; ++t) {
+    if (m->ch_node[t].empty()) continue;
+    std::vector<int64_t> mp(m->ch_node[t].size());
+    for (size_t i = 0; i < mp.size(); ++i) mp[i] = m->node_elem[m->ch_node[t][i]];
+    P.owned_maps.push_back(std::move(mp));
+    const int g0 = cn::chan_gate0(t), g1 = t + 1 < cn::kChanTypes ? cn::chan_gate0(t + 1) : cn::kChanGates;
+    for (int gi = g0; gi < g1; ++gi) add(m->dm.ch_gate[gi], m->node_elems, m->gate_bytes, &P.owned_maps.back());
+  }
+  if (m->dm.cai) add(m->dm.cai, m->node_elems, 8, &m->node_elem);
+}
+
+size_t ck_bytes(const cn_model* m, const CkPlan& P, int64_t nwin) {
+  size_t b = sizeof(CkHeader);
+  for (size_t k = 0; k < P.dev.size(); ++k) b += P.map[k]->size() * 8;
+  b += (size_t)m->n_cells;                          // threshold flags
+  b += (size_t)nwin * m->n_cells * sizeof(uint64_t);  // spike history window
+  return b;
+}
+}  // namespace
+
 extern "C" {
 
 int32_t cn_mech_nparams(int32_t type) {
@@ -1687,7 +1805,7 @@ cn_status cn_get_spikes(cn_model* m, int32_t* gid, int64_t* step, size_t cap, si
       while (mk) {
         int b = __builtin_ctzll(mk);
         mk &= mk - 1;
-        sp.emplace_back(J * m->D + b + 1, c);
+        if (J * m->D + b + 1 > m->raster_from) sp.emplace_back(J * m->D + b + 1, c);
       }
     }
   std::sort(sp.begin(), sp.end());
@@ -1913,6 +2031,129 @@ cn_status cn_get_cell_param(cn_model* m, int32_t param, double* values) {
   std::vector<uint8_t> seen(m->n_cells, 0);
   for (size_t i = 0; i < idx.size(); ++i)
     if (!seen[cell[i]]++) values[cell[i]] = h[i];
+  return CN_OK;
+}
+
+// ---- checkpoint / restart (Section 3.4).  The file holds the state in the
+// model's input order (nodes, mechanism instances, cells), so it does not
+// depend on the layout: a checkpoint taken under one mapping restores under
+// another.  Pending NetCon deliveries are not stored as events: the spike
+// history of the intervals that can still deliver is stored instead (one bit
+// per source and step), and the pull kernel re-derives every delivery from
+// it, exactly as in an uninterrupted run.
+
+cn_status cn_checkpoint_save(cn_model* m, void* buf, size_t cap, size_t* n) {
+  if (!m || !n) return CN_EINVAL;
+  CN_TRY_CUDA(m, cudaSetDevice(m->opt.device));
+  CN_CHECK(prepare(m));
+  if (m->step % m->D != 0) return m->fail(CN_ESTATE, "checkpoints are taken at interval boundaries");
+  CN_CHECK(ensure_capacity(m, m->step));
+  CkPlan P;
+  ck_plan(m, P);
+  const int64_t J = m->step / m->D;
+  const int64_t w0 = std::max<int64_t>(0, J - (m->max_ds + m->D - 1) / m->D - 1);
+  *n = ck_bytes(m, P, J - w0);
+  if (!buf) return CN_OK;
+  if (cap < *n) return m->fail(CN_ERANGE, "checkpoint buffer too small");
+  CN_CHECK(cn_sync(m));
+  char* out = static_cast<char*>(buf);
+  CkHeader hd{};
+  hd.magic = kCkMagic;
+  hd.fingerprint = network_fingerprint(m);
+  hd.step = m->step;
+  hd.window0 = w0;
+  hd.n_nodes = m->n_nodes;
+  hd.n_hh = (int64_t)m->hh_node.size();
+  hd.n_syn = (int64_t)m->syn_node.size();
+  for (int t = 0; t < cn::kChanTypes; ++t) hd.n_ch[t] = (int64_t)m->ch_node[t].size();
+  hd.n_cells = m->n_cells;
+  hd.D = m->D;
+  hd.has_cai = m->dm.cai != nullptr;
+  std::memcpy(out, &hd, sizeof(hd));
+  out += sizeof(hd);
+  std::vector<char> h;
+  for (size_t k = 0; k < P.dev.size(); ++k) {
+    h.resize((size_t)std::max<int64_t>(P.dev_elems[k], 1) * P.bytes[k]);
+    CN_TRY_CUDA(m, cudaMemcpy(h.data(), P.dev[k], (size_t)P.dev_elems[k] * P.bytes[k], cudaMemcpyDeviceToHost));
+    for (int64_t e : *P.map[k]) {
+      const double x = gate_load(h.data(), e, P.bytes[k]);
+      std::memcpy(out, &x, 8);
+      out += 8;
+    }
+  }
+  std::vector<uint8_t> above(m->n_slots);
+  CN_TRY_CUDA(m, cudaMemcpy(above.data(), m->dm.s_above, above.size(), cudaMemcpyDeviceToHost));
+  for (int c = 0; c < m->n_cells; ++c) *out++ = (char)above[m->node_slot[m->off[c] + m->spike_node[c]]];
+  const size_t hb = (size_t)(J - w0) * m->n_cells * sizeof(uint64_t);
+  if (hb) CN_TRY_CUDA(m, cudaMemcpy(out, m->dm.hist + (size_t)w0 * m->n_cells, hb, cudaMemcpyDeviceToHost));
+  return CN_OK;
+}
+
+cn_status cn_checkpoint_load(cn_model* m, const void* buf, size_t n) {
+  if (!m || !buf) return CN_EINVAL;
+  CN_TRY_CUDA(m, cudaSetDevice(m->opt.device));
+  CN_CHECK(prepare(m));
+  CkHeader hd;
+  if (n < sizeof(hd)) return m->fail(CN_EINVAL, "not a checkpoint");
+  std::memcpy(&hd, buf, sizeof(hd));
+  if (hd.magic != kCkMagic) return m->fail(CN_EINVAL, "not a checkpoint");
+  if (hd.fingerprint != network_fingerprint(m) || hd.n_cells != m->n_cells || hd.D != m->D ||
+      hd.n_nodes != m->n_nodes || hd.has_cai != (m->dm.cai != nullptr))
+    return m->fail(CN_EINVAL, "the checkpoint belongs to another network");
+  CkPlan P;
+  ck_plan(m, P);
+  const int64_t J = hd.step / m->D;
+  if (hd.step % m->D != 0 || hd.window0 < 0 || hd.window0 > J || n != ck_bytes(m, P, J - hd.window0))
+    return m->fail(CN_EINVAL, "malformed checkpoint");
+  CN_CHECK(ensure_capacity(m, hd.step));
+  CN_CHECK(cn_sync(m));
+  const char* in = static_cast<const char*>(buf) + sizeof(hd);
+  std::vector<char> h;
+  for (size_t k = 0; k < P.dev.size(); ++k) {
+    const size_t nb = (size_t)P.dev_elems[k] * P.bytes[k];
+    h.resize(std::max<size_t>(nb, 1));
+    CN_TRY_CUDA(m, cudaMemcpy(h.data(), P.dev[k], nb, cudaMemcpyDeviceToHost));
+    for (int64_t e : *P.map[k]) {
+      double x;
+      std::memcpy(&x, in, 8);
+      in += 8;
+      gate_store(h.data(), e, P.bytes[k], x);
+    }
+    CN_TRY_CUDA(m, cudaMemcpy(P.dev[k], h.data(), nb, cudaMemcpyHostToDevice));
+  }
+  std::vector<uint8_t> above(m->n_slots);
+  CN_TRY_CUDA(m, cudaMemcpy(above.data(), m->dm.s_above, above.size(), cudaMemcpyDeviceToHost));
+  for (int c = 0; c < m->n_cells; ++c) above[m->node_slot[m->off[c] + m->spike_node[c]]] = (uint8_t)*in++;
+  CN_TRY_CUDA(m, cudaMemcpy(m->dm.s_above, above.data(), above.size(), cudaMemcpyHostToDevice));
+  CN_TRY_CUDA(m, cudaMemset(m->dm.hist, 0, (size_t)m->hist_cap * m->n_cells * sizeof(uint64_t)));
+  const size_t hb = (size_t)(J - hd.window0) * m->n_cells * sizeof(uint64_t);
+  if (hb) CN_TRY_CUDA(m, cudaMemcpy(m->dm.hist + (size_t)hd.window0 * m->n_cells, in, hb, cudaMemcpyHostToDevice));
+  // this model's own external events apply from the checkpoint step on
+  std::vector<int64_t> xpos(m->n_slots);
+  for (int s = 0; s < m->n_slots; ++s)
+    xpos[s] = std::lower_bound(m->x_step_h.begin() + m->x_off_h[s], m->x_step_h.begin() + m->x_off_h[s + 1],
+                               hd.step) - m->x_step_h.begin();
+  CN_TRY_CUDA(m, cudaMemcpy(m->dm.x_pos, xpos.data(), xpos.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+  CN_TRY_CUDA(m, cudaMemset(m->dm.status, 0, sizeof(int32_t)));
+  CN_TRY_CUDA(m, cudaMemcpy(m->dm.jdev, &J, sizeof(J), cudaMemcpyHostToDevice));
+  if (m->dense) {  // channel currents (and ica) follow from the restored gates and voltages
+    const int tb = 128, nb = (m->n_slots + tb - 1) / tb;
+    cn::DevModel dm = m->dm;
+    switch (m->opt.precision) {
+      case CN_PREC_FP64: CN_CHECK(launch_checked(m, [&] { cn::k_dense_currents<0><<<nb, tb, 0, m->stream>>>(dm); })); break;
+      case CN_PREC_GATE_FP32: CN_CHECK(launch_checked(m, [&] { cn::k_dense_currents<1><<<nb, tb, 0, m->stream>>>(dm); })); break;
+      default: CN_CHECK(launch_checked(m, [&] { cn::k_dense_currents<2><<<nb, tb, 0, m->stream>>>(dm); })); break;
+    }
+  }
+  m->step = hd.step;
+  m->raster_from = hd.step;
+  if (m->dm.trace) {
+    const int tb = 128, nb = (m->n_slots + tb - 1) / tb;
+    cn::DevModel dm = m->dm;
+    const int64_t k = m->step;
+    CN_CHECK(launch_checked(m, [&] { cn::k_record0<<<nb, tb, 0, m->stream>>>(dm, k); }));
+  }
+  CN_TRY_CUDA(m, cudaStreamSynchronize(m->stream));
   return CN_OK;
 }
 

@@ -263,35 +263,37 @@ __device__ __forceinline__ void gate_ab(const double* kin, T v, T& al, T& be) {
   be = B * dexp_(-(v - vh2) / k2);
 }
 
+// Channel conductance G and sum of g E of row e at voltage v from the stored
+// gates (the nrn_cur of the channel types), and ica for the calcium update.
 template <int PREC>
 __device__ __forceinline__ void dense_cur(const DevModel& M, int mask, int64_t e, double v, const double* kin,
-                                          double& G, double& GE) {
+                                          int64_t ks, double& G, double& GE) {
   using S = typename GateT<PREC>::S;
   auto x = [&](int gi) { return (double)g_load(static_cast<const S*>(M.ch_gate[gi]) + e); };
   double g = 0.0, ge = 0.0;
   if (mask & 1) {  // NA3H: m^3 h
     const double m = x(0), c = M.ch_gbar[0][e] * (m * m * m * x(1));
     g += c;
-    ge = fma(c, kin[chan_kin0(0) * kLanes], ge);
+    ge = fma(c, kin[chan_kin0(0) * ks], ge);
   }
   if (mask & 2) {  // KDR4: n^4
     const double n = x(2), c = M.ch_gbar[1][e] * ((n * n) * (n * n));
     g += c;
-    ge = fma(c, kin[chan_kin0(1) * kLanes], ge);
+    ge = fma(c, kin[chan_kin0(1) * ks], ge);
   }
   if (mask & 4) {  // KA: a^3 b
     const double a = x(3), c = M.ch_gbar[2][e] * (a * a * a * x(4));
     g += c;
-    ge = fma(c, kin[chan_kin0(2) * kLanes], ge);
+    ge = fma(c, kin[chan_kin0(2) * ks], ge);
   }
   if (mask & 8) {  // IH: q
     const double c = M.ch_gbar[3][e] * x(5);
     g += c;
-    ge = fma(c, kin[chan_kin0(3) * kLanes], ge);
+    ge = fma(c, kin[chan_kin0(3) * ks], ge);
   }
   if (mask & 16) {  // CAHVA: m^2 h; its current drives [Ca]i
     const double m = x(6), c = M.ch_gbar[4][e] * (m * m * x(7));
-    const double eca = kin[chan_kin0(4) * kLanes];
+    const double eca = kin[chan_kin0(4) * ks];
     g += c;
     ge = fma(c, eca, ge);
     M.ica[e] = c * M.cdt[e] * (v - eca);
@@ -299,49 +301,101 @@ __device__ __forceinline__ void dense_cur(const DevModel& M, int mask, int64_t e
   if (mask & 32) {  // KCA: c
     const double c = M.ch_gbar[5][e] * x(8);
     g += c;
-    ge = fma(c, kin[chan_kin0(5) * kLanes], ge);
+    ge = fma(c, kin[chan_kin0(5) * ks], ge);
   }
   G = g;
   GE = ge;
 }
 
+// nrn_state of the channel types at v_{k+1} (cnexp, in type order; the
+// calcium update uses the ica of step k), followed at once by their nrn_cur
+// for step k+1 from the new gates and v_{k+1}: G and G E go to ch_g/ch_ge,
+// which the next elimination streams with the row, and ica is kept for the
+// next calcium update.  The values are those a separate nrn_cur at the start
+// of step k+1 would compute.
 template <int PREC>
-__device__ __forceinline__ void dense_state(const DevModel& M, int mask, int64_t e, double vnew, const double* kin) {
+__device__ __forceinline__ void dense_step(const DevModel& M, int mask, int64_t e, double vnew, const double* kin) {
   using S = typename GateT<PREC>::S;
   using T = typename GateT<PREC>::M;
   const T v = (T)vnew, tdt = (T)M.dt;
-  auto upd = [&](int gi, const double* k6) {
+  auto upd = [&](int gi, const double* k6) -> double {
     T al, be;
     gate_ab<T>(k6, v, al, be);
     S* p = static_cast<S*>(M.ch_gate[gi]) + e;
-    g_store(p, cnexp_step<T>(g_load(p), al, be, tdt));
+    return (double)g_store_ret(p, cnexp_step<T>(g_load(p), al, be, tdt));
   };
-  if (mask & 1) {
-    upd(0, kin + (chan_kin0(0) + 1) * kLanes);
-    upd(1, kin + (chan_kin0(0) + 7) * kLanes);
+  double g = 0.0, ge = 0.0;
+  if (mask & 1) {  // NA3H: m^3 h
+    const double m = upd(0, kin + (chan_kin0(0) + 1) * kLanes);
+    const double h = upd(1, kin + (chan_kin0(0) + 7) * kLanes);
+    const double c = M.ch_gbar[0][e] * (m * m * m * h);
+    g += c;
+    ge = fma(c, kin[chan_kin0(0) * kLanes], ge);
   }
-  if (mask & 2) upd(2, kin + (chan_kin0(1) + 1) * kLanes);
-  if (mask & 4) {
-    upd(3, kin + (chan_kin0(2) + 1) * kLanes);
-    upd(4, kin + (chan_kin0(2) + 7) * kLanes);
+  if (mask & 2) {  // KDR4: n^4
+    const double n = upd(2, kin + (chan_kin0(1) + 1) * kLanes);
+    const double c = M.ch_gbar[1][e] * ((n * n) * (n * n));
+    g += c;
+    ge = fma(c, kin[chan_kin0(1) * kLanes], ge);
   }
-  if (mask & 8) upd(5, kin + (chan_kin0(3) + 1) * kLanes);
-  if (mask & 16) {
-    upd(6, kin + (chan_kin0(4) + 1) * kLanes);
-    upd(7, kin + (chan_kin0(4) + 7) * kLanes);
+  if (mask & 4) {  // KA: a^3 b
+    const double a = upd(3, kin + (chan_kin0(2) + 1) * kLanes);
+    const double b = upd(4, kin + (chan_kin0(2) + 7) * kLanes);
+    const double c = M.ch_gbar[2][e] * (a * a * a * b);
+    g += c;
+    ge = fma(c, kin[chan_kin0(2) * kLanes], ge);
+  }
+  if (mask & 8) {  // IH: q
+    const double q = upd(5, kin + (chan_kin0(3) + 1) * kLanes);
+    const double c = M.ch_gbar[3][e] * q;
+    g += c;
+    ge = fma(c, kin[chan_kin0(3) * kLanes], ge);
+  }
+  if (mask & 16) {  // CAHVA: m^2 h, [Ca]i from the current of step k
+    const double m = upd(6, kin + (chan_kin0(4) + 1) * kLanes);
+    const double h = upd(7, kin + (chan_kin0(4) + 7) * kLanes);
     const double* kc = kin + chan_kin0(4) * kLanes;
     const T depth = (T)kc[13 * kLanes], taur = (T)kc[14 * kLanes], cainf = (T)kc[15 * kLanes];
     T drive = T(-1e4) * (T)M.ica[e] / (T(2.0 * 96485.3321) * depth);
     if (drive < T(0)) drive = T(0);
     const T cai = (T)M.cai[e];
     M.cai[e] = (double)(cai + (T(1) - dexp_(-tdt / taur)) * (cainf + drive * taur - cai));
+    const double c = M.ch_gbar[4][e] * (m * m * h);
+    const double eca = kc[0];
+    g += c;
+    ge = fma(c, eca, ge);
+    M.ica[e] = c * M.cdt[e] * (vnew - eca);
   }
-  if (mask & 32) {
+  if (mask & 32) {  // KCA: c, activated by the new [Ca]i
     const double* kk = kin + chan_kin0(5) * kLanes;
     const T cai = (T)M.cai[e];
     const T al = (T)kk[1 * kLanes] * cai / (cai + (T)kk[2 * kLanes]);
     S* p = static_cast<S*>(M.ch_gate[8]) + e;
-    g_store(p, cnexp_step<T>(g_load(p), al, (T)kk[3 * kLanes], tdt));
+    const double x = (double)g_store_ret(p, cnexp_step<T>(g_load(p), al, (T)kk[3 * kLanes], tdt));
+    const double c = M.ch_gbar[5][e] * x;
+    g += c;
+    ge = fma(c, kk[0], ge);
+  }
+  M.ch_g[e] = g;
+  M.ch_ge[e] = ge;
+}
+
+// Channel currents of every row from the stored gates and v (after setup or
+// a restore).
+template <int PREC>
+__global__ void k_dense_currents(DevModel M) {
+  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot >= M.n_slots) return;
+  const int g = slot / kLanes, lane = slot % kLanes;
+  const int mask = M.g_chmask[g];
+  const int64_t nb = M.g_node_base[g] + lane;
+  const double* kin = M.ch_kin + slot;  // [param][n_slots]
+  for (int j = 0; j < M.g_rows[g]; ++j) {
+    const int64_t e = nb + (int64_t)j * kLanes;
+    double G = 0.0, GE = 0.0;
+    if (M.flags[e] & kRealBit) dense_cur<PREC>(M, mask, e, M.v[e], kin, M.n_slots, G, GE);
+    M.ch_g[e] = G;
+    M.ch_ge[e] = GE;
   }
 }
 
@@ -385,7 +439,10 @@ __global__ void k_setup_dense(DevModel M, double v_init, bool scale_gbar) {
       const T be = (T)kin[(chan_kin0(5) + 3) * ks];
       g_store(static_cast<S*>(M.ch_gate[8]) + e, al / (al + be));
     }
-    if (M.ica) M.ica[e] = 0.0;
+    double G, GE;  // channel currents of step 0 (ica included)
+    dense_cur<PREC>(M, mask, e, v_init, kin, ks, G, GE);
+    M.ch_g[e] = G;
+    M.ch_ge[e] = GE;
   }
 }
 
@@ -435,11 +492,14 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 4)
   double* const e_d0 = e_ge + kElimRows * kLanes;
   double* const e_a = e_d0 + kElimRows * kLanes;
   double* const e_b = e_a + kElimRows * kLanes;
-  int32_t* const e_fl = reinterpret_cast<int32_t*>(reinterpret_cast<double*>(smem) + 5 * kElimRows * kLanes) + lane;
+  double* const e_cg = e_b + kElimRows * kLanes;    // channel G and G E (DENSE)
+  double* const e_cge = e_cg + kElimRows * kLanes;
+  int32_t* const e_fl =
+      reinterpret_cast<int32_t*>(reinterpret_cast<double*>(smem) + (DENSE ? 7 : 5) * kElimRows * kLanes) + lane;
   double* const b_x = reinterpret_cast<double*>(smem) + lane;
   double* const b_bp = b_x + kBackRows * kLanes;
   int32_t* const b_fl = reinterpret_cast<int32_t*>(reinterpret_cast<double*>(smem) + 2 * kBackRows * kLanes) + lane;
-  double* const wsm = reinterpret_cast<double*>(smem + ring_bytes());
+  double* const wsm = reinterpret_cast<double*>(smem + ring_bytes(DENSE));
   double* const st_a = wsm + lane;  // far stack [DS][32] each
   double* const st_x = st_a + DS * kLanes;
   double* const st_y = st_x + DS * kLanes;
@@ -494,6 +554,10 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 4)
       cp_async8(e_d0 + u * kLanes, gd0 + o);
       cp_async8(e_a + u * kLanes, ga + o);
       cp_async8(e_b + u * kLanes, gb + o);
+      if (DENSE) {
+        cp_async8(e_cg + u * kLanes, M.ch_g + nb + o);
+        cp_async8(e_cge + u * kLanes, M.ch_ge + nb + o);
+      }
       cp_async4(e_fl + u * kLanes, gfl + o);
     }
     cp_async_commit();
@@ -618,11 +682,9 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 4)
             next_syn();
           }
           double base = e_v[ro] + acc_ge;
-          if (DENSE) {
-            double Gc, GEc;
-            dense_cur<PREC>(M, chmask, nb + (int64_t)j * kLanes, e_v[ro], kin, Gc, GEc);
-            base += GEc;
-            dd0 += Gc;
+          if (DENSE) {  // channel currents of this step (computed at the end of the previous one)
+            base += e_cge[ro];
+            dd0 += e_cg[ro];
           }
           double rhs = fma(fa, fx, base);
           double d = fma(fa, fb, dd0);
@@ -698,7 +760,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 4)
           const double vj = fma(-b_bp[ro], vp, b_x[ro]);
           gv[(int64_t)j * kLanes] = vj;
           if (f & kJuncBit) mail[4 * ((f >> kJmailShift) & kMailMask) + 3] = vj;
-          if (DENSE && (f & kRealBit)) dense_state<PREC>(M, chmask, nb + (int64_t)j * kLanes, vj, kin);
+          if (DENSE && (f & kRealBit)) dense_step<PREC>(M, chmask, nb + (int64_t)j * kLanes, vj, kin);
           if (TRAJ) M.traj_v[(k + 1 - M.traj_k0) * M.node_elems + nb + (int64_t)j * kLanes] = vj;
           const int np = (f >> kNFarShift) & kNFarMask;
           if (np > 0) st_x[tp * kLanes] = vj;

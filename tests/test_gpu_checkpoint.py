@@ -1,0 +1,113 @@
+"""Checkpoint / restart of the network (Section 3.4) on the GPU.
+
+A run that is checkpointed at an interval boundary and restored into a new
+model must continue exactly as the uninterrupted run: same spikes after the
+checkpoint step, bit-identical voltages and traces, whether or not NetCon
+deliveries are pending at the checkpoint (they are re-derived from the
+stored spike history).  A restored model continues with its own external
+events, so the network can be resumed with new inputs.  The checkpoint is
+in input order, so it also restores under another layout."""
+import numpy as np
+import pytest
+
+from scenarios import network
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cn():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1901_10975_gb300 import build
+    build.build()
+    from paper_1901_10975_gb300 import cn as _cn
+    return _cn
+
+
+def driven(**kw):
+    return network(n_cells=160, tstop=40.0, w_median=0.03, bg_w=0.03, bg_rate_hz=30.0, **kw)
+
+
+def outputs(md, sc, k0):
+    md.cn_sync()
+    g, k = md.cn_get_spikes()
+    sel = k > k0
+    tr = np.stack([md.cn_get_trace(r)[k0:] for r in range(len(sc.rec_node))])
+    return g[sel], k[sel], tr, md.cn_get_v()
+
+
+def test_restart_continues_bit_exact(cn):
+    sc = driven()
+    a = cn.from_scenario(sc)
+    a.cn_run(20.0)
+    ck = a.cn_checkpoint_save()
+    a.cn_run(40.0)
+    ga, ka, tra, va = outputs(a, sc, 800)
+    assert len(ga) > 10
+    b = cn.from_scenario(sc)
+    b.cn_checkpoint_load(ck)
+    assert b.step == 800
+    b.cn_run(40.0)
+    gb, kb, trb, vb = outputs(b, sc, 800)
+    assert np.array_equal(ga, gb) and np.array_equal(ka, kb)
+    assert np.array_equal(tra, trb) and np.array_equal(va, vb)
+    # the restored raster holds no spike at or before the checkpoint step
+    assert np.all(b.cn_get_spikes()[1] > 800)
+
+
+def test_restart_with_new_inputs(cn):
+    """The saving model only knew the inputs before 20 ms; the restoring model
+    has the full input train and continues as a model that had it all along."""
+    full = driven()
+    early = driven()
+    keep = early.ev_t < 20.0
+    early.ev_syn, early.ev_t, early.ev_w = early.ev_syn[keep], early.ev_t[keep], early.ev_w[keep]
+    ref = cn.from_scenario(full)
+    ref.cn_run(40.0)
+    g0, k0, tr0, v0 = outputs(ref, full, 800)
+    sav = cn.from_scenario(early)
+    sav.cn_run(20.0)
+    ck = sav.cn_checkpoint_save()
+    res = cn.from_scenario(full)
+    res.cn_checkpoint_load(ck)
+    res.cn_run(40.0)
+    g1, k1, tr1, v1 = outputs(res, full, 800)
+    assert len(g0) > 10
+    assert np.array_equal(g0, g1) and np.array_equal(k0, k1)
+    assert np.array_equal(tr0, tr1) and np.array_equal(v0, v1)
+
+
+def test_restart_under_another_layout(cn):
+    """Saved with one cell per lane, restored with split cells in tall warps:
+    the elimination order differs, so voltages agree to rounding."""
+    sc = driven()
+    a = cn.from_scenario(sc, mapping=cn.CN_MAP_THREAD)
+    a.cn_run(16.0)
+    ck = a.cn_checkpoint_save()
+    a.cn_run(32.0)
+    ga, ka, tra, va = outputs(a, sc, 640)
+    b = cn.from_scenario(sc, mapping=48 | cn.CN_MAP_TALL)
+    b.cn_checkpoint_load(ck)
+    b.cn_run(32.0)
+    gb, kb, trb, vb = outputs(b, sc, 640)
+    assert np.array_equal(ga, gb) and np.array_equal(ka, kb)
+    assert np.max(np.abs(tra - trb)) <= 1e-9 and np.max(np.abs(va - vb)) <= 1e-9
+
+
+def test_checkpoint_errors(cn):
+    sc = driven()
+    a = cn.from_scenario(sc)
+    a.cn_run(10.5)
+    with pytest.raises(cn.CNError) as e:
+        a.cn_checkpoint_save()
+    assert e.value.status == cn.CN_ESTATE
+    a.cn_run(11.0)
+    ck = a.cn_checkpoint_save()
+    other = cn.from_scenario(network(n_cells=160, tstop=40.0, seed=7))
+    with pytest.raises(cn.CNError) as e:
+        other.cn_checkpoint_load(ck)
+    assert e.value.status == cn.CN_EINVAL
+    with pytest.raises(cn.CNError):
+        cn.from_scenario(sc).cn_checkpoint_load(ck[:-8])
