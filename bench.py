@@ -144,6 +144,10 @@ def max_over_ranks(x, world):
 
 
 def workload(args, intervals):
+    if args.workload == "morph_types":
+        from scenarios import morph_types
+        return morph_types(n_cells=args.cells or 131072, cells_per_type=args.cells_per_type,
+                           tstop=float(intervals) + 1.0)
     if args.workload == "batched":
         from scenarios import batched
         return batched(n_cells=args.cells or 50000, tstop=float(intervals) + 1.0, seed=1903)
@@ -153,7 +157,10 @@ def workload(args, intervals):
 
 def config_dict(args, sc, layout=None):
     cells = int(len(sc.cell_offset) - 1)
-    if args.workload == "batched":
+    if args.workload == "morph_types":
+        name = (f"morphological types {cells} cells x 83 compartments, {args.cells_per_type} identical cells per "
+                f"type, rings of 16, HH soma, pas dendrites, dt 0.025 ms")
+    elif args.workload == "batched":
         name = (f"batched {cells} cells x lognormal(400, 0.8) compartments in [50, 5000], random subset of "
                 f"6 channel types per cell on every node, network as the plain workload, dt 0.025 ms")
     else:
@@ -323,7 +330,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cells", type=int, default=0, help="0: the workload's full size")
-    ap.add_argument("--workload", choices=["network", "batched"], default="network")
+    ap.add_argument("--workload", choices=["network", "batched", "morph_types"], default="network")
+    ap.add_argument("--cells-per-type", type=int, default=32, help="morph_types: identical cells per type")
     ap.add_argument("--precision", choices=["fp64", "gate_fp32", "gate_bf16"], default="fp64")
     ap.add_argument("--cpu-intervals", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")

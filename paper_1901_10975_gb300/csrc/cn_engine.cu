@@ -290,8 +290,21 @@ std::vector<int> part_bases(const std::vector<CellPart>& parts, const std::vecto
 
 CellPlan plan_cell(const int32_t* parent, int n, int target) {
   CellPlan P;
-  std::vector<std::vector<int32_t>> ch(n);
-  for (int i = 1; i < n; ++i) ch[parent[i]].push_back(i);
+  // children in CSR form: kids of i are cidx[cofs[i] .. cofs[i+1])
+  std::vector<int32_t> cofs(n + 1, 0), cidx(n > 0 ? n - 1 : 0);
+  for (int i = 1; i < n; ++i) cofs[parent[i] + 1]++;
+  for (int i = 0; i < n; ++i) cofs[i + 1] += cofs[i];
+  {
+    std::vector<int32_t> fill(cofs.begin(), cofs.end() - 1);
+    for (int i = 1; i < n; ++i) cidx[fill[parent[i]]++] = i;
+  }
+  struct Kids {
+    const int32_t* b;
+    const int32_t* e;
+    const int32_t* begin() const { return b; }
+    const int32_t* end() const { return e; }
+  };
+  auto ch = [&](int i) { return Kids{cidx.data() + cofs[i], cidx.data() + cofs[i + 1]}; };
   P.part_of.assign(n, 0);
   P.parts.push_back(CellPart{});
   std::vector<int32_t> child_part_at(n, -1);  // junction node -> child part
@@ -301,7 +314,7 @@ CellPlan plan_cell(const int32_t* parent, int n, int target) {
     // in-part subtree sizes and depths
     for (int i = n - 1; i >= 0; --i) {
       sub[i] = 1;
-      for (int c : ch[i])
+      for (int c : ch(i))
         if (P.part_of[c] == P.part_of[i]) sub[i] += sub[c];
     }
     std::vector<int> psize(P.parts.size(), 0);
@@ -334,13 +347,13 @@ CellPlan plan_cell(const int32_t* parent, int n, int target) {
     P.parts.push_back(np_);
     child_part_at[parent[best_c]] = nq;
     // move the in-part subtree of best_c (and re-parent child parts hanging inside it)
-    std::vector<int32_t> st{best_c};
-    while (!st.empty()) {
-      int u = st.back();
-      st.pop_back();
+    std::vector<int32_t> mv{best_c};
+    while (!mv.empty()) {
+      int u = mv.back();
+      mv.pop_back();
       P.part_of[u] = nq;
-      for (int c : ch[u])
-        if (P.part_of[c] == worst) st.push_back(c);
+      for (int c : ch(u))
+        if (P.part_of[c] == worst) mv.push_back(c);
     }
     for (size_t q = 1; q < P.parts.size(); ++q)
       if (P.part_of[P.parts[q].jnode] == nq && (int)q != nq) P.parts[q].parent_part = nq;
@@ -348,28 +361,29 @@ CellPlan plan_cell(const int32_t* parent, int n, int target) {
   // row order inside every part
   for (int i = n - 1; i >= 0; --i) {
     sub[i] = 1;
-    for (int c : ch[i])
+    for (int c : ch(i))
       if (P.part_of[c] == P.part_of[i]) sub[i] += sub[c];
   }
   std::vector<uint8_t> leads(n, 0);  // in-part subtree contains a junction node
   for (int i = n - 1; i >= 0; --i) {
     if (child_part_at[i] >= 0) leads[i] = 1;
-    for (int c : ch[i])
+    for (int c : ch(i))
       if (P.part_of[c] == P.part_of[i] && leads[c]) leads[i] = 1;
   }
   P.row_of.assign(n, -1);
   P.far.assign(n, 0);
   P.nfar.assign(n, 0);
+  std::vector<int32_t> cc, st;
   for (size_t q = 0; q < P.parts.size(); ++q) {
     CellPart& pt = P.parts[q];
-    std::vector<int32_t> st{pt.root};
+    st.assign(1, pt.root);
     while (!st.empty()) {
       int u = st.back();
       st.pop_back();
       P.row_of[u] = (int)pt.nodes.size();
       pt.nodes.push_back(u);
-      std::vector<int32_t> cc;
-      for (int c : ch[u])
+      cc.clear();
+      for (int c : ch(u))
         if (P.part_of[c] == (int)q) cc.push_back(c);
       std::stable_sort(cc.begin(), cc.end(), [&](int x, int y) {
         if (leads[x] != leads[y]) return leads[x] > leads[y];
@@ -466,7 +480,7 @@ struct Layout {
   std::vector<int32_t> node_flags;            // global node -> topology bits
 };
 
-constexpr size_t kPackWindow = 4;
+constexpr int kPackLookahead = 512;  // remaining cells tried per warp  // refusals after which a warp takes no more cells
 
 bool build_layout(int32_t n_cells, const int32_t* off, const int32_t* parent, const int32_t* cell_mask,
                   const int32_t* spike_node, int target, bool stack, bool tall, Layout& L, std::string& err) {
@@ -503,6 +517,7 @@ bool build_layout(int32_t n_cells, const int32_t* off, const int32_t* parent, co
     int32_t mask = 0;
     int min_lev = 0;
     int H = 0;               // rows of this warp: the span of the cell that opened it
+    int max_free = 1 << 30;  // longest free run of rows in any lane
   };
   std::vector<Warp> warps;
   // per cell: part order (parents first), and the placement found
@@ -549,7 +564,11 @@ bool build_layout(int32_t n_cells, const int32_t* off, const int32_t* parent, co
     std::copy(lev, lev + cn::kLanes, w.lev);
     std::copy(own, own + cn::kLanes, w.owner);
     w.root[plane[qsp]] = true;
-    w.min_lev = *std::min_element(w.lev, w.lev + cn::kLanes);
+    w.max_free = 0;
+    for (int l = 0; l < cn::kLanes; ++l) w.max_free = std::max(w.max_free, w.H - w.lev[l]);
+    w.min_lev = cn::kMailMask + (1 << 30);
+    for (int l = 0; l < cn::kLanes; ++l)
+      if (!w.root[l]) w.min_lev = std::min(w.min_lev, w.lev[l]);  // where a spike-source part can go
     warp_mail0[c] = w.n_mail;
     w.n_mail += np - 1;
     cell_warp[c] = wi;
@@ -559,8 +578,7 @@ bool build_layout(int32_t n_cells, const int32_t* off, const int32_t* parent, co
     }
     return true;
   };
-  size_t group_first = 0;  // first warp of the current channel set
-  for (int c : order) {
+  auto set_order = [&](int c) {  // parts of cell c in part-tree order (parents first)
     const CellPlan& P = L.plans[c];
     const int np = (int)P.parts.size();
     kids.assign(np, {});
@@ -569,30 +587,83 @@ bool build_layout(int32_t n_cells, const int32_t* off, const int32_t* parent, co
     porder.push_back(0);
     for (size_t h = 0; h < porder.size(); ++h)
       for (int k : kids[porder[h]]) porder.push_back(k);
-    if (!warps.empty() && warps.back().mask != mask(c)) group_first = warps.size();
-    bool placed = false;
-    const int size0 = (int)P.parts[0].nodes.size();
-    // first fit among the most recent warps of this channel set, so that a
-    // warp holds cells of similar span
-    const size_t window = tall ? warps.size() : kPackWindow;
-    const size_t from = std::max(group_first, warps.size() > window ? warps.size() - window : 0);
-    for (size_t wi = from; wi < warps.size() && !placed; ++wi) {
-      if (warps[wi].min_lev + size0 > warps[wi].H) continue;
-      placed = try_place(c, warps[wi], (int)wi);
+  };
+  // Fill one warp at a time: it opens with the largest remaining cell and
+  // takes, among the next kPackLookahead remaining cells of the same channel
+  // set, every cell that still fits; the rest wait for later warps.
+  std::vector<int32_t> next_of(n_cells + 1);  // linked list of unplaced cells in order
+  for (int k = 0; k <= n_cells; ++k) next_of[k] = k + 1;
+  int head = 0;  // position in order of the first unplaced cell
+  auto advance = [&](int k) { return next_of[k]; };
+  std::vector<uint8_t> placed(n_cells, 0);
+  int tail = n_cells;  // cells at positions >= tail are placed (or of another channel set)
+  while (head < n_cells) {
+    const int c0 = order[head];
+    const CellPlan& P0 = L.plans[c0];
+    Warp w;
+    std::fill(w.lev, w.lev + cn::kLanes, 0);
+    std::fill(w.owner, w.owner + cn::kLanes, -1);
+    std::fill(w.root, w.root + cn::kLanes, false);
+    w.mask = mask(c0);
+    w.H = tall ? H : P0.span;
+    warps.push_back(w);
+    const int wi = (int)warps.size() - 1;
+    set_order(c0);
+    if (!try_place(c0, warps[wi], wi)) {
+      err = "internal: a cell does not fit an empty warp";
+      return false;
     }
-    if (!placed) {
-      Warp w;
-      std::fill(w.lev, w.lev + cn::kLanes, 0);
-      std::fill(w.owner, w.owner + cn::kLanes, -1);
-      std::fill(w.root, w.root + cn::kLanes, false);
-      w.mask = mask(c);
-      w.H = tall ? H : P.span;
-      warps.push_back(w);
-      if (!try_place(c, warps.back(), (int)warps.size() - 1)) {
-        err = "internal: a cell does not fit an empty warp";
-        return false;
+    placed[c0] = 1;
+    int k = advance(head), seen = 0;
+    head = k;  // c0 leaves the list
+    int last_kept = -1;
+    while (k < n_cells && seen < kPackLookahead) {
+      const int c = order[k];
+      if (placed[c]) {  // taken by an earlier warp's gap filling: unlink
+        const int nk = advance(k);
+        if (last_kept < 0) head = nk;
+        else next_of[last_kept] = nk;
+        k = nk;
+        continue;
       }
+      if (mask(c) != w.mask) break;
+      ++seen;
+      Warp& ww = warps[wi];
+      const CellPlan& P = L.plans[c];
+      const int size0 = (int)P.parts[P.part_of[spike_node ? spike_node[c] : 0]].nodes.size();
+      bool ok = false;
+      if (ww.min_lev + size0 <= ww.H) {
+        set_order(c);
+        ok = try_place(c, ww, wi);
+      }
+      const int nk = advance(k);
+      if (ok) {
+        placed[c] = 1;
+        if (last_kept < 0) head = nk;  // unlink k
+        else next_of[last_kept] = nk;
+      } else {
+        last_kept = k;
+      }
+      k = nk;
     }
+    // then the smallest remaining cells of the same channel set, to fill gaps
+    while (tail > 0 && placed[order[tail - 1]]) --tail;
+    int tk = tail;
+    seen = 0;
+    while (tk > head && seen < kPackLookahead) {
+      const int c = order[tk - 1];
+      --tk;
+      if (placed[c]) continue;
+      if (mask(c) != w.mask) break;
+      ++seen;
+      Warp& ww = warps[wi];
+      const CellPlan& P = L.plans[c];
+      const int size0 = (int)P.parts[P.part_of[spike_node ? spike_node[c] : 0]].nodes.size();
+      if (ww.min_lev + size0 > ww.H) continue;
+      set_order(c);
+      if (try_place(c, ww, wi)) placed[c] = 1;
+    }
+    while (head < n_cells && placed[order[head]]) head = advance(head);
   }
   L.n_groups = (int)warps.size();
   L.n_mail = 1;

@@ -317,50 +317,66 @@ template <int PREC>
 __device__ __forceinline__ void dense_step(const DevModel& M, int mask, int64_t e, double vnew, const double* kin) {
   using S = typename GateT<PREC>::S;
   using T = typename GateT<PREC>::M;
+  // Every input of the row is loaded first (the loads are independent and
+  // overlap), then the gates and currents are computed and stored.
+  T x[kChanGates];
+  double gb[kChanTypes];
+#pragma unroll
+  for (int t = 0; t < kChanTypes; ++t) {
+    if (mask & (1 << t)) {
+      gb[t] = M.ch_gbar[t][e];
+      for (int gi = chan_gate0(t); gi < (t + 1 < kChanTypes ? chan_gate0(t + 1) : kChanGates); ++gi)
+        x[gi] = g_load(static_cast<const S*>(M.ch_gate[gi]) + e);
+    }
+  }
+  const double ica0 = (mask & 16) ? M.ica[e] : 0.0;
+  const double cai0 = (mask & 48) ? M.cai[e] : 0.0;
   const T v = (T)vnew, tdt = (T)M.dt;
   auto upd = [&](int gi, const double* k6) -> double {
     T al, be;
     gate_ab<T>(k6, v, al, be);
     S* p = static_cast<S*>(M.ch_gate[gi]) + e;
-    return (double)g_store_ret(p, cnexp_step<T>(g_load(p), al, be, tdt));
+    return (double)g_store_ret(p, cnexp_step<T>(x[gi], al, be, tdt));
   };
   double g = 0.0, ge = 0.0;
   if (mask & 1) {  // NA3H: m^3 h
     const double m = upd(0, kin + (chan_kin0(0) + 1) * kLanes);
     const double h = upd(1, kin + (chan_kin0(0) + 7) * kLanes);
-    const double c = M.ch_gbar[0][e] * (m * m * m * h);
+    const double c = gb[0] * (m * m * m * h);
     g += c;
     ge = fma(c, kin[chan_kin0(0) * kLanes], ge);
   }
   if (mask & 2) {  // KDR4: n^4
     const double n = upd(2, kin + (chan_kin0(1) + 1) * kLanes);
-    const double c = M.ch_gbar[1][e] * ((n * n) * (n * n));
+    const double c = gb[1] * ((n * n) * (n * n));
     g += c;
     ge = fma(c, kin[chan_kin0(1) * kLanes], ge);
   }
   if (mask & 4) {  // KA: a^3 b
     const double a = upd(3, kin + (chan_kin0(2) + 1) * kLanes);
     const double b = upd(4, kin + (chan_kin0(2) + 7) * kLanes);
-    const double c = M.ch_gbar[2][e] * (a * a * a * b);
+    const double c = gb[2] * (a * a * a * b);
     g += c;
     ge = fma(c, kin[chan_kin0(2) * kLanes], ge);
   }
   if (mask & 8) {  // IH: q
     const double q = upd(5, kin + (chan_kin0(3) + 1) * kLanes);
-    const double c = M.ch_gbar[3][e] * q;
+    const double c = gb[3] * q;
     g += c;
     ge = fma(c, kin[chan_kin0(3) * kLanes], ge);
   }
+  double cai1 = cai0;
   if (mask & 16) {  // CAHVA: m^2 h, [Ca]i from the current of step k
     const double m = upd(6, kin + (chan_kin0(4) + 1) * kLanes);
     const double h = upd(7, kin + (chan_kin0(4) + 7) * kLanes);
     const double* kc = kin + chan_kin0(4) * kLanes;
     const T depth = (T)kc[13 * kLanes], taur = (T)kc[14 * kLanes], cainf = (T)kc[15 * kLanes];
-    T drive = T(-1e4) * (T)M.ica[e] / (T(2.0 * 96485.3321) * depth);
+    T drive = T(-1e4) * (T)ica0 / (T(2.0 * 96485.3321) * depth);
     if (drive < T(0)) drive = T(0);
-    const T cai = (T)M.cai[e];
-    M.cai[e] = (double)(cai + (T(1) - dexp_(-tdt / taur)) * (cainf + drive * taur - cai));
-    const double c = M.ch_gbar[4][e] * (m * m * h);
+    const T cai = (T)cai0;
+    cai1 = (double)(cai + (T(1) - dexp_(-tdt / taur)) * (cainf + drive * taur - cai));
+    M.cai[e] = cai1;
+    const double c = gb[4] * (m * m * h);
     const double eca = kc[0];
     g += c;
     ge = fma(c, eca, ge);
@@ -368,11 +384,11 @@ __device__ __forceinline__ void dense_step(const DevModel& M, int mask, int64_t 
   }
   if (mask & 32) {  // KCA: c, activated by the new [Ca]i
     const double* kk = kin + chan_kin0(5) * kLanes;
-    const T cai = (T)M.cai[e];
+    const T cai = (T)cai1;
     const T al = (T)kk[1 * kLanes] * cai / (cai + (T)kk[2 * kLanes]);
     S* p = static_cast<S*>(M.ch_gate[8]) + e;
-    const double x = (double)g_store_ret(p, cnexp_step<T>(g_load(p), al, (T)kk[3 * kLanes], tdt));
-    const double c = M.ch_gbar[5][e] * x;
+    const double xk = (double)g_store_ret(p, cnexp_step<T>(x[8], al, (T)kk[3 * kLanes], tdt));
+    const double c = gb[5] * xk;
     g += c;
     ge = fma(c, kk[0], ge);
   }
@@ -468,7 +484,7 @@ __global__ void k_setup_dense(DevModel M, double v_init, bool scale_gbar) {
 // into the trajectory buffers, and leave spikes, threshold flags and traces
 // untouched.
 template <int PREC, bool TRAJ, bool DENSE>
-__global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 4)
+__global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, DENSE ? 3 : 4)
     k_interval(DevModel M, int64_t J, int s_begin, int s_end, const int64_t* Jp) {
   using S = typename GateT<PREC>::S;
   using T = typename GateT<PREC>::M;

@@ -216,8 +216,8 @@ def _assemble(name, dt, tstop, cells, mechs, **kw):
     return sc
 
 
-def _hh_soma_cell(rng, n_dend, Ra=100.0, cm=1.0, soma_L=20.0, soma_d=20.0):
-    par, dx, diam, sec = random_section_tree(rng, n_dend)
+def _hh_soma_cell(rng, n_dend, Ra=100.0, cm=1.0, soma_L=20.0, soma_d=20.0, nseg=5):
+    par, dx, diam, sec = random_section_tree(rng, n_dend, nseg=nseg)
     return {
         "parent": np.concatenate([[-1], par]).astype(np.int32),
         "dx": np.concatenate([[soma_L], dx]),
@@ -441,6 +441,40 @@ def batched(n_cells: int = 50000, tstop: float = 1000.0, n_clip=(50, 5000), logn
     rec = off[:-1].astype(np.int32) if record == "soma" else np.zeros(0, np.int32)
     return _assemble("batched", dt, tstop, cells, mechs, rec_node=rec, threshold=-20.0,
                      meta={"seed": seed, "config": "batched"}, **kw)
+
+
+def morph_types(n_cells: int = 131072, cells_per_type: int = 32, tstop: float = 10.0, ring: int = 16,
+                weight: float = 0.02, seed: int = 1906, dt: float = 0.025) -> Scenario:
+    """Cells of many morphological types, as in the node-ordering study.
+
+    Every cell has 83 nodes: an HH soma and 41 passive sections of 2 segments
+    (L U[50,200] um, d U[1,3] um) in a random binary branching pattern that is
+    drawn per type.  ``cells_per_type`` consecutive gids share a type (1: every
+    cell distinct).  Cells form rings of ``ring`` (cell i drives i+1 through an
+    ExpSyn in the middle of its first section, delay 1 ms), each ring kicked
+    by one external event at 1 ms.
+    """
+    n_types = (n_cells + cells_per_type - 1) // cells_per_type
+    shapes = [_hh_soma_cell(_cell_rng(seed, t), 82, nseg=2) for t in range(n_types)]
+    cells = []
+    for g in range(n_cells):
+        cells.append(shapes[g // cells_per_type])
+    off = _offsets(cells)
+    hh, pas = _hh_and_pas(cells, off)
+    syn_node = (off[:-1] + 1).astype(np.int32)
+    syn = MechTable("expsyn", syn_node, {"tau": np.full(n_cells, 2.0), "e": np.zeros(n_cells)})
+    src = np.arange(n_cells, dtype=np.int32)
+    base = (src // ring) * ring
+    tgt = (base + (src - base + 1) % np.minimum(ring, n_cells - base)).astype(np.int32)
+    kick = np.arange(0, n_cells, ring, dtype=np.int32)
+    return _assemble(
+        "morph_types", dt, tstop, cells, [hh, pas, syn],
+        netcon_src=src, netcon_syn=tgt, netcon_w=np.full(n_cells, weight),
+        netcon_delay=np.full(n_cells, 1.0),
+        ev_syn=kick, ev_t=np.full(kick.shape[0], 1.0), ev_w=np.full(kick.shape[0], weight),
+        rec_node=off[:-1].astype(np.int32), threshold=-20.0,
+        meta={"seed": seed, "cells_per_type": cells_per_type},
+    )
 
 
 def passive_cable(nseg: int, L: float = 1000.0, diam: float = 1.0, Ra: float = 100.0, cm: float = 1.0,

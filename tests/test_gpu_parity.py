@@ -6,7 +6,7 @@ Bar (FP64 path): spike raster (gid, step) bit-exact; every voltage within
 import numpy as np
 import pytest
 
-from scenarios import ring16, network, adjoint_net, single_compartment, passive_cable
+from scenarios import ring16, network, adjoint_net, single_compartment, passive_cable, morph_types
 from oracle import simulate
 
 pytestmark = pytest.mark.gpu
@@ -268,3 +268,15 @@ def test_profile_counts_graph_launches(cn):
     assert k_n == 27 and p_n == 27 and k_ms > 0 and p_ms > 0
     md.cn_run(30.0)
     assert md.cn_profile_read()[1] == 3
+
+
+@pytest.mark.parametrize("cpt", [1, 4, 32])
+@pytest.mark.parametrize("mapping", [1, 0])
+def test_morphological_types(cn, cpt, mapping):
+    """Cells of 83 nodes with 1, 4 or 32 identical cells per branching type
+    (rings of 16, HH soma): same raster and voltages as the oracle whether
+    the 32 lanes of a warp hold identical or all different trees."""
+    sc = morph_types(n_cells=160, cells_per_type=cpt, tstop=25.0)
+    ref = run_oracle(sc)
+    assert len(ref["g"]) > 20
+    assert_parity(run_gpu(cn, sc, mapping=mapping), ref)
