@@ -171,9 +171,9 @@ def config_dict(args, sc, layout=None):
          "precision": args.precision}
     if layout is not None:
         mp, wpb, nw, tuned = layout
-        span, tall = mp & ~(1 << 20), bool(mp & (1 << 20))
-        d["layout"] = {"mapping": "one cell per lane" if mp == 1 else
-                       f"cells split to ~{span} rows per lane" + (", tall warps" if tall else ""),
+        span = mp & ~(3 << 20)
+        tall = ", warps twice the largest span" if mp & (2 << 20) else ", tall warps" if mp & (1 << 20) else ""
+        d["layout"] = {"mapping": "one cell per lane" if mp == 1 else f"cells split to ~{span} rows per lane" + tall,
                        "warps_per_block": wpb, "warps": nw,
                        "chosen_by": "autotuner" if args.mapping == 2 else "fixed"}
     return d

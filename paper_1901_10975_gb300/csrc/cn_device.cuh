@@ -108,8 +108,6 @@ struct DevModel {
   const int32_t* flags;
   // mechanism slots (rows carrying point processes or channels)
   const int32_t* slot_row;
-  const double* slot_ge0;   // ge of the slot's row
-  const double* slot_d00;   // d0 of the slot's row
   // synapses (ExpSyn)
   const int32_t* syn_row;      // warp row of the synapse (a lane's synapses by row, descending)
   double* syn_g;
@@ -138,6 +136,8 @@ struct DevModel {
   void* ch_gate[kChanGates];
   const double* ch_kin;
   double* cai;
+  double* ge_syn;  // per row: ge plus the ExpSyn sum of G E of the coming step (streamed by the solve)
+  double* d0_syn;  // per row: d0 plus the ExpSyn sum of G
   double* ch_g;    // channel conductance of the row for the coming step, / cdt
   double* ch_ge;   // its sum of g E, / cdt
   double* ica;

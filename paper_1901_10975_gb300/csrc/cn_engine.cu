@@ -420,9 +420,15 @@ CellPlan plan_cell(const int32_t* parent, int n, int target) {
   return P;
 }
 
+// Warp height policy of a mapping value: 0 = the opening cell's span,
+// 1 = the largest span, 2 = twice the largest span.
+int tall_factor(int32_t mapping) {
+  return (mapping & CN_MAP_TALL2) ? 2 : (mapping & CN_MAP_TALL) ? 1 : 0;
+}
+
 // Target span (rows per lane) of a mapping value; 0 = never split.
 int map_target(int32_t mapping, int64_t n_nodes, int32_t n_cells, bool adjoint) {
-  mapping &= ~CN_MAP_TALL;
+  mapping &= ~(CN_MAP_TALL | CN_MAP_TALL2);
   if (mapping >= 16) return mapping;
   if (mapping == CN_MAP_AUTO && !adjoint && n_cells > 0)
     return (int)std::max<int64_t>(16, (n_nodes + n_cells - 1) / n_cells);
@@ -483,7 +489,7 @@ struct Layout {
 constexpr int kPackLookahead = 512;  // remaining cells tried per warp  // refusals after which a warp takes no more cells
 
 bool build_layout(int32_t n_cells, const int32_t* off, const int32_t* parent, const int32_t* cell_mask,
-                  const int32_t* spike_node, int target, bool stack, bool tall, Layout& L, std::string& err) {
+                  const int32_t* spike_node, int target, bool stack, int tall, Layout& L, std::string& err) {
   auto mask = [&](int c) { return cell_mask ? cell_mask[c] : 0; };
   L.plans.assign(n_cells, CellPlan{});
   L.depth = 1;
@@ -605,7 +611,7 @@ bool build_layout(int32_t n_cells, const int32_t* off, const int32_t* parent, co
     std::fill(w.owner, w.owner + cn::kLanes, -1);
     std::fill(w.root, w.root + cn::kLanes, false);
     w.mask = mask(c0);
-    w.H = tall ? H : P0.span;
+    w.H = tall ? tall * H : P0.span;
     warps.push_back(w);
     const int wi = (int)warps.size() - 1;
     set_order(c0);
@@ -753,7 +759,7 @@ cn_status finalize(cn_model* m) {
   {
     std::string lerr;
     if (!build_layout(m->n_cells, m->off.data(), m->parent.data(), cell_mask.data(), m->spike_node.data(), target,
-                      !m->dense && m->ck_steps <= 0, (m->opt.mapping & CN_MAP_TALL) != 0, L, lerr))
+                      !m->dense && m->ck_steps <= 0, tall_factor(m->opt.mapping), L, lerr))
       return m->fail(CN_EINVAL, lerr);
   }
   const int depth = L.depth;
@@ -987,12 +993,12 @@ cn_status finalize(cn_model* m) {
   CN_CHECK(zeros(m, &pd, acc)); dm.bp = pd;
   CN_CHECK(zeros(m, &pd, acc)); dm.ge = pd;
   CN_CHECK(zeros(m, &pd, acc)); dm.d0 = pd;
+  CN_CHECK(zeros(m, &pd, acc)); dm.ge_syn = pd;
+  CN_CHECK(zeros(m, &pd, acc)); dm.d0_syn = pd;
   CN_CHECK(zeros(m, &pd, acc)); dm.a = pd;
   CN_CHECK(zeros(m, &pd, acc)); dm.b = pd;
   CN_CHECK(upload(m, &p32, h_flags)); dm.flags = p32;
   CN_CHECK(upload(m, &p32, h_slot_row)); dm.slot_row = p32;
-  CN_CHECK(zeros(m, &pd, std::max<int64_t>(sacc, 1))); dm.slot_ge0 = pd;
-  CN_CHECK(zeros(m, &pd, std::max<int64_t>(sacc, 1))); dm.slot_d00 = pd;
   CN_CHECK(upload(m, &p32, h_syn_row)); dm.syn_row = p32;
   CN_CHECK(zeros(m, &pd, rs.elems)); dm.syn_g = pd;
   CN_CHECK(zeros(m, &pd, rs.elems)); dm.syn_s = pd;
@@ -1098,7 +1104,6 @@ cn_status finalize(cn_model* m) {
   CN_CHECK(launch_checked(m, [&] { cn::k_setup_pad<<<nbe, 256, 0, st>>>(dm); }));
   CN_CHECK(launch_checked(m, [&] { cn::k_setup_geom<<<nbc, tb, 0, st>>>(dm, m->n_cells, d_off, d_parent, d_area, d_ri, d_cm, d_elem); }));
   CN_CHECK(launch_checked(m, [&] { cn::k_pas_apply<<<nb, tb, 0, st>>>(dm); }));
-  CN_CHECK(launch_checked(m, [&] { cn::k_setup_slots<<<nb, tb, 0, st>>>(dm); }));
   CN_CHECK(launch_checked(m, [&] { cn::k_setup_syn<<<nb, tb, 0, st>>>(dm, d_syn_area, d_syn_cm, d_syn_tau); }));
   CN_CHECK(launch_checked(m, [&] { cn::k_hh_params<<<nb, tb, 0, st>>>(dm); }));
   CN_CHECK(launch_checked(m, [&] { cn::k_setup_stim<<<nb, tb, 0, st>>>(dm, d_st_amp, d_st_area, d_st_cm); }));
@@ -1372,7 +1377,10 @@ cn_status autotune(cn_model* m) {
       const int32_t v = (int32_t)std::max<int64_t>(16, t);
       if (std::find(cand.begin(), cand.end(), v) == cand.end()) {
         cand.push_back(v);
-        if (!m->dense) cand.push_back(v | CN_MAP_TALL);
+        if (!m->dense) {
+          cand.push_back(v | CN_MAP_TALL);
+          cand.push_back(v | CN_MAP_TALL2);
+        }
       }
     }
   float best = 0.f;
@@ -1638,7 +1646,7 @@ cn_status cn_plan_layout(int32_t n_cells, const int32_t* cell_offset, const int3
   const int64_t nn = cell_offset[n_cells];
   Layout L;
   if (!build_layout(n_cells, cell_offset, parent, nullptr, nullptr, map_target(mapping, nn, n_cells, false), true,
-                    (mapping & CN_MAP_TALL) != 0, L, g_create_error))
+                    tall_factor(mapping), L, g_create_error))
     return CN_EINVAL;
   if (node_lane) std::copy(L.node_slot.begin(), L.node_slot.end(), node_lane);
   if (node_row) std::copy(L.node_row.begin(), L.node_row.end(), node_row);
@@ -1665,8 +1673,8 @@ cn_status cn_model_create(const cn_morph* morph, const cn_mech_table* mechs, int
   if ((o.alloc == nullptr) != (o.free == nullptr)) return bad("alloc and free must be given together");
   if (o.warps_per_block < 0 || o.warps_per_block > cn::kMaxWarpsPerBlock) return bad("warps_per_block must be 0..4");
   {
-    const int32_t mv = o.mapping & ~CN_MAP_TALL;
-    if (o.mapping < 0 || (mv > CN_MAP_TUNE && mv < 16) || ((o.mapping & CN_MAP_TALL) && mv < 16))
+    const int32_t mv = o.mapping & ~(CN_MAP_TALL | CN_MAP_TALL2);
+    if (o.mapping < 0 || (mv > CN_MAP_TUNE && mv < 16) || ((o.mapping & (CN_MAP_TALL | CN_MAP_TALL2)) && mv < 16))
       return bad("mapping must be 0, 1, 2, or a span >= 16 (optionally with CN_MAP_TALL)");
   }
   const int32_t nc = morph->n_cells;
@@ -2072,7 +2080,6 @@ cn_status cn_set_cell_param(cn_model* m, int32_t param, const double* values) {
   }
   if (param < 2) CN_CHECK(launch_checked(m, [&] { cn::k_hh_params<<<nb, tb, 0, m->stream>>>(dm); }));
   else CN_CHECK(launch_checked(m, [&] { cn::k_pas_apply<<<nb, tb, 0, m->stream>>>(dm); }));
-  CN_CHECK(launch_checked(m, [&] { cn::k_setup_slots<<<nb, tb, 0, m->stream>>>(dm); }));
   CN_TRY_CUDA(m, cudaStreamSynchronize(m->stream));
   return CN_OK;
 }

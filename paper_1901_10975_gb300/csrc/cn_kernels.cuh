@@ -61,6 +61,8 @@ __global__ void k_pas_apply(DevModel M) {
       d0[i] = 1.0;
       ge[i] = 0.0;
     }
+    M.d0_syn[i] = d0[i];  // rows with synapses are rewritten every step
+    M.ge_syn[i] = ge[i];
   }
 }
 
@@ -128,21 +130,6 @@ __global__ void k_state_init(DevModel M, double v_init) {
   M.ev_count[slot] = 0;
 }
 
-// Per-slot copies of the slot row's constants (the slot buffer is reset to
-// them at the start of every step).
-__global__ void k_setup_slots(DevModel M) {
-  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
-  if (slot >= M.n_slots) return;
-  const int g = slot / kLanes, lane = slot % kLanes;
-  const int n = M.s_nslot[slot];
-  const int64_t sb = M.g_slot_base[g] + lane, nb = M.g_node_base[g] + lane;
-  for (int t = 0; t < n; ++t) {
-    const int64_t i = sb + (int64_t)t * kLanes;
-    const int64_t r = nb + (int64_t)M.slot_row[i] * kLanes;
-    const_cast<double*>(M.slot_ge0)[i] = M.ge[r];
-    const_cast<double*>(M.slot_d00)[i] = M.d0[r];
-  }
-}
 
 // ExpSyn constants: s = 100/(area cdt) (nA -> mA/cm2, row-scaled),
 // decay = exp(-dt/tau), g = 0.
@@ -314,69 +301,79 @@ __device__ __forceinline__ void dense_cur(const DevModel& M, int mask, int64_t e
 // next calcium update.  The values are those a separate nrn_cur at the start
 // of step k+1 would compute.
 template <int PREC>
-__device__ __forceinline__ void dense_step(const DevModel& M, int mask, int64_t e, double vnew, const double* kin) {
-  using S = typename GateT<PREC>::S;
-  using T = typename GateT<PREC>::M;
-  // Every input of the row is loaded first (the loads are independent and
-  // overlap), then the gates and currents are computed and stored.
-  T x[kChanGates];
+struct ChanIn {  // the inputs of one row's channel update
+  typename GateT<PREC>::M x[kChanGates];
   double gb[kChanTypes];
+  double ica, cai;
+};
+
+template <int PREC>
+__device__ __forceinline__ void dense_load(const DevModel& M, int mask, int64_t e, ChanIn<PREC>& in) {
+  using S = typename GateT<PREC>::S;
 #pragma unroll
   for (int t = 0; t < kChanTypes; ++t) {
     if (mask & (1 << t)) {
-      gb[t] = M.ch_gbar[t][e];
+      in.gb[t] = M.ch_gbar[t][e];
+#pragma unroll
       for (int gi = chan_gate0(t); gi < (t + 1 < kChanTypes ? chan_gate0(t + 1) : kChanGates); ++gi)
-        x[gi] = g_load(static_cast<const S*>(M.ch_gate[gi]) + e);
+        in.x[gi] = g_load(static_cast<const S*>(M.ch_gate[gi]) + e);
     }
   }
-  const double ica0 = (mask & 16) ? M.ica[e] : 0.0;
-  const double cai0 = (mask & 48) ? M.cai[e] : 0.0;
+  in.ica = (mask & 16) ? M.ica[e] : 0.0;
+  in.cai = (mask & 48) ? M.cai[e] : 0.0;
+}
+
+template <int PREC>
+__device__ __forceinline__ void dense_step(const DevModel& M, int mask, int64_t e, double vnew, const double* kin,
+                                           const ChanIn<PREC>& in) {
+  using S = typename GateT<PREC>::S;
+  using T = typename GateT<PREC>::M;
   const T v = (T)vnew, tdt = (T)M.dt;
   auto upd = [&](int gi, const double* k6) -> double {
     T al, be;
     gate_ab<T>(k6, v, al, be);
     S* p = static_cast<S*>(M.ch_gate[gi]) + e;
-    return (double)g_store_ret(p, cnexp_step<T>(x[gi], al, be, tdt));
+    return (double)g_store_ret(p, cnexp_step<T>(in.x[gi], al, be, tdt));
   };
   double g = 0.0, ge = 0.0;
   if (mask & 1) {  // NA3H: m^3 h
     const double m = upd(0, kin + (chan_kin0(0) + 1) * kLanes);
     const double h = upd(1, kin + (chan_kin0(0) + 7) * kLanes);
-    const double c = gb[0] * (m * m * m * h);
+    const double c = in.gb[0] * (m * m * m * h);
     g += c;
     ge = fma(c, kin[chan_kin0(0) * kLanes], ge);
   }
   if (mask & 2) {  // KDR4: n^4
     const double n = upd(2, kin + (chan_kin0(1) + 1) * kLanes);
-    const double c = gb[1] * ((n * n) * (n * n));
+    const double c = in.gb[1] * ((n * n) * (n * n));
     g += c;
     ge = fma(c, kin[chan_kin0(1) * kLanes], ge);
   }
   if (mask & 4) {  // KA: a^3 b
     const double a = upd(3, kin + (chan_kin0(2) + 1) * kLanes);
     const double b = upd(4, kin + (chan_kin0(2) + 7) * kLanes);
-    const double c = gb[2] * (a * a * a * b);
+    const double c = in.gb[2] * (a * a * a * b);
     g += c;
     ge = fma(c, kin[chan_kin0(2) * kLanes], ge);
   }
   if (mask & 8) {  // IH: q
     const double q = upd(5, kin + (chan_kin0(3) + 1) * kLanes);
-    const double c = gb[3] * q;
+    const double c = in.gb[3] * q;
     g += c;
     ge = fma(c, kin[chan_kin0(3) * kLanes], ge);
   }
-  double cai1 = cai0;
+  double cai1 = in.cai;
   if (mask & 16) {  // CAHVA: m^2 h, [Ca]i from the current of step k
     const double m = upd(6, kin + (chan_kin0(4) + 1) * kLanes);
     const double h = upd(7, kin + (chan_kin0(4) + 7) * kLanes);
     const double* kc = kin + chan_kin0(4) * kLanes;
     const T depth = (T)kc[13 * kLanes], taur = (T)kc[14 * kLanes], cainf = (T)kc[15 * kLanes];
-    T drive = T(-1e4) * (T)ica0 / (T(2.0 * 96485.3321) * depth);
+    T drive = T(-1e4) * (T)in.ica / (T(2.0 * 96485.3321) * depth);
     if (drive < T(0)) drive = T(0);
-    const T cai = (T)cai0;
+    const T cai = (T)in.cai;
     cai1 = (double)(cai + (T(1) - dexp_(-tdt / taur)) * (cainf + drive * taur - cai));
     M.cai[e] = cai1;
-    const double c = gb[4] * (m * m * h);
+    const double c = in.gb[4] * (m * m * h);
     const double eca = kc[0];
     g += c;
     ge = fma(c, eca, ge);
@@ -387,8 +384,8 @@ __device__ __forceinline__ void dense_step(const DevModel& M, int mask, int64_t 
     const T cai = (T)cai1;
     const T al = (T)kk[1 * kLanes] * cai / (cai + (T)kk[2 * kLanes]);
     S* p = static_cast<S*>(M.ch_gate[8]) + e;
-    const double xk = (double)g_store_ret(p, cnexp_step<T>(x[8], al, (T)kk[3 * kLanes], tdt));
-    const double c = gb[5] * xk;
+    const double xk = (double)g_store_ret(p, cnexp_step<T>(in.x[8], al, (T)kk[3 * kLanes], tdt));
+    const double c = in.gb[5] * xk;
     g += c;
     ge = fma(c, kk[0], ge);
   }
@@ -484,7 +481,7 @@ __global__ void k_setup_dense(DevModel M, double v_init, bool scale_gbar) {
 // into the trajectory buffers, and leave spikes, threshold flags and traces
 // untouched.
 template <int PREC, bool TRAJ, bool DENSE>
-__global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, DENSE ? 3 : 4)
+__global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, DENSE ? 2 : 4)
     k_interval(DevModel M, int64_t J, int s_begin, int s_end, const int64_t* Jp) {
   using S = typename GateT<PREC>::S;
   using T = typename GateT<PREC>::M;
@@ -532,8 +529,8 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, DENSE ? 3 : 4)
   // this lane's column of every per-row array
   double* const gv = M.v + nb;
   double* const gbp = M.bp + nb;
-  const double* const gge = M.ge + nb;
-  const double* const gd0 = M.d0 + nb;
+  const double* const gge = M.ge_syn + nb;  // row constants with this step's synaptic terms
+  const double* const gd0 = M.d0_syn + nb;
   const double* const ga = M.a + nb;
   const double* const gb = M.b + nb;
   const int32_t* const gfl = M.flags + nb;
@@ -588,53 +585,75 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, DENSE ? 3 : 4)
     cp_async_commit();
   };
 
-  // Slot buffer: seeded once per launch with the rows' constants; after that
-  // every elimination row re-seeds its own slot from the ring for the next step.
+  // Slot buffer (HH and IClamp terms of a row): cleared once per launch; after
+  // that every elimination row clears its own slot for the next step.
   for (int t = 0; t < SLR; ++t) {
     if (t < nslot) {
-      const int64_t i = slb + (int64_t)t * kLanes;
-      sl_ge[t * kLanes] = M.slot_ge0[i];
-      sl_d[t * kLanes] = M.slot_d00[i];
+      sl_ge[t * kLanes] = 0.0;
+      sl_d[t * kLanes] = 0.0;
     }
   }
 
   for (int s = s_begin; s < s_end; ++s) {
     const int64_t k = T0 + s;
-    // start streaming the top rows while the mechanisms are evaluated
-#pragma unroll
-    for (int u = 0; u < kElimRows; ++u) fetch_elim(R - 1 - u, u);
     // (1) event delivery
     while (ei < ne && ev[ei].step == s) {
       M.syn_g[sb + (int64_t)ev[ei].syn * kLanes] += ev[ei].w;
       ++ei;
     }
-    // (2) nrn_cur: HH and IClamp into the slot buffer; the synapses of the
-    //     lane are merged into the elimination below, in row order
-    // Two synapses are kept in registers (the current one and the next) so
-    // that a synapse's loads are issued one synapse ahead of its row.
-    int sq = 0, srow = -1, srow2 = -1;
-    int64_t si_ = 0, si2 = 0;
-    double ng = 0.0, ns_ = 0.0, ne_ = 0.0, nd_ = 0.0;
-    double ng2 = 0.0, ns2 = 0.0, ne2 = 0.0, nd2 = 0.0;
-    auto load_syn = [&]() {  // the lane's synapse sq (rows descending) into the second stage
-      if (sq < nsyn) {
-        si2 = sb + (int64_t)sq * kLanes;
-        srow2 = M.syn_row[si2];
-        ng2 = M.syn_g[si2];
-        ns2 = M.syn_s[si2];
-        ne2 = M.syn_e[si2];
-        nd2 = M.syn_decay[si2];
-        ++sq;
-      } else {
-        srow2 = -1;
+    // (2) nrn_cur.  ExpSyn: G = g s and G E of every synapse of the lane
+    //     (kSynBatch at a time, their loads in flight together), summed per
+    //     row onto the row's constants into ge_syn / d0_syn, which the
+    //     elimination streams; then the v-independent decay of g.  A lane's
+    //     synapses are sorted by row, so each row's sum is contiguous.
+    {
+      constexpr int kSynBatch = 4;
+      int prow = -1;
+      double age = 0.0, ad = 0.0;
+      for (int q0 = 0; q0 < nsyn; q0 += kSynBatch) {
+        double sg_[kSynBatch], ss_[kSynBatch], se_[kSynBatch], sd_[kSynBatch], cg[kSynBatch], cd[kSynBatch];
+        int sr_[kSynBatch];
+#pragma unroll
+        for (int u = 0; u < kSynBatch; ++u) {
+          sr_[u] = -1;
+          if (q0 + u < nsyn) {
+            const int64_t i = sb + (int64_t)(q0 + u) * kLanes;
+            sr_[u] = M.syn_row[i];
+            sg_[u] = M.syn_g[i];
+            ss_[u] = M.syn_s[i];
+            se_[u] = M.syn_e[i];
+            sd_[u] = M.syn_decay[i];
+            cg[u] = M.ge[nb + (int64_t)sr_[u] * kLanes];
+            cd[u] = M.d0[nb + (int64_t)sr_[u] * kLanes];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < kSynBatch; ++u) {
+          if (sr_[u] < 0) continue;
+          if (sr_[u] != prow) {
+            if (prow >= 0) {
+              M.ge_syn[nb + (int64_t)prow * kLanes] = age;
+              M.d0_syn[nb + (int64_t)prow * kLanes] = ad;
+            }
+            prow = sr_[u];
+            age = cg[u];
+            ad = cd[u];
+          }
+          const double G = sg_[u] * ss_[u];
+          age = fma(G, se_[u], age);
+          ad += G;
+          M.syn_g[sb + (int64_t)(q0 + u) * kLanes] = sg_[u] * sd_[u];
+        }
       }
-    };
-    auto next_syn = [&]() {
-      srow = srow2; si_ = si2; ng = ng2; ns_ = ns2; ne_ = ne2; nd_ = nd2;
-      load_syn();
-    };
-    load_syn();
-    next_syn();
+      if (prow >= 0) {
+        M.ge_syn[nb + (int64_t)prow * kLanes] = age;
+        M.d0_syn[nb + (int64_t)prow * kLanes] = ad;
+      }
+    }
+    // start streaming the top rows (after this lane's row constants are final)
+#pragma unroll
+    for (int u = 0; u < kElimRows; ++u) fetch_elim(R - 1 - u, u);
+    // HH and IClamp into the slot buffer
     for (int q = 0; q < HR; ++q) {
       if (q < nhh) {
         const int64_t i = hb + (int64_t)q * kLanes;
@@ -673,12 +692,16 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, DENSE ? 3 : 4)
           const int f = e_fl[ro];
           const int sl = f & kNoSlot;
           const bool hs = sl != kNoSlot;
-          const int si = (hs ? sl : 0) * kLanes;
-          const double g0 = e_ge[ro], d00 = e_d0[ro];
-          const double sg = sl_ge[si], sd = sl_d[si];
-          if (hs) {
-            sl_ge[si] = g0;  // re-seed the slot for the next step
-            sl_d[si] = d00;
+          double acc_ge = e_ge[ro];  // constants with this step's synaptic terms
+          double dd0 = e_d0[ro];
+          if (__any_sync(0xffffffffu, hs)) {  // HH / IClamp rows (somas): add and clear the slot
+            if (hs) {
+              const int si = sl * kLanes;
+              acc_ge += sl_ge[si];
+              dd0 += sl_d[si];
+              sl_ge[si] = 0.0;
+              sl_d[si] = 0.0;
+            }
           }
           const int np = (f >> kNFarShift) & kNFarMask;
           const int tp = np > 0 ? top - 1 : top;
@@ -688,15 +711,6 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, DENSE ? 3 : 4)
           const double fx = np > 0 ? st_x[ti] : 0.0;
           const double fb = np > 0 ? st_y[ti] : 0.0;
           top = tp;
-          double acc_ge = hs ? sg : g0;
-          double dd0 = hs ? sd : d00;
-          while (srow == j) {  // ExpSyn G and G E at this row; then its decay (v-independent)
-            const double G = ng * ns_;
-            acc_ge = fma(G, ne_, acc_ge);
-            dd0 += G;
-            M.syn_g[si_] = ng * nd_;
-            next_syn();
-          }
           double base = e_v[ro] + acc_ge;
           if (DENSE) {  // channel currents of this step (computed at the end of the previous one)
             base += e_cge[ro];
@@ -776,7 +790,6 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, DENSE ? 3 : 4)
           const double vj = fma(-b_bp[ro], vp, b_x[ro]);
           gv[(int64_t)j * kLanes] = vj;
           if (f & kJuncBit) mail[4 * ((f >> kJmailShift) & kMailMask) + 3] = vj;
-          if (DENSE && (f & kRealBit)) dense_step<PREC>(M, chmask, nb + (int64_t)j * kLanes, vj, kin);
           if (TRAJ) M.traj_v[(k + 1 - M.traj_k0) * M.node_elems + nb + (int64_t)j * kLanes] = vj;
           const int np = (f >> kNFarShift) & kNFarMask;
           if (np > 0) st_x[tp * kLanes] = vj;
@@ -788,6 +801,31 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, DENSE ? 3 : 4)
       }
     }
     cp_async_wait<0>();
+    // (3b) channel types: nrn_state at v_{k+1}, then their nrn_cur for the
+    //      next step.  Rows are independent here, so kChanBatch rows load
+    //      their inputs together before any of them computes.
+    if (DENSE) {
+      constexpr int kChanBatch = 2;
+      for (int j0 = 0; j0 < R; j0 += kChanBatch) {
+        ChanIn<PREC> in[kChanBatch];
+        double vv[kChanBatch];
+        int fr[kChanBatch];
+#pragma unroll
+        for (int u = 0; u < kChanBatch; ++u) {
+          const int j = j0 + u;
+          fr[u] = 0;
+          if (j < R) {
+            const int64_t e = nb + (int64_t)j * kLanes;
+            fr[u] = M.flags[e] & kRealBit;
+            vv[u] = M.v[e];
+            dense_load<PREC>(M, chmask, e, in[u]);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < kChanBatch; ++u)
+          if (fr[u]) dense_step<PREC>(M, chmask, nb + (int64_t)(j0 + u) * kLanes, vv[u], kin, in[u]);
+      }
+    }
     // (4) nrn_state: HH gates (cnexp) at v_{k+1}
     for (int q = 0; q < HR; ++q) {
       if (q < nhh) {
