@@ -189,9 +189,10 @@ __host__ __device__ inline size_t ring_bytes(bool dense) {
   return ((elim > back ? elim : back) + 15) / 16 * 16;
 }
 __host__ __device__ inline size_t interval_smem_bytes(int stack_depth, int max_slots, bool dense, int n_mail) {
-  return ring_bytes(dense) + (size_t)stack_depth * kLanes * 3 * sizeof(double) +
+  return ring_bytes(dense) + (size_t)(stack_depth + 1) * kLanes * 3 * sizeof(double) +
          (size_t)max_slots * kLanes * 2 * sizeof(double) +
-         (dense ? (size_t)kChanParams * kLanes * sizeof(double) : 0) + (size_t)n_mail * 4 * sizeof(double);
+         (dense ? (size_t)kChanParams * kLanes * (sizeof(double) + sizeof(float)) : 0) +
+         (size_t)n_mail * 4 * sizeof(double);
 }
 
 // Per-thread asynchronous global->shared copies (through L1, so a lane's own

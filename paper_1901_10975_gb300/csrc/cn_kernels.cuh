@@ -243,9 +243,9 @@ __global__ void k_next_interval(int64_t* Jp) { *Jp += 1; }
 // the matrix in FP64 whatever the gate precision.  kin points at the lane's
 // kinetics in shared memory ([param][32]).
 template <typename T>
-__device__ __forceinline__ void gate_ab(const double* kin, T v, T& al, T& be) {
-  const T A = (T)kin[0], vh = (T)kin[kLanes], k = (T)kin[2 * kLanes];
-  const T B = (T)kin[3 * kLanes], vh2 = (T)kin[4 * kLanes], k2 = (T)kin[5 * kLanes];
+__device__ __forceinline__ void gate_ab(const T* kin, T v, T& al, T& be) {
+  const T A = kin[0], vh = kin[kLanes], k = kin[2 * kLanes];
+  const T B = kin[3 * kLanes], vh2 = kin[4 * kLanes], k2 = kin[5 * kLanes];
   al = vtrap<T>(A, vh, k, v);
   be = B * dexp_(-(v - vh2) / k2);
 }
@@ -256,37 +256,42 @@ template <int PREC>
 __device__ __forceinline__ void dense_cur(const DevModel& M, int mask, int64_t e, double v, const double* kin,
                                           int64_t ks, double& G, double& GE) {
   using S = typename GateT<PREC>::S;
-  auto x = [&](int gi) { return (double)g_load(static_cast<const S*>(M.ch_gate[gi]) + e); };
+  using T = typename GateT<PREC>::M;
+  auto x = [&](int gi) { return (T)g_load(static_cast<const S*>(M.ch_gate[gi]) + e); };
   double g = 0.0, ge = 0.0;
   if (mask & 1) {  // NA3H: m^3 h
-    const double m = x(0), c = M.ch_gbar[0][e] * (m * m * m * x(1));
+    const T m = x(0);
+    const double c = M.ch_gbar[0][e] * (double)(m * m * m * x(1));
     g += c;
     ge = fma(c, kin[chan_kin0(0) * ks], ge);
   }
   if (mask & 2) {  // KDR4: n^4
-    const double n = x(2), c = M.ch_gbar[1][e] * ((n * n) * (n * n));
+    const T n = x(2);
+    const double c = M.ch_gbar[1][e] * (double)((n * n) * (n * n));
     g += c;
     ge = fma(c, kin[chan_kin0(1) * ks], ge);
   }
   if (mask & 4) {  // KA: a^3 b
-    const double a = x(3), c = M.ch_gbar[2][e] * (a * a * a * x(4));
+    const T a = x(3);
+    const double c = M.ch_gbar[2][e] * (double)(a * a * a * x(4));
     g += c;
     ge = fma(c, kin[chan_kin0(2) * ks], ge);
   }
   if (mask & 8) {  // IH: q
-    const double c = M.ch_gbar[3][e] * x(5);
+    const double c = M.ch_gbar[3][e] * (double)x(5);
     g += c;
     ge = fma(c, kin[chan_kin0(3) * ks], ge);
   }
   if (mask & 16) {  // CAHVA: m^2 h; its current drives [Ca]i
-    const double m = x(6), c = M.ch_gbar[4][e] * (m * m * x(7));
+    const T m = x(6);
+    const double c = M.ch_gbar[4][e] * (double)(m * m * x(7));
     const double eca = kin[chan_kin0(4) * ks];
     g += c;
     ge = fma(c, eca, ge);
     M.ica[e] = c * M.cdt[e] * (v - eca);
   }
   if (mask & 32) {  // KCA: c
-    const double c = M.ch_gbar[5][e] * x(8);
+    const double c = M.ch_gbar[5][e] * (double)x(8);
     g += c;
     ge = fma(c, kin[chan_kin0(5) * ks], ge);
   }
@@ -325,55 +330,58 @@ __device__ __forceinline__ void dense_load(const DevModel& M, int mask, int64_t 
 
 template <int PREC>
 __device__ __forceinline__ void dense_step(const DevModel& M, int mask, int64_t e, double vnew, const double* kin,
-                                           const ChanIn<PREC>& in) {
+                                           const typename GateT<PREC>::M* kinT, const ChanIn<PREC>& in) {
   using S = typename GateT<PREC>::S;
   using T = typename GateT<PREC>::M;
   const T v = (T)vnew, tdt = (T)M.dt;
-  auto upd = [&](int gi, const double* k6) -> double {
+  // the gate powers are formed in the gate type; gbar times that product
+  // and the sums that enter the matrix are FP64
+  auto upd = [&](int gi, const T* k6) -> T {
     T al, be;
     gate_ab<T>(k6, v, al, be);
     S* p = static_cast<S*>(M.ch_gate[gi]) + e;
-    return (double)g_store_ret(p, cnexp_step<T>(in.x[gi], al, be, tdt));
+    return g_store_ret(p, cnexp_step<T>(in.x[gi], al, be, tdt));
   };
   double g = 0.0, ge = 0.0;
   if (mask & 1) {  // NA3H: m^3 h
-    const double m = upd(0, kin + (chan_kin0(0) + 1) * kLanes);
-    const double h = upd(1, kin + (chan_kin0(0) + 7) * kLanes);
-    const double c = in.gb[0] * (m * m * m * h);
+    const T m = upd(0, kinT + (chan_kin0(0) + 1) * kLanes);
+    const T h = upd(1, kinT + (chan_kin0(0) + 7) * kLanes);
+    const double c = in.gb[0] * (double)(m * m * m * h);
     g += c;
     ge = fma(c, kin[chan_kin0(0) * kLanes], ge);
   }
   if (mask & 2) {  // KDR4: n^4
-    const double n = upd(2, kin + (chan_kin0(1) + 1) * kLanes);
-    const double c = in.gb[1] * ((n * n) * (n * n));
+    const T n = upd(2, kinT + (chan_kin0(1) + 1) * kLanes);
+    const double c = in.gb[1] * (double)((n * n) * (n * n));
     g += c;
     ge = fma(c, kin[chan_kin0(1) * kLanes], ge);
   }
   if (mask & 4) {  // KA: a^3 b
-    const double a = upd(3, kin + (chan_kin0(2) + 1) * kLanes);
-    const double b = upd(4, kin + (chan_kin0(2) + 7) * kLanes);
-    const double c = in.gb[2] * (a * a * a * b);
+    const T a = upd(3, kinT + (chan_kin0(2) + 1) * kLanes);
+    const T b = upd(4, kinT + (chan_kin0(2) + 7) * kLanes);
+    const double c = in.gb[2] * (double)(a * a * a * b);
     g += c;
     ge = fma(c, kin[chan_kin0(2) * kLanes], ge);
   }
   if (mask & 8) {  // IH: q
-    const double q = upd(5, kin + (chan_kin0(3) + 1) * kLanes);
-    const double c = in.gb[3] * q;
+    const T q = upd(5, kinT + (chan_kin0(3) + 1) * kLanes);
+    const double c = in.gb[3] * (double)q;
     g += c;
     ge = fma(c, kin[chan_kin0(3) * kLanes], ge);
   }
   double cai1 = in.cai;
   if (mask & 16) {  // CAHVA: m^2 h, [Ca]i from the current of step k
-    const double m = upd(6, kin + (chan_kin0(4) + 1) * kLanes);
-    const double h = upd(7, kin + (chan_kin0(4) + 7) * kLanes);
+    const T m = upd(6, kinT + (chan_kin0(4) + 1) * kLanes);
+    const T h = upd(7, kinT + (chan_kin0(4) + 7) * kLanes);
     const double* kc = kin + chan_kin0(4) * kLanes;
-    const T depth = (T)kc[13 * kLanes], taur = (T)kc[14 * kLanes], cainf = (T)kc[15 * kLanes];
+    const T* kct = kinT + chan_kin0(4) * kLanes;
+    const T depth = kct[13 * kLanes], taur = kct[14 * kLanes], cainf = kct[15 * kLanes];
     T drive = T(-1e4) * (T)in.ica / (T(2.0 * 96485.3321) * depth);
     if (drive < T(0)) drive = T(0);
     const T cai = (T)in.cai;
     cai1 = (double)(cai + (T(1) - dexp_(-tdt / taur)) * (cainf + drive * taur - cai));
     M.cai[e] = cai1;
-    const double c = in.gb[4] * (m * m * h);
+    const double c = in.gb[4] * (double)(m * m * h);
     const double eca = kc[0];
     g += c;
     ge = fma(c, eca, ge);
@@ -381,11 +389,12 @@ __device__ __forceinline__ void dense_step(const DevModel& M, int mask, int64_t 
   }
   if (mask & 32) {  // KCA: c, activated by the new [Ca]i
     const double* kk = kin + chan_kin0(5) * kLanes;
+    const T* kkt = kinT + chan_kin0(5) * kLanes;
     const T cai = (T)cai1;
-    const T al = (T)kk[1 * kLanes] * cai / (cai + (T)kk[2 * kLanes]);
+    const T al = kkt[1 * kLanes] * cai / (cai + kkt[2 * kLanes]);
     S* p = static_cast<S*>(M.ch_gate[8]) + e;
-    const double xk = (double)g_store_ret(p, cnexp_step<T>(in.x[8], al, (T)kk[3 * kLanes], tdt));
-    const double c = in.gb[5] * xk;
+    const T xk = g_store_ret(p, cnexp_step<T>(in.x[8], al, kkt[3 * kLanes], tdt));
+    const double c = in.gb[5] * (double)xk;
     g += c;
     ge = fma(c, kk[0], ge);
   }
@@ -514,17 +523,26 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, DENSE ? 2 : 4)
   int32_t* const b_fl = reinterpret_cast<int32_t*>(reinterpret_cast<double*>(smem) + 2 * kBackRows * kLanes) + lane;
   double* const wsm = reinterpret_cast<double*>(smem + ring_bytes(DENSE));
   double* const st_a = wsm + lane;  // far stack [DS][32] each
-  double* const st_x = st_a + DS * kLanes;
-  double* const st_y = st_x + DS * kLanes;
-  double* const sl_ge = st_y + DS * kLanes;  // slot buffer [max_slots][32]
+  double* const st_x = st_a + (DS + 1) * kLanes;  // entry DS stays zero: rows that pop nothing read it
+  double* const st_y = st_x + (DS + 1) * kLanes;
+  double* const sl_ge = st_y + (DS + 1) * kLanes;  // slot buffer [max_slots][32]
   double* const sl_d = sl_ge + M.max_slots * kLanes;
   double* const kin = sl_d + M.max_slots * kLanes;  // dense kinetics [kChanParams][32]
   // mailbox [n_mail][4] shared by the warp: a part root leaves (-a, x, b/d)
   // for its junction row, the junction row leaves v for the part root
-  double* const mail = wsm + (3 * DS + 2 * M.max_slots + (DENSE ? kChanParams : 0)) * kLanes;
+  double* const mail = wsm + (3 * (DS + 1) + 2 * M.max_slots + (DENSE ? kChanParams : 0)) * kLanes;
+  st_a[DS * kLanes] = 0.0;
+  st_x[DS * kLanes] = 0.0;
+  st_y[DS * kLanes] = 0.0;
   const int chmask = DENSE ? M.g_chmask[g] : 0;
+  // gate kinetics in the gate arithmetic's type (after the mailbox); FP64 uses kin itself
+  T* const kinT = (DENSE && PREC != 0) ? reinterpret_cast<T*>(mail + 4 * M.n_mail) + lane
+                                       : reinterpret_cast<T*>(kin);
   if (DENSE)
-    for (int q = 0; q < kChanParams; ++q) kin[q * kLanes] = M.ch_kin[(int64_t)q * M.n_slots + slot];
+    for (int q = 0; q < kChanParams; ++q) {
+      kin[q * kLanes] = M.ch_kin[(int64_t)q * M.n_slots + slot];
+      if (PREC != 0) kinT[q * kLanes] = (T)kin[q * kLanes];
+    }
 
   // this lane's column of every per-row array
   double* const gv = M.v + nb;
@@ -705,11 +723,11 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, DENSE ? 2 : 4)
           }
           const int np = (f >> kNFarShift) & kNFarMask;
           const int tp = np > 0 ? top - 1 : top;
-          const int ti = (tp < DS ? tp : DS - 1) * kLanes;
-          // stale stack words must not reach the FMAs (0 * NaN is NaN): select
-          const double fa = np > 0 ? st_a[ti] : 0.0;
-          const double fx = np > 0 ? st_x[ti] : 0.0;
-          const double fb = np > 0 ? st_y[ti] : 0.0;
+          // a row that pops nothing reads the zero entry DS (no stale words reach the FMAs)
+          const int ti = (np > 0 ? min(max(tp, 0), DS - 1) : DS) * kLanes;
+          const double fa = st_a[ti];
+          const double fx = st_x[ti];
+          const double fb = st_y[ti];
           top = tp;
           double base = e_v[ro] + acc_ge;
           if (DENSE) {  // channel currents of this step (computed at the end of the previous one)
@@ -823,7 +841,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, DENSE ? 2 : 4)
         }
 #pragma unroll
         for (int u = 0; u < kChanBatch; ++u)
-          if (fr[u]) dense_step<PREC>(M, chmask, nb + (int64_t)(j0 + u) * kLanes, vv[u], kin, in[u]);
+          if (fr[u]) dense_step<PREC>(M, chmask, nb + (int64_t)(j0 + u) * kLanes, vv[u], kin, kinT, in[u]);
       }
     }
     // (4) nrn_state: HH gates (cnexp) at v_{k+1}
