@@ -207,6 +207,17 @@ cn_status cn_add_events(cn_model* m, int64_t n, const int32_t* target_syn, const
  * Before the first cn_run only.                                            */
 cn_status cn_add_stim(cn_model* m, int32_t node, double del_ms, double dur_ms, double amp_nA);
 
+/* Half gap junctions (gap-junction coupling under the fixed step, Section
+ * 3.5; voltages exchanged every time step, Section 5; here they stay on the
+ * device): entry i injects g_uS[i] (v(peer[i]) - v(node[i])) nA into
+ * node[i], with node[i]'s own voltage implicit and the peer's voltage of
+ * the start of the step (voltages are exchanged every step).  A symmetric
+ * junction is two entries.  node and peer are global node indices (host
+ * arrays, copied).  With any gap junction the exchange interval becomes one
+ * step.  Call before the first cn_run.  Errors: CN_EINVAL (range, g < 0),
+ * CN_ESTATE.                                                              */
+cn_status cn_add_gaps(cn_model* m, int64_t n, const int32_t* node, const int32_t* peer, const double* g_uS);
+
 /* Record the voltage of a node (global index) at every step; *rec_id is the
  * handle for cn_get_trace.  Before the first cn_run only.                  */
 cn_status cn_record(cn_model* m, int32_t node, int32_t* rec_id);

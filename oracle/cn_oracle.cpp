@@ -36,6 +36,9 @@
 //    when |u| < 1e-6.  q10 = 1, rates evaluated directly (no tables).
 //  * initial state: v = v_init, gates at their steady state at v_init,
 //    synaptic g = 0, cai = cainf.
+//  * a half gap junction at node i with peer j injects g (v_j,k - v_i) with
+//    v_i implicit and the peer voltage of the start of the step (voltages are
+//    exchanged every step; the minimum-delay interval becomes one step).
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -90,6 +93,10 @@ struct or_scenario {
   const double* stim_amp;      // nA
   int32_t n_rec;
   const int32_t* rec_node;
+  int64_t n_gap;               // half gap junctions (one entry per side)
+  const int32_t* gap_node;     // global node carrying the half gap
+  const int32_t* gap_peer;     // global node of the other side
+  const double* gap_g;         // uS
 };
 
 }  // extern "C"
@@ -167,6 +174,11 @@ struct Model {
   std::vector<int32_t> st_node;
   std::vector<double> st_del, st_dur, st_amp;
   std::vector<std::vector<int32_t>> cell_stims;
+  // gap junctions: per half gap its node, peer node and g; the peer voltage of
+  // the current step is copied into gap_vpeer before any cell advances
+  std::vector<int32_t> gap_node, gap_peer;
+  std::vector<double> gap_g, gap_vpeer;
+  std::vector<std::vector<int32_t>> cell_gaps;
   // network
   std::vector<int64_t> nc_start;     // CSR by source gid, NetCon index order
   std::vector<int64_t> nc_idx;
@@ -311,6 +323,19 @@ bool build(Model& M, const or_scenario* s) {
   M.st_amp.assign(s->stim_amp, s->stim_amp + s->n_stim);
   M.cell_stims.assign(M.n_cells, {});
   for (int i = 0; i < s->n_stim; ++i) M.cell_stims[cell_of[M.st_node[i]]].push_back(i);
+  // Gap junctions.
+  M.gap_node.assign(s->gap_node, s->gap_node + s->n_gap);
+  M.gap_peer.assign(s->gap_peer, s->gap_peer + s->n_gap);
+  M.gap_g.assign(s->gap_g, s->gap_g + s->n_gap);
+  M.gap_vpeer.assign(s->n_gap, 0.0);
+  M.cell_gaps.assign(M.n_cells, {});
+  for (int64_t i = 0; i < s->n_gap; ++i) {
+    if (M.gap_node[i] < 0 || M.gap_node[i] >= N || M.gap_peer[i] < 0 || M.gap_peer[i] >= N) {
+      M.err = "bad gap junction";
+      return false;
+    }
+    M.cell_gaps[cell_of[M.gap_node[i]]].push_back((int32_t)i);
+  }
   // NetCons: CSR by source in index order.
   M.nc_start.assign(M.n_cells + 1, 0);
   for (int64_t j = 0; j < s->n_netcon; ++j) {
@@ -420,6 +445,14 @@ void cell_step(Model& M, int c, int64_t k, std::vector<std::pair<int64_t, int32_
       M.d[nd] += G;
     }
   }
+  // Gap junctions: I = g (v - v_peer,k), the peer voltage taken at the start
+  // of the step (exchanged every step), the own voltage implicit.
+  for (int gi : M.cell_gaps[c]) {
+    int nd = M.gap_node[gi];
+    double G = 100.0 * M.gap_g[gi] / M.area[nd];
+    M.rhs[nd] -= G * (M.v[nd] - M.gap_vpeer[gi]);
+    M.d[nd] += G;
+  }
   const double tmid = (k + 0.5) * dt;
   for (int si : M.cell_stims[c]) {
     if (M.st_del[si] <= tmid && tmid < M.st_del[si] + M.st_dur[si]) {
@@ -526,6 +559,7 @@ void exchange(Model& M, std::vector<std::pair<int64_t, int32_t>>& spikes) {
 
 void run(Model& M, int64_t nsteps, int nthreads) {
   int64_t D = M.min_delay > 0 ? M.min_delay : 40;
+  if (!M.gap_node.empty()) D = 1;  // gap junctions exchange voltages every step
   int64_t end = M.step + nsteps;
   if (nthreads < 1) nthreads = 1;
   if (nthreads > M.n_cells) nthreads = std::max(1, M.n_cells);
@@ -534,6 +568,7 @@ void run(Model& M, int64_t nsteps, int nthreads) {
     // the cells are independent (every NetCon delay is at least D steps).
     int64_t stop = std::min(end, (M.step / D + 1) * D);
     int64_t k0 = M.step;
+    for (size_t i = 0; i < M.gap_peer.size(); ++i) M.gap_vpeer[i] = M.v[M.gap_peer[i]];
     for (auto& tr : M.trace) tr.resize(stop + 1);
     std::vector<std::vector<std::pair<int64_t, int32_t>>> sp(nthreads);
     auto work = [&](int tid) {

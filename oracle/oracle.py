@@ -39,6 +39,7 @@ class _Scenario(C.Structure):
         ("n_stim", C.c_int32), ("stim_node", _P_I32), ("stim_del", _P_F64), ("stim_dur", _P_F64),
         ("stim_amp", _P_F64),
         ("n_rec", C.c_int32), ("rec_node", _P_I32),
+        ("n_gap", C.c_int64), ("gap_node", _P_I32), ("gap_peer", _P_I32), ("gap_g", _P_F64),
     ]
 
 
@@ -133,6 +134,8 @@ def _marshal(sc, keep):
     s.stim_node, s.stim_del, s.stim_dur, s.stim_amp = (i32(sc.stim_node), f64(sc.stim_del),
                                                        f64(sc.stim_dur), f64(sc.stim_amp))
     s.n_rec, s.rec_node = len(sc.rec_node), i32(sc.rec_node)
+    s.n_gap = len(sc.gap_node)
+    s.gap_node, s.gap_peer, s.gap_g = i32(sc.gap_node), i32(sc.gap_peer), f64(sc.gap_g)
     return s
 
 
@@ -164,38 +167,7 @@ class OracleModel:
     def __init__(self, sc):
         L = lib()
         keep = []
-
-        def i32(x):
-            a = np.ascontiguousarray(x, np.int32)
-            keep.append(a)
-            return _p(a, _P_I32)
-
-        def f64(x):
-            a = np.ascontiguousarray(x, np.float64)
-            keep.append(a)
-            return _p(a, _P_F64)
-
-        mechs = (_MechIn * max(1, len(sc.mechs)))()
-        for t, m in enumerate(sc.mechs):
-            mechs[t].kind = KIND[m.kind]
-            mechs[t].n = m.n
-            mechs[t].node = i32(m.node)
-            mechs[t].param = f64(m.param_matrix().reshape(-1))
-        s = _Scenario()
-        s.dt, s.v_init, s.n_cells = sc.dt, sc.v_init, sc.n_cells
-        s.cell_offset, s.parent = i32(sc.cell_offset), i32(sc.parent)
-        s.dx, s.diam, s.Ra, s.cm = f64(sc.dx), f64(sc.diam), f64(sc.Ra), f64(sc.cm)
-        s.spike_node, s.threshold = i32(sc.spike_node), f64(sc.threshold)
-        s.n_mech, s.mechs = len(sc.mechs), mechs
-        s.n_netcon = len(sc.netcon_src)
-        s.nc_src, s.nc_syn, s.nc_w, s.nc_delay = (i32(sc.netcon_src), i32(sc.netcon_syn),
-                                                  f64(sc.netcon_w), f64(sc.netcon_delay))
-        s.n_ev = len(sc.ev_syn)
-        s.ev_syn, s.ev_t, s.ev_w = i32(sc.ev_syn), f64(sc.ev_t), f64(sc.ev_w)
-        s.n_stim = len(sc.stim_node)
-        s.stim_node, s.stim_del, s.stim_dur, s.stim_amp = (i32(sc.stim_node), f64(sc.stim_del),
-                                                           f64(sc.stim_dur), f64(sc.stim_amp))
-        s.n_rec, s.rec_node = len(sc.rec_node), i32(sc.rec_node)
+        s = _marshal(sc, keep)
         err = C.create_string_buffer(512)
         h = L.or_create(C.byref(s), err, 512)
         if not h:

@@ -79,6 +79,8 @@ def lib():
         L.cn_checkpoint_save.restype = st
         L.cn_checkpoint_load.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t]
         L.cn_checkpoint_load.restype = st
+        L.cn_add_gaps.argtypes = [C.c_void_p, C.c_int64, _P_I32, _P_I32, _P_F64]
+        L.cn_add_gaps.restype = st
         L.cn_model_create.argtypes = [C.POINTER(cn_morph), C.POINTER(cn_mech_table), C.c_int32,
                                       C.POINTER(cn_options), C.POINTER(C.c_void_p)]
         L.cn_model_create.restype = st
@@ -299,6 +301,11 @@ class Model:
     def cn_add_stim(self, node, delay, dur, amp):
         _check(lib().cn_add_stim(self._h, int(node), float(delay), float(dur), float(amp)), self._h)
 
+    def cn_add_gaps(self, node, peer, g_uS):
+        node, peer, g = _i32(node), _i32(peer), _f64(g_uS)
+        _check(lib().cn_add_gaps(self._h, node.shape[0], _p(node, _P_I32), _p(peer, _P_I32), _p(g, _P_F64)),
+               self._h)
+
     def cn_record(self, node) -> int:
         rid = C.c_int32()
         _check(lib().cn_record(self._h, int(node), C.byref(rid)), self._h)
@@ -416,6 +423,9 @@ def from_scenario(sc, precision="fp64", device=0, stream=None, record=True, torc
         md.cn_add_events(sc.ev_syn, sc.ev_t, sc.ev_w)
     for i in range(len(sc.stim_node)):
         md.cn_add_stim(sc.stim_node[i], sc.stim_del[i], sc.stim_dur[i], sc.stim_amp[i])
+    gap_node = getattr(sc, "gap_node", ())
+    if len(gap_node):
+        md.cn_add_gaps(gap_node, sc.gap_peer, sc.gap_g)
     if record:
         for node in sc.rec_node:
             md.cn_record(int(node))

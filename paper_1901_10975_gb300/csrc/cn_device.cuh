@@ -85,6 +85,10 @@ struct DevModel {
   const int32_t* g_hh_rows;
   const int64_t* g_st_base;
   const int32_t* g_st_rows;
+  const int64_t* g_gap_base;   // half gap junctions of the lane
+  const int32_t* g_gap_rows;
+  const int64_t* g_gsrc_base;  // gap peer nodes whose voltage the lane publishes
+  const int32_t* g_gsrc_rows;
   const int64_t* g_rec_base;
   const int32_t* g_rec_rows;
   // per slot (group * 32 + lane)
@@ -93,6 +97,8 @@ struct DevModel {
   const int32_t* s_nsyn;
   const int32_t* s_nhh;
   const int32_t* s_nst;
+  const int32_t* s_ngap;
+  const int32_t* s_ngsrc;
   const int32_t* s_nrec;
   const int32_t* s_gid;
   const int32_t* s_spike_row;
@@ -147,6 +153,14 @@ struct DevModel {
   int64_t traj_k0;
   // stimuli
   const int32_t* st_slot;
+  // gap junctions: slot of the row, index of the peer voltage, 100 g/(area cdt)
+  const int32_t* gap_slot;
+  const int32_t* gap_src;
+  double* gap_gs;
+  const int32_t* gsrc_row;     // published voltages: row in the lane, index
+  const int32_t* gsrc_id;
+  double* vgap;                // [2][n_gsrc]: peer voltages of even / odd steps
+  int32_t n_gsrc;
   const double* st_del;
   const double* st_dur;
   const double* st_amp;     // 100 amp / (area cdt)
@@ -188,10 +202,16 @@ __host__ __device__ inline size_t ring_bytes(bool dense) {
   const size_t back = (size_t)kBackRows * kLanes * (2 * sizeof(double) + sizeof(int32_t));
   return ((elim > back ? elim : back) + 15) / 16 * 16;
 }
-__host__ __device__ inline size_t interval_smem_bytes(int stack_depth, int max_slots, bool dense, int n_mail) {
+// Dynamic shared memory of one warp of the interval kernel: row rings, far
+// stack (+1 zero entry), slot buffer, channel reversal potentials and gate
+// kinetics (gate_bytes: 8 for FP64 gating, else 4), mailbox.
+__host__ __device__ inline size_t interval_smem_bytes(int stack_depth, int max_slots, bool dense, int n_mail,
+                                                      int gate_bytes) {
   return ring_bytes(dense) + (size_t)(stack_depth + 1) * kLanes * 3 * sizeof(double) +
          (size_t)max_slots * kLanes * 2 * sizeof(double) +
-         (dense ? (size_t)kChanParams * kLanes * (sizeof(double) + sizeof(float)) : 0) +
+         (dense ? (size_t)kChanTypes * kLanes * sizeof(double) +
+                      (size_t)kChanParams * kLanes * (gate_bytes == 8 ? sizeof(double) : sizeof(float))
+                : 0) +
          (size_t)n_mail * 4 * sizeof(double);
 }
 

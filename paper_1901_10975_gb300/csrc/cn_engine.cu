@@ -61,6 +61,8 @@ struct cn_model {
   std::vector<int32_t> st_node;
   std::vector<double> st_del, st_dur, st_amp;
   std::vector<int32_t> rec_node;
+  std::vector<int32_t> gap_node, gap_peer;  // half gap junctions (global nodes)
+  std::vector<double> gap_g;                // uS
   std::vector<int32_t> node_cell;
   std::vector<int32_t> node_row;   // global node -> warp row of its lane
   std::vector<int32_t> node_slot;  // global node -> lane (slot) holding it
@@ -220,6 +222,15 @@ cn_status launch_checked(cn_model* m, F&& f) {
   return CN_OK;
 }
 
+// Gap peer voltages of the current step into the buffer that step reads.
+cn_status gap_publish(cn_model* m) {
+  if (m->dm.n_gsrc == 0) return CN_OK;
+  const int tb = 128, nb = (m->n_slots + tb - 1) / tb;
+  cn::DevModel dm = m->dm;
+  const int parity = (int)(m->step & 1);
+  return launch_checked(m, [&] { cn::k_gap_publish<<<nb, tb, 0, m->stream>>>(dm, parity); });
+}
+
 cn_status state_init(cn_model* m) {
   const int tb = 128, nb = (m->n_slots + tb - 1) / tb;
   cn::DevModel dm = m->dm;
@@ -229,16 +240,21 @@ cn_status state_init(cn_model* m) {
     case CN_PREC_FP64:
       CN_CHECK(launch_checked(m, [&] { cn::k_state_init<0><<<nb, tb, 0, st>>>(dm, v0); }));
       if (m->dense) CN_CHECK(launch_checked(m, [&] { cn::k_setup_dense<0><<<nb, tb, 0, st>>>(dm, v0, false); }));
-      return CN_OK;
+      break;
     case CN_PREC_GATE_FP32:
       CN_CHECK(launch_checked(m, [&] { cn::k_state_init<1><<<nb, tb, 0, st>>>(dm, v0); }));
       if (m->dense) CN_CHECK(launch_checked(m, [&] { cn::k_setup_dense<1><<<nb, tb, 0, st>>>(dm, v0, false); }));
-      return CN_OK;
+      break;
     default:
       CN_CHECK(launch_checked(m, [&] { cn::k_state_init<2><<<nb, tb, 0, st>>>(dm, v0); }));
       if (m->dense) CN_CHECK(launch_checked(m, [&] { cn::k_setup_dense<2><<<nb, tb, 0, st>>>(dm, v0, false); }));
-      return CN_OK;
+      break;
   }
+  const int64_t step = m->step;
+  m->step = 0;  // state_init always describes step 0
+  const cn_status r = gap_publish(m);
+  m->step = step;
+  return r;
 }
 
 // Split plan and row order of one cell.  The cell (local nodes 0..n-1,
@@ -723,6 +739,7 @@ cn_status finalize(cn_model* m) {
     if (dmin == 0 || ds < dmin) dmin = ds;
   }
   m->D = (int32_t)(dmin == 0 ? cn::kMaxInterval : std::min<int64_t>(dmin, cn::kMaxInterval));
+  if (!m->gap_node.empty()) m->D = 1;  // gap junctions exchange voltages every step
 
   // dense channel types: per-cell presence mask and per-cell kinetics (every
   // column after gbar must be uniform within a cell for this mapping)
@@ -811,10 +828,26 @@ cn_status finalize(cn_model* m) {
   std::vector<int32_t> hh_slotid(m->hh_node.size()), st_slotid(m->st_node.size());
   for (size_t i = 0; i < m->hh_node.size(); ++i) hh_slotid[i] = slot_of_node(m->hh_node[i]);
   for (size_t i = 0; i < m->st_node.size(); ++i) st_slotid[i] = slot_of_node(m->st_node[i]);
+  std::vector<int32_t> gap_slotid(m->gap_node.size());
+  for (size_t i = 0; i < m->gap_node.size(); ++i) gap_slotid[i] = slot_of_node(m->gap_node[i]);
+  // distinct gap peers: each is published by the lane that holds it
+  std::vector<int32_t> gsrc_node, gap_src(m->gap_node.size());
+  {
+    std::vector<int32_t> id(m->n_nodes, -1);
+    for (size_t i = 0; i < m->gap_peer.size(); ++i) {
+      int32_t& x = id[m->gap_peer[i]];
+      if (x < 0) {
+        x = (int32_t)gsrc_node.size();
+        gsrc_node.push_back(m->gap_peer[i]);
+      }
+      gap_src[i] = x;
+    }
+  }
   int max_slots = 1;
   for (int sl = 0; sl < m->n_slots; ++sl) max_slots = std::max<int>(max_slots, (int)lane_slot_rows[sl].size());
   if (max_slots >= cn::kNoSlot) return m->fail(CN_EINVAL, "too many mechanism rows in one cell part");
-  const size_t smem = cn::interval_smem_bytes(depth, max_slots, m->dense, L.n_mail);
+  const size_t smem = cn::interval_smem_bytes(depth, max_slots, m->dense, L.n_mail,
+                                              m->opt.precision == CN_PREC_FP64 ? 8 : 4);
   if (smem > kMaxSmemPerBlock)
     return m->fail(CN_EINVAL, "cell needs " + std::to_string(smem) + " bytes of shared memory (slots " +
                                   std::to_string(max_slots) + ", stack " + std::to_string(depth) + ")");
@@ -852,6 +885,24 @@ cn_status finalize(cn_model* m) {
   // synapses, HH, stimuli, records
   Rows rs = interleave(m, m->syn_node, true), rh = interleave(m, m->hh_node), rt = interleave(m, m->st_node),
        rr = interleave(m, m->rec_node);
+  Rows rg = interleave(m, m->gap_node), rgs = interleave(m, gsrc_node);
+  std::vector<int32_t> h_gap_slot(std::max<int64_t>(rg.elems, 1), 0), h_gap_src(std::max<int64_t>(rg.elems, 1), 0);
+  std::vector<double> h_gap_area(std::max<int64_t>(rg.elems, 1), 1.0), h_gap_cm(std::max<int64_t>(rg.elems, 1), 1.0),
+      h_gap_g(std::max<int64_t>(rg.elems, 1), 0.0);
+  for (size_t i = 0; i < m->gap_node.size(); ++i) {
+    const int64_t e = elem_of(rg, i);
+    h_gap_slot[e] = gap_slotid[i];
+    h_gap_src[e] = gap_src[i];
+    h_gap_area[e] = m->area[m->gap_node[i]];
+    h_gap_cm[e] = m->cm[m->gap_node[i]];
+    h_gap_g[e] = m->gap_g[i];
+  }
+  std::vector<int32_t> h_gsrc_row(std::max<int64_t>(rgs.elems, 1), 0), h_gsrc_id(std::max<int64_t>(rgs.elems, 1), 0);
+  for (size_t i = 0; i < gsrc_node.size(); ++i) {
+    const int64_t e = elem_of(rgs, i);
+    h_gsrc_row[e] = m->node_row[gsrc_node[i]];
+    h_gsrc_id[e] = (int32_t)i;
+  }
   m->syn_slot = rs.inst_slot; m->syn_q = rs.inst_q;
   m->syn_elem.resize(m->syn_node.size());
   for (size_t i = 0; i < m->syn_node.size(); ++i) m->syn_elem[i] = elem_of(rs, i);
@@ -983,6 +1034,19 @@ cn_status finalize(cn_model* m) {
   CN_CHECK(upload(m, &p32, rs.slot_n)); dm.s_nsyn = p32;
   CN_CHECK(upload(m, &p32, rh.slot_n)); dm.s_nhh = p32;
   CN_CHECK(upload(m, &p32, rt.slot_n)); dm.s_nst = p32;
+  CN_CHECK(upload(m, &p64, rg.g_base)); dm.g_gap_base = p64;
+  CN_CHECK(upload(m, &p32, rg.g_rows)); dm.g_gap_rows = p32;
+  CN_CHECK(upload(m, &p32, rg.slot_n)); dm.s_ngap = p32;
+  CN_CHECK(upload(m, &p64, rgs.g_base)); dm.g_gsrc_base = p64;
+  CN_CHECK(upload(m, &p32, rgs.g_rows)); dm.g_gsrc_rows = p32;
+  CN_CHECK(upload(m, &p32, rgs.slot_n)); dm.s_ngsrc = p32;
+  CN_CHECK(upload(m, &p32, h_gap_slot)); dm.gap_slot = p32;
+  CN_CHECK(upload(m, &p32, h_gap_src)); dm.gap_src = p32;
+  CN_CHECK(zeros(m, &pd, h_gap_g.size())); dm.gap_gs = pd;
+  CN_CHECK(upload(m, &p32, h_gsrc_row)); dm.gsrc_row = p32;
+  CN_CHECK(upload(m, &p32, h_gsrc_id)); dm.gsrc_id = p32;
+  CN_CHECK(zeros(m, &pd, 2 * std::max<size_t>(gsrc_node.size(), 1))); dm.vgap = pd;
+  dm.n_gsrc = (int32_t)gsrc_node.size();
   CN_CHECK(upload(m, &p32, rr.slot_n)); dm.s_nrec = p32;
   CN_CHECK(upload(m, &p32, slot_gid)); dm.s_gid = p32;
   CN_CHECK(upload(m, &p32, slot_spike)); dm.s_spike_row = p32;
@@ -1107,6 +1171,16 @@ cn_status finalize(cn_model* m) {
   CN_CHECK(launch_checked(m, [&] { cn::k_setup_syn<<<nb, tb, 0, st>>>(dm, d_syn_area, d_syn_cm, d_syn_tau); }));
   CN_CHECK(launch_checked(m, [&] { cn::k_hh_params<<<nb, tb, 0, st>>>(dm); }));
   CN_CHECK(launch_checked(m, [&] { cn::k_setup_stim<<<nb, tb, 0, st>>>(dm, d_st_amp, d_st_area, d_st_cm); }));
+  if (rg.elems > 0) {
+    double *d_ga, *d_gc, *d_gg;
+    CN_CHECK(upload(m, &d_ga, h_gap_area));
+    CN_CHECK(upload(m, &d_gc, h_gap_cm));
+    CN_CHECK(upload(m, &d_gg, h_gap_g));
+    const int64_t ng = rg.elems;
+    CN_CHECK(launch_checked(m, [&] { cn::k_setup_gap<<<(unsigned)((ng + 255) / 256), 256, 0, st>>>(dm, d_ga, d_gc, d_gg, ng); }));
+    CN_TRY_CUDA(m, cudaStreamSynchronize(st));
+    for (double* q : {d_ga, d_gc, d_gg}) dfree_raw(m, q);
+  }
   if (m->dense) {
     const double v0 = m->opt.v_init_mV;
     switch (m->opt.precision) {
@@ -1503,6 +1577,9 @@ uint64_t network_fingerprint(const cn_model* m) {
   h = fnv_vec(h, m->nc_syn);
   h = fnv_vec(h, m->nc_delay);
   h = fnv_vec(h, m->nc_w);
+  h = fnv_vec(h, m->gap_node);
+  h = fnv_vec(h, m->gap_peer);
+  h = fnv_vec(h, m->gap_g);
   h = fnv(h, &m->opt.dt_ms, sizeof(double));
   return h;
 }
@@ -1816,6 +1893,20 @@ cn_status cn_add_stim(cn_model* m, int32_t node, double del, double dur, double 
   m->st_del.push_back(del);
   m->st_dur.push_back(dur);
   m->st_amp.push_back(amp);
+  return CN_OK;
+}
+
+cn_status cn_add_gaps(cn_model* m, int64_t n, const int32_t* node, const int32_t* peer, const double* g_uS) {
+  CN_CHECK(state_check(m));
+  if (n < 0 || (n > 0 && (!node || !peer || !g_uS))) return m->fail(CN_EINVAL, "bad gap junction arrays");
+  for (int64_t i = 0; i < n; ++i) {
+    if (node[i] < 0 || node[i] >= m->n_nodes || peer[i] < 0 || peer[i] >= m->n_nodes)
+      return m->fail(CN_EINVAL, "gap junction node out of range");
+    if (!std::isfinite(g_uS[i]) || g_uS[i] < 0) return m->fail(CN_EINVAL, "bad gap junction conductance");
+  }
+  m->gap_node.insert(m->gap_node.end(), node, node + n);
+  m->gap_peer.insert(m->gap_peer.end(), peer, peer + n);
+  m->gap_g.insert(m->gap_g.end(), g_uS, g_uS + n);
   return CN_OK;
 }
 
@@ -2225,6 +2316,7 @@ cn_status cn_checkpoint_load(cn_model* m, const void* buf, size_t n) {
   }
   m->step = hd.step;
   m->raster_from = hd.step;
+  CN_CHECK(gap_publish(m));
   if (m->dm.trace) {
     const int tb = 128, nb = (m->n_slots + tb - 1) / tb;
     cn::DevModel dm = m->dm;
@@ -2239,8 +2331,8 @@ cn_status cn_enable_adjoint(cn_model* m, int32_t checkpoint_steps) {
   if (!m || checkpoint_steps < 1) return m ? m->fail(CN_EINVAL, "checkpoint interval must be >= 1 step") : CN_EINVAL;
   if (m->step != 0) return m->fail(CN_ESTATE, "enable the adjoint at step 0");
   if (m->opt.precision != CN_PREC_FP64) return m->fail(CN_ESTATE, "the adjoint is defined for the FP64 path");
-  if (!m->nc_src.empty() || !m->ev_syn.empty())
-    return m->fail(CN_ESTATE, "the adjoint needs a model without NetCons or external events");
+  if (!m->nc_src.empty() || !m->ev_syn.empty() || !m->gap_node.empty())
+    return m->fail(CN_ESTATE, "the adjoint needs a model without NetCons, external events or gap junctions");
   if (m->dense) return m->fail(CN_ESTATE, "the adjoint covers HH, pas and IClamp models");
   std::vector<int> nh(m->n_cells, 0);
   for (int32_t node : m->hh_node)

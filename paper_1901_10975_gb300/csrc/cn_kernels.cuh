@@ -160,6 +160,25 @@ __global__ void k_setup_stim(DevModel M, const double* amp, const double* node_a
   }
 }
 
+// Half gap junction constants: gs = 100 g / (area cdt) of the junction's row.
+__global__ void k_setup_gap(DevModel M, const double* area, const double* cm, const double* g_uS, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) M.gap_gs[i] = 100.0 * g_uS[i] / (area[i] * (1e-3 * cm[i] / M.dt));
+}
+
+// Publishes every gap peer voltage of the current step into vgap[parity].
+__global__ void k_gap_publish(DevModel M, int parity) {
+  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot >= M.n_slots) return;
+  const int g = slot / kLanes, lane = slot % kLanes;
+  const int n = M.s_ngsrc[slot];
+  const int64_t sb = M.g_gsrc_base[g] + lane, nb = M.g_node_base[g] + lane;
+  for (int q = 0; q < n; ++q) {
+    const int64_t i = sb + (int64_t)q * kLanes;
+    M.vgap[(int64_t)parity * M.n_gsrc + M.gsrc_id[i]] = M.v[nb + (int64_t)M.gsrc_row[i] * kLanes];
+  }
+}
+
 // ------------------------------------------------------- interval boundary
 // Spike exchange at the start of interval J (Section 2: spikes are exchanged
 // once per minimum delay).  Each cell pulls, from the spike masks of earlier
@@ -329,7 +348,7 @@ __device__ __forceinline__ void dense_load(const DevModel& M, int mask, int64_t 
 }
 
 template <int PREC>
-__device__ __forceinline__ void dense_step(const DevModel& M, int mask, int64_t e, double vnew, const double* kin,
+__device__ __forceinline__ void dense_step(const DevModel& M, int mask, int64_t e, double vnew, const double* erev,
                                            const typename GateT<PREC>::M* kinT, const ChanIn<PREC>& in) {
   using S = typename GateT<PREC>::S;
   using T = typename GateT<PREC>::M;
@@ -348,32 +367,31 @@ __device__ __forceinline__ void dense_step(const DevModel& M, int mask, int64_t 
     const T h = upd(1, kinT + (chan_kin0(0) + 7) * kLanes);
     const double c = in.gb[0] * (double)(m * m * m * h);
     g += c;
-    ge = fma(c, kin[chan_kin0(0) * kLanes], ge);
+    ge = fma(c, erev[0 * kLanes], ge);
   }
   if (mask & 2) {  // KDR4: n^4
     const T n = upd(2, kinT + (chan_kin0(1) + 1) * kLanes);
     const double c = in.gb[1] * (double)((n * n) * (n * n));
     g += c;
-    ge = fma(c, kin[chan_kin0(1) * kLanes], ge);
+    ge = fma(c, erev[1 * kLanes], ge);
   }
   if (mask & 4) {  // KA: a^3 b
     const T a = upd(3, kinT + (chan_kin0(2) + 1) * kLanes);
     const T b = upd(4, kinT + (chan_kin0(2) + 7) * kLanes);
     const double c = in.gb[2] * (double)(a * a * a * b);
     g += c;
-    ge = fma(c, kin[chan_kin0(2) * kLanes], ge);
+    ge = fma(c, erev[2 * kLanes], ge);
   }
   if (mask & 8) {  // IH: q
     const T q = upd(5, kinT + (chan_kin0(3) + 1) * kLanes);
     const double c = in.gb[3] * (double)q;
     g += c;
-    ge = fma(c, kin[chan_kin0(3) * kLanes], ge);
+    ge = fma(c, erev[3 * kLanes], ge);
   }
   double cai1 = in.cai;
   if (mask & 16) {  // CAHVA: m^2 h, [Ca]i from the current of step k
     const T m = upd(6, kinT + (chan_kin0(4) + 1) * kLanes);
     const T h = upd(7, kinT + (chan_kin0(4) + 7) * kLanes);
-    const double* kc = kin + chan_kin0(4) * kLanes;
     const T* kct = kinT + chan_kin0(4) * kLanes;
     const T depth = kct[13 * kLanes], taur = kct[14 * kLanes], cainf = kct[15 * kLanes];
     T drive = T(-1e4) * (T)in.ica / (T(2.0 * 96485.3321) * depth);
@@ -382,13 +400,12 @@ __device__ __forceinline__ void dense_step(const DevModel& M, int mask, int64_t 
     cai1 = (double)(cai + (T(1) - dexp_(-tdt / taur)) * (cainf + drive * taur - cai));
     M.cai[e] = cai1;
     const double c = in.gb[4] * (double)(m * m * h);
-    const double eca = kc[0];
+    const double eca = erev[4 * kLanes];
     g += c;
     ge = fma(c, eca, ge);
     M.ica[e] = c * M.cdt[e] * (vnew - eca);
   }
   if (mask & 32) {  // KCA: c, activated by the new [Ca]i
-    const double* kk = kin + chan_kin0(5) * kLanes;
     const T* kkt = kinT + chan_kin0(5) * kLanes;
     const T cai = (T)cai1;
     const T al = kkt[1 * kLanes] * cai / (cai + kkt[2 * kLanes]);
@@ -396,7 +413,7 @@ __device__ __forceinline__ void dense_step(const DevModel& M, int mask, int64_t 
     const T xk = g_store_ret(p, cnexp_step<T>(in.x[8], al, kkt[3 * kLanes], tdt));
     const double c = in.gb[5] * (double)xk;
     g += c;
-    ge = fma(c, kk[0], ge);
+    ge = fma(c, erev[5 * kLanes], ge);
   }
   M.ch_g[e] = g;
   M.ch_ge[e] = ge;
@@ -527,22 +544,23 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, DENSE ? 2 : 4)
   double* const st_y = st_x + (DS + 1) * kLanes;
   double* const sl_ge = st_y + (DS + 1) * kLanes;  // slot buffer [max_slots][32]
   double* const sl_d = sl_ge + M.max_slots * kLanes;
-  double* const kin = sl_d + M.max_slots * kLanes;  // dense kinetics [kChanParams][32]
+  // channel types: reversal potentials [6][32] (FP64) and the gate kinetics
+  // [kChanParams][32] in the gate arithmetic's type
+  double* const erev = sl_d + M.max_slots * kLanes;
+  unsigned char* const kin_base = reinterpret_cast<unsigned char*>(
+      wsm + (3 * (DS + 1) + 2 * M.max_slots + (DENSE ? kChanTypes : 0)) * kLanes);
+  T* const kinT = reinterpret_cast<T*>(kin_base) + lane;
   // mailbox [n_mail][4] shared by the warp: a part root leaves (-a, x, b/d)
   // for its junction row, the junction row leaves v for the part root
-  double* const mail = wsm + (3 * (DS + 1) + 2 * M.max_slots + (DENSE ? kChanParams : 0)) * kLanes;
+  double* const mail = reinterpret_cast<double*>(kin_base + (DENSE ? kChanParams * kLanes * sizeof(T) : 0));
   st_a[DS * kLanes] = 0.0;
   st_x[DS * kLanes] = 0.0;
   st_y[DS * kLanes] = 0.0;
   const int chmask = DENSE ? M.g_chmask[g] : 0;
-  // gate kinetics in the gate arithmetic's type (after the mailbox); FP64 uses kin itself
-  T* const kinT = (DENSE && PREC != 0) ? reinterpret_cast<T*>(mail + 4 * M.n_mail) + lane
-                                       : reinterpret_cast<T*>(kin);
-  if (DENSE)
-    for (int q = 0; q < kChanParams; ++q) {
-      kin[q * kLanes] = M.ch_kin[(int64_t)q * M.n_slots + slot];
-      if (PREC != 0) kinT[q * kLanes] = (T)kin[q * kLanes];
-    }
+  if (DENSE) {
+    for (int q = 0; q < kChanParams; ++q) kinT[q * kLanes] = (T)M.ch_kin[(int64_t)q * M.n_slots + slot];
+    for (int t = 0; t < kChanTypes; ++t) erev[t * kLanes] = M.ch_kin[(int64_t)chan_kin0(t) * M.n_slots + slot];
+  }
 
   // this lane's column of every per-row array
   double* const gv = M.v + nb;
@@ -554,13 +572,16 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, DENSE ? 2 : 4)
   const int32_t* const gfl = M.flags + nb;
 
   const int SLR = M.g_slot_rows[g], nslot = M.s_nslot[slot];
-  const int64_t slb = M.g_slot_base[g] + lane;
   const int nsyn = M.s_nsyn[slot];
   const int64_t sb = M.g_syn_base[g] + lane;
   const int HR = M.g_hh_rows[g], nhh = M.s_nhh[slot];
   const int64_t hb = M.g_hh_base[g] + lane;
   const int STR = M.g_st_rows[g], nst = M.s_nst[slot];
   const int64_t stb = M.g_st_base[g] + lane;
+  const int GR = M.g_gap_rows[g], ngap = M.s_ngap[slot];
+  const int64_t gpb = M.g_gap_base[g] + lane;
+  const int GSR = M.g_gsrc_rows[g], ngsrc = M.s_ngsrc[slot];
+  const int64_t gsb = M.g_gsrc_base[g] + lane;
   const int RR = M.g_rec_rows[g], nrec = M.s_nrec[slot];
   const int64_t rcb = M.g_rec_base[g] + lane;
   const double dt = M.dt;
@@ -685,6 +706,16 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, DENSE ? 2 : 4)
         sl_d[t] += gna + gk + gl;
       }
     }
+    // gap junctions: g (v_peer,k - v) with the peers' voltages of step k
+    for (int q = 0; q < GR; ++q) {
+      if (q < ngap) {
+        const int64_t i = gpb + (int64_t)q * kLanes;
+        const double gs = M.gap_gs[i];
+        const int t = M.gap_slot[i] * kLanes;
+        sl_ge[t] = fma(gs, M.vgap[(k & 1) * M.n_gsrc + M.gap_src[i]], sl_ge[t]);
+        sl_d[t] += gs;
+      }
+    }
     if (STR > 0) {
       const double tmid = ((double)k + 0.5) * dt;
       for (int q = 0; q < STR; ++q) {
@@ -780,7 +811,6 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, DENSE ? 2 : 4)
         fetch_elim(j - kElimRows, u);
       }
     }
-    const double x0 = x;  // row 0 is eliminated last
     cp_async_wait<0>();
     // back substitution, root to leaves (row 0: b = 0, so v_0 = x_0)
 #pragma unroll
@@ -841,7 +871,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, DENSE ? 2 : 4)
         }
 #pragma unroll
         for (int u = 0; u < kChanBatch; ++u)
-          if (fr[u]) dense_step<PREC>(M, chmask, nb + (int64_t)(j0 + u) * kLanes, vv[u], kin, kinT, in[u]);
+          if (fr[u]) dense_step<PREC>(M, chmask, nb + (int64_t)(j0 + u) * kLanes, vv[u], erev, kinT, in[u]);
       }
     }
     // (4) nrn_state: HH gates (cnexp) at v_{k+1}
@@ -849,7 +879,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, DENSE ? 2 : 4)
       if (q < nhh) {
         const int64_t i = hb + (int64_t)q * kLanes;
         const int row = M.hh_row[i];
-        const T vv = (T)(row == 0 ? x0 : M.v[nb + (int64_t)row * kLanes]);
+        const T vv = (T)M.v[nb + (int64_t)row * kLanes];
         T am, bm, ah, bh, an, bn;
         hh_rates<T>(vv, am, bm, ah, bh, an, bn);
         const T tdt = (T)dt;
@@ -864,9 +894,18 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, DENSE ? 2 : 4)
         }
       }
     }
+    // publish this lane's gap peer voltages of step k+1 (the other buffer:
+    // lanes of other warps may still read the step-k values)
+    for (int q = 0; q < GSR; ++q) {
+      if (q < ngsrc) {
+        const int64_t i = gsb + (int64_t)q * kLanes;
+        const int row = M.gsrc_row[i];
+        M.vgap[((k + 1) & 1) * M.n_gsrc + M.gsrc_id[i]] = M.v[nb + (int64_t)row * kLanes];
+      }
+    }
     // (5) threshold detection and recording
     if (!TRAJ && N > 0) {
-      const double vs = spike_row == 0 ? x0 : M.v[nb + (int64_t)spike_row * kLanes];
+      const double vs = M.v[nb + (int64_t)spike_row * kLanes];
       const int now = vs > thresh;
       if (now && !above) mask |= 1ull << s;
       above = now;
@@ -874,7 +913,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, DENSE ? 2 : 4)
         if (q < nrec) {
           const int64_t i = rcb + (int64_t)q * kLanes;
           const int row = M.rec_row[i];
-          M.trace[(k + 1) * M.n_rec + M.rec_id[i]] = row == 0 ? x0 : M.v[nb + (int64_t)row * kLanes];
+          M.trace[(k + 1) * M.n_rec + M.rec_id[i]] = M.v[nb + (int64_t)row * kLanes];
         }
       }
     }

@@ -112,6 +112,10 @@ class Scenario:
     rec_node: np.ndarray      # int32 global nodes whose voltage is recorded
     v_init: float = -65.0
     meta: dict = field(default_factory=dict)
+    # half gap junctions: node, peer node (global), conductance (uS); one entry per side
+    gap_node: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int32))
+    gap_peer: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int32))
+    gap_g: np.ndarray = field(default_factory=lambda: np.zeros(0, np.float64))
 
     @property
     def n_cells(self) -> int:

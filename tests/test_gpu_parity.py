@@ -280,3 +280,41 @@ def test_morphological_types(cn, cpt, mapping):
     ref = run_oracle(sc)
     assert len(ref["g"]) > 20
     assert_parity(run_gpu(cn, sc, mapping=mapping), ref)
+
+
+def _with_gaps(sc, g=0.0005, seed=5):
+    """Adds symmetric gap junctions between random node pairs of different
+    cells (one pair per cell: a node of cell i with a node of cell i+1)."""
+    import dataclasses
+    rng = np.random.default_rng(seed)
+    off = np.asarray(sc.cell_offset)
+    a, b = [], []
+    for c in range(sc.n_cells - 1):
+        a.append(off[c] + rng.integers(0, off[c + 1] - off[c]))
+        b.append(off[c + 1] + rng.integers(0, off[c + 2] - off[c + 1]))
+    a, b = np.array(a, np.int32), np.array(b, np.int32)
+    return dataclasses.replace(sc, gap_node=np.concatenate([a, b]), gap_peer=np.concatenate([b, a]),
+                               gap_g=np.full(2 * len(a), g))
+
+
+@pytest.mark.parametrize("mapping", [1, 0, 16 | (1 << 20)])
+def test_gap_junctions_against_oracle(cn, mapping):
+    """Gap junctions between random node pairs of neighbouring cells of a
+    driven network: the exchange interval drops to one step; raster and
+    voltages must still match the oracle in every layout."""
+    sc = _with_gaps(network(n_cells=64, tstop=20.0, w_median=0.03, bg_w=0.03, bg_rate_hz=30.0))
+    ref = run_oracle(sc)
+    gpu = run_gpu(cn, sc, mapping=mapping)
+    assert len(ref["g"]) > 10
+    assert_parity(gpu, ref)
+
+
+def test_gap_pair_closed_form(cn):
+    """The two-compartment junction of the oracle pins, on the GPU."""
+    import importlib
+    pins = importlib.import_module("test_oracle_pins")
+    sc = pins.gap_pair()
+    ref = run_oracle(sc)
+    gpu = run_gpu(cn, sc)
+    assert np.max(np.abs(gpu["tr"] - ref["tr"])) <= 1e-9
+    assert np.max(np.abs(gpu["tr"][1] + 65.0)) > 0.1  # the junction moved the second cell

@@ -469,3 +469,54 @@ def test_oracle_adjoint_matches_central_differences():
     # checkpoint spacing does not change the result
     J2, gna2, gk2, gp2 = adjoint(sc, K, tgt, seg=K, nthreads=2)
     assert np.allclose(gna2, gna, rtol=1e-12) and np.allclose(gp2, gp, rtol=1e-12, atol=1e-12)
+
+
+# -------------------------------------------------------- gap junctions
+def gap_pair(g_uS=0.002, tstop=5.0, both_sides=True, gl=1e-3, e=-65.0, amp=0.2):
+    """Two single passive compartments (L = d = 20 um); cell 0 gets a 0.5 ms
+    current pulse; a gap junction of g uS couples their nodes (one half gap
+    per side, or only the half gap on cell 0)."""
+    import dataclasses
+    a = single_compartment(mech="pas", tstop=tstop, pas_g=gl, pas_e=e, v_init=e,
+                           stim_amp=amp, stim_del=0.0, stim_dur=0.5)
+    off = np.array([0, 1, 2], np.int32)
+    pas = MechTable("pas", np.array([0, 1], np.int32), {"g": np.full(2, gl), "e": np.full(2, e)})
+    sc = dataclasses.replace(
+        a, cell_offset=off, parent=np.array([-1, -1], np.int32), dx=np.repeat(a.dx, 2),
+        diam=np.repeat(a.diam, 2), Ra=np.repeat(a.Ra, 2), cm=np.repeat(a.cm, 2),
+        spike_node=np.zeros(2, np.int32), threshold=np.full(2, 100.0), mechs=[pas],
+        rec_node=np.array([0, 1], np.int32),
+        gap_node=np.array([0, 1] if both_sides else [0], np.int32),
+        gap_peer=np.array([1, 0] if both_sides else [1], np.int32),
+        gap_g=np.full(2 if both_sides else 1, g_uS))
+    return sc
+
+
+def test_gap_junction_sum_and_difference_laws():
+    """With the peer voltage of the start of the step and the own voltage
+    implicit, two equal passive compartments obey, step by step,
+    (s' - 2e) = (s - 2e)(c + G)/(c + gl + G) for the sum s = v0 + v1 and
+    d' = d (c - G)/(c + gl + G) for the difference, c = 1e-3 cm/dt,
+    G = 100 g/area.  Checked after the pulse ends."""
+    g, gl, e, dt = 0.002, 1e-3, -65.0, 0.025
+    sc = gap_pair(g_uS=g, gl=gl, e=e)
+    tr = simulate(sc, nthreads=1).traces()
+    area = math.pi * 20.0 * 20.0
+    c, G = 1e-3 * 1.0 / dt, 100.0 * g / area
+    s, d = tr[0] + tr[1], tr[0] - tr[1]
+    k0 = 25  # the pulse is over
+    for k in range(k0, sc.nsteps):
+        assert abs((s[k + 1] - 2 * e) - (s[k] - 2 * e) * (c + G) / (c + gl + G)) <= 1e-12 * abs(s[k] - 2 * e) + 1e-14
+        assert abs(d[k + 1] - d[k] * (c - G) / (c + gl + G)) <= 1e-12 * abs(d[k]) + 1e-14
+    assert abs(d[k0]) > 1.0  # the pulse made a real difference
+
+
+def test_half_gap_acts_on_its_own_side_only():
+    """A half gap on cell 0 alone: cell 1 evolves exactly as an uncoupled
+    compartment at rest, cell 0 feels the junction."""
+    sc = gap_pair(both_sides=False)
+    tr = simulate(sc, nthreads=1).traces()
+    assert np.all(tr[1] == -65.0)
+    ref = gap_pair(g_uS=0.0)
+    tr0 = simulate(ref, nthreads=1).traces()
+    assert np.max(np.abs(tr[0] - tr0[0])) > 0.1
