@@ -13,7 +13,7 @@ DEPS = SOURCES + [os.path.join(HERE, "csrc", f) for f in ("cn_device.cuh", "cn_k
 
 def nvcc_cmd(out, extra=()):
     return ["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
-            "-Xcompiler", "-fPIC", "-shared", "--threads", "4", "-I", os.path.join(ROOT, "include"), *extra,
+            "-Xcompiler", "-fPIC", "-Xcompiler", "-pthread", "-shared", "--threads", "4", "-I", os.path.join(ROOT, "include"), *extra,
             "-o", out, *SOURCES]
 
 

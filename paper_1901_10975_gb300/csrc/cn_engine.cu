@@ -10,6 +10,7 @@
 #include <cstring>
 #include <numeric>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "cn.h"
@@ -510,9 +511,23 @@ bool build_layout(int32_t n_cells, const int32_t* off, const int32_t* parent, co
   L.plans.assign(n_cells, CellPlan{});
   L.depth = 1;
   int H = 1;
+  {  // cells are planned independently: spread them over the host's cores
+    const int nt = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    auto work = [&](int t) {
+      for (int c = (int)((int64_t)n_cells * t / nt); c < (int)((int64_t)n_cells * (t + 1) / nt); ++c)
+        L.plans[c] = plan_cell(parent + off[c], off[c + 1] - off[c], target);
+    };
+    if (nt == 1 || n_cells < 256) {
+      work(0);
+      for (int t = 1; t < nt; ++t) work(t);
+    } else {
+      std::vector<std::thread> th;
+      for (int t = 0; t < nt; ++t) th.emplace_back(work, t);
+      for (auto& x : th) x.join();
+    }
+  }
   for (int c = 0; c < n_cells; ++c) {
     const int n = off[c + 1] - off[c];
-    L.plans[c] = plan_cell(parent + off[c], n, target);
     L.depth = std::max(L.depth, L.plans[c].depth);
     H = std::max(H, L.plans[c].span);
     for (int32_t li = 0; li < n; ++li)
