@@ -313,13 +313,13 @@ def e2e_measure(args, cn, K, layout):
                           warps_per_block=layout[1])
     md.cn_run(float(K))
     g, k = md.cn_get_spikes()
-    tr = [md.cn_get_trace(r) for r in range(len(sc.rec_node))]
+    tr = md.cn_get_traces()
     dt = time.perf_counter() - t0
-    d2h = g.nbytes + k.nbytes + sum(x.nbytes for x in tr)
+    d2h = g.nbytes + k.nbytes + tr.nbytes
     md.close()
     return {"value": sc.n_nodes * 40 * K / dt, "unit": UNIT, "h2d_bytes_per_step": h2d / K,
             "d2h_bytes_per_step": d2h / K, "seconds": dt,
-            "region": "cn_geometry + cn_model_create + cn_add_* + cn_run + cn_get_spikes + cn_get_trace "
+            "region": "cn_geometry + cn_model_create + cn_add_* + cn_run + cn_get_spikes + cn_get_traces "
                       "(with the layout the autotuner chose for the device-timed run)"}
 
 

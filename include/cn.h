@@ -246,6 +246,11 @@ cn_status cn_get_spikes(cn_model* m, int32_t* gid, int64_t* step, size_t cap, si
  * Two-call form as cn_get_spikes.                                          */
 cn_status cn_get_trace(cn_model* m, int32_t rec_id, double* out, size_t cap, size_t* n);
 
+/* Every recorded trace at once, step-major: out[k * n_rec + rec_id] for
+ * k = 0..step (one contiguous copy; cn_get_trace reads one probe).
+ * Two-call: out NULL -> *n = (step + 1) * n_rec.  Errors: CN_ERANGE.     */
+cn_status cn_get_traces(cn_model* m, double* out, size_t cap, size_t* n);
+
 /* Node voltages v_k of every node, in global input order (cap >= n_nodes). */
 cn_status cn_get_v(cn_model* m, double* out, size_t cap);
 

@@ -81,6 +81,8 @@ def lib():
         L.cn_checkpoint_load.restype = st
         L.cn_add_gaps.argtypes = [C.c_void_p, C.c_int64, _P_I32, _P_I32, _P_F64]
         L.cn_add_gaps.restype = st
+        L.cn_get_traces.argtypes = [C.c_void_p, _P_F64, C.c_size_t, C.POINTER(C.c_size_t)]
+        L.cn_get_traces.restype = st
         L.cn_model_create.argtypes = [C.POINTER(cn_morph), C.POINTER(cn_mech_table), C.c_int32,
                                       C.POINTER(cn_options), C.POINTER(C.c_void_p)]
         L.cn_model_create.restype = st
@@ -390,6 +392,15 @@ class Model:
         if n.value:
             _check(lib().cn_get_spikes(self._h, _p(g, _P_I32), _p(k, _P_I64), n.value, C.byref(n)), self._h)
         return g, k
+
+    def cn_get_traces(self) -> np.ndarray:
+        """All recorded traces, [n_rec, steps + 1] (one device-to-host copy)."""
+        n = C.c_size_t(0)
+        _check(lib().cn_get_traces(self._h, None, 0, C.byref(n)), self._h)
+        nr = self.n_rec
+        out = np.empty(n.value, np.float64)
+        _check(lib().cn_get_traces(self._h, _p(out, _P_F64), n.value, C.byref(n)), self._h)
+        return out.reshape(-1, nr).T if nr else np.zeros((0, self.step + 1))  # a view, no copy
 
     def cn_get_trace(self, rec_id):
         n = C.c_size_t()

@@ -2021,6 +2021,21 @@ cn_status cn_get_trace(cn_model* m, int32_t rec_id, double* out, size_t cap, siz
   return CN_OK;
 }
 
+cn_status cn_get_traces(cn_model* m, double* out, size_t cap, size_t* n) {
+  if (!m || !n) return CN_EINVAL;
+  const size_t nr = m->rec_node.size();
+  *n = ((size_t)m->step + 1) * nr;
+  if (!out) return CN_OK;
+  if (cap < *n) return m->fail(CN_ERANGE, "trace buffer too small");
+  if (!m->finalized) {
+    for (size_t i = 0; i < nr; ++i) out[i] = m->opt.v_init_mV;
+    return CN_OK;
+  }
+  CN_CHECK(cn_sync(m));
+  if (*n) CN_TRY_CUDA(m, cudaMemcpy(out, m->dm.trace, *n * sizeof(double), cudaMemcpyDeviceToHost));
+  return CN_OK;
+}
+
 cn_status cn_get_v(cn_model* m, double* out, size_t cap) {
   if (!m || !out) return CN_EINVAL;
   if (cap < (size_t)m->n_nodes) return m->fail(CN_ERANGE, "buffer too small");

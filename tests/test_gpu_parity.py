@@ -318,3 +318,14 @@ def test_gap_pair_closed_form(cn):
     gpu = run_gpu(cn, sc)
     assert np.max(np.abs(gpu["tr"] - ref["tr"])) <= 1e-9
     assert np.max(np.abs(gpu["tr"][1] + 65.0)) > 0.1  # the junction moved the second cell
+
+
+def test_bulk_trace_readback(cn):
+    """cn_get_traces returns every probe's trace in one copy, equal to the
+    per-probe reads."""
+    sc = network(n_cells=40, tstop=5.0)
+    md = cn.from_scenario(sc)
+    md.cn_run(5.0)
+    md.cn_sync()
+    one = np.stack([md.cn_get_trace(r) for r in range(len(sc.rec_node))])
+    assert np.array_equal(md.cn_get_traces(), one)
