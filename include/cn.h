@@ -114,9 +114,10 @@ typedef struct {
 
 /* Cell-to-lane mapping.  Cells are packed 32 lanes to a warp with
  * interleaved rows; a cell larger than the target span is cut into subtrees
- * ("parts") that occupy several lanes of one warp and exchange their
- * junction values by warp shuffles (the warp-cooperative solve of large
- * cells).  A value >= 16 sets the target span in rows directly.           */
+ * ("parts") that occupy lanes of one warp and hand their junction values to
+ * each other through a per-warp shared-memory mailbox (the warp-cooperative
+ * solve of large cells); parts of several cells may stack in one lane.  A
+ * value >= 16 sets the target span in rows directly.                      */
 typedef enum {
   CN_MAP_TALL = 1 << 20, /* flag on a target span: every warp as tall as the largest cell span, so
                             that more parts stack in a lane (default: a warp is as tall as the
@@ -140,22 +141,25 @@ cn_status cn_get_mapping(cn_model* m, int32_t* mapping, int32_t* warps_per_block
                          float* tuned_interval_ms);
 
 /* Host-only preview of the placement cn_model_create makes for a morphology
- * (no GPU is touched).  The elimination order is the Hines order of
- * Section 2: in every part the rows are a depth-first preorder of its
- * subtree, so a row's parent is an earlier row of the same lane, or, for a
- * part root, the junction row of the parent part, exactly one warp row
- * earlier in another lane of the same warp.
+ * (no GPU is touched), with the stacking of several cells' parts per lane
+ * allowed.  The elimination order is the Hines order of Section 2: in every
+ * part the rows are a depth-first preorder of its subtree, so a row's parent
+ * is an earlier (lower) row of the same lane, or, for a part root, the
+ * junction row of the parent part, at a lower warp row in any lane of the
+ * same warp, reached through a per-warp mailbox entry.
  *   n_cells, cell_offset[n_cells+1], parent[n_nodes]: as in cn_morph.
- *   mapping: a cn_mapping value or a target span (>= 16 rows).
+ *   mapping: a cn_mapping value or a target span (>= 16 rows), optionally
+ *   with CN_MAP_TALL or CN_MAP_TALL2.
  * Outputs (caller-owned, each may be NULL):
  *   node_lane[n_nodes]  global lane = 32 * warp + lane of the node's part
  *   node_row[n_nodes]   warp row of the node
- *   node_flags[n_nodes] topology bits: 1<<12 the in-part parent is not the
- *                       previous row ("far"); bits 13-15 number of far
- *                       children; 1<<17 real node; 1<<18 junction (a child
- *                       part hangs from it) with that part's lane in bits
- *                       19-23; 1<<24 part root with its parent part's lane
- *                       in bits 25-29.
+ *   node_flags[n_nodes] topology bits: 1<<6 the in-part parent is not the
+ *                       previous row ("far"); bits 7-9 number of far
+ *                       children; 1<<11 real node; 1<<12 junction (a child
+ *                       part hangs from it) with the mailbox entry in bits
+ *                       14-22; 1<<13 part root with its mailbox entry in
+ *                       bits 23-31 (bits 0-5 and 10 are filled at model
+ *                       creation: mechanism slot, pas).
  *   n_warps, stack_depth: warps used; far-child stack words per lane.
  * Errors: CN_EINVAL on malformed trees or a node with more than 8 children. */
 cn_status cn_plan_layout(int32_t n_cells, const int32_t* cell_offset, const int32_t* parent, int32_t mapping,

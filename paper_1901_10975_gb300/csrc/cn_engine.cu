@@ -259,15 +259,16 @@ cn_status state_init(cn_model* m) {
 }
 
 // Split plan and row order of one cell.  The cell (local nodes 0..n-1,
-// parent[i] < i) is cut into parts (subtrees) that go to different lanes of
-// one warp: part 0 holds the root; every other part hangs from a "junction"
-// node of its parent part.  A part whose junction is at row r of a parent
-// part placed at warp row B starts at warp row B + r + 1, so its root is
-// eliminated one warp row before the junction row and back-substituted one
-// row after it.  Rows of a part follow a depth-first preorder that visits
-// children leading to junctions first, then smaller subtrees first; a row's
-// in-part parent is then the previous row except for "far" children, whose
-// contributions nest last-in-first-out on a per-lane stack.
+// parent[i] < i) is cut into parts (subtrees) that go to lanes of one warp:
+// part 0 holds the root; every other part hangs from a "junction" node of
+// its parent part and must start above that node's warp row (it is
+// eliminated before the junction row and back-substituted after it).  The
+// plan's base is the earliest such start (junction row + 1), which makes
+// span the cell's critical path; the placer may start a part later.  Rows
+// of a part follow a depth-first preorder that visits children leading to
+// junctions first, then smaller subtrees first; a row's in-part parent is
+// then the previous row except for "far" children, whose contributions nest
+// last-in-first-out on a per-lane stack.
 struct CellPart {
   int root = 0;          // local node
   int parent_part = -1;
@@ -285,8 +286,8 @@ struct CellPlan {
   int span = 0;                          // max over parts of base + size
 };
 
-// Warp row of each part's first row: a part starts one row after the row of
-// its junction node in the parent part.  Re-parenting during the split can
+// Earliest warp row of each part's first row: one row after the row of its
+// junction node in the parent part.  Re-parenting during the split can
 // give a part a parent with a larger index, so bases follow the part tree,
 // not the index order.
 std::vector<int> part_bases(const std::vector<CellPart>& parts, const std::vector<int32_t>& row) {

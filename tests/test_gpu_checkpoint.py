@@ -111,3 +111,32 @@ def test_checkpoint_errors(cn):
     assert e.value.status == cn.CN_EINVAL
     with pytest.raises(cn.CNError):
         cn.from_scenario(sc).cn_checkpoint_load(ck[:-8])
+
+
+def test_restart_with_channel_types_and_gaps(cn):
+    """The heterogeneous channel workload (gates, calcium, the channel
+    currents derived from them) and gap junctions between its cells restart
+    bit-identically."""
+    import dataclasses
+    from scenarios import batched
+    sc = batched(n_cells=24, tstop=12.0, n_in=8)
+    off = np.asarray(sc.cell_offset)
+    a = off[:-2] + 1
+    b = off[1:-1] + 1
+    sc = dataclasses.replace(sc, gap_node=np.concatenate([a, b]).astype(np.int32),
+                             gap_peer=np.concatenate([b, a]).astype(np.int32), gap_g=np.full(2 * len(a), 0.001))
+    x = cn.from_scenario(sc)
+    x.cn_run(6.0)
+    ck = x.cn_checkpoint_save()
+    x.cn_run(12.0)
+    gx, kx, trx, vx = outputs(x, sc, 240)
+    y = cn.from_scenario(sc)
+    y.cn_checkpoint_load(ck)
+    y.cn_run(12.0)
+    gy, ky, try_, vy = outputs(y, sc, 240)
+    assert np.array_equal(gx, gy) and np.array_equal(kx, ky)
+    assert np.array_equal(trx, try_) and np.array_equal(vx, vy)
+    for kind, ncol in (("na3h", 2), ("cahva", 3)):
+        n = sc.mech(kind).n
+        for col in range(ncol):
+            assert np.array_equal(x.cn_get_state(kind, col, n), y.cn_get_state(kind, col, n))
