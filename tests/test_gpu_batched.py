@@ -102,3 +102,19 @@ def test_single_channel_type_against_oracle(cn, kind):
     assert np.max(np.abs(tr - ref.trace(0))) <= 1e-9, (tr[:4], ref.trace(0)[:4])
     for c in range(CHANNELS[kind]):
         assert abs(md.cn_get_state(kind, c, 1)[0] - ref.state(kind, c)[0]) <= 1e-9
+
+
+def test_batched_full_size_short(cn):
+    """All 50,000 cells (27.8 M compartments) of the heterogeneous workload,
+    FP64, 2 ms, autotuned layout: raster, soma traces and every node voltage
+    against the oracle."""
+    sc = batched(tstop=2.0)
+    ref = simulate(sc)
+    md = cn.from_scenario(sc, mapping=cn.CN_MAP_TUNE)
+    md.cn_run(sc.tstop)
+    md.cn_sync()
+    g, k = md.cn_get_spikes()
+    rg, rk = ref.spikes()
+    assert np.array_equal(g, rg) and np.array_equal(k, rk)
+    assert np.max(np.abs(md.cn_get_traces() - ref.traces())) <= 1e-9
+    assert np.max(np.abs(md.cn_get_v() - ref.v())) <= 1e-9

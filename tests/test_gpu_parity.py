@@ -113,11 +113,22 @@ def test_network_driven_spiking(cn):
 
 
 def test_network_full_size_short(cn):
-    """All 16,384 cells of the network workload, 10 ms, every soma trace and
-    every node voltage against the oracle."""
+    """All 16,384 cells of the network workload, 10 ms, in the benchmark's
+    launch configuration (autotuned layout, graph replay): every soma trace
+    and every node voltage against the oracle."""
     sc = network(tstop=10.0)
     ref = run_oracle(sc)
-    gpu = run_gpu(cn, sc)
+    gpu = run_gpu(cn, sc, mapping=cn.CN_MAP_TUNE)
+    assert_parity(gpu, ref)
+
+
+def test_morph_types_full_size_short(cn):
+    """All 131,072 cells (10,878,976 compartments) of the morphological-types
+    workload with every cell distinct, 10 ms, autotuned layout."""
+    sc = morph_types(cells_per_type=1, tstop=10.0)
+    ref = run_oracle(sc)
+    assert len(ref["g"]) > 1000
+    gpu = run_gpu(cn, sc, mapping=cn.CN_MAP_TUNE)
     assert_parity(gpu, ref)
 
 
