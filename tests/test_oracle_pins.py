@@ -520,3 +520,22 @@ def test_half_gap_acts_on_its_own_side_only():
     ref = gap_pair(g_uS=0.0)
     tr0 = simulate(ref, nthreads=1).traces()
     assert np.max(np.abs(tr[0] - tr0[0])) > 0.1
+
+
+def test_spike_upstrokes_amplify_rounding():
+    """The spiking dynamics amplify a one-ulp change of the initial voltage
+    by orders of magnitude (it stays far below the 1e-9 mV bar for one
+    perturbation) without changing the raster: the scale against which two
+    correct FP64 implementations that round differently at every step are
+    compared."""
+    import dataclasses
+    from scenarios import morph_types
+    sc = morph_types(n_cells=1024, cells_per_type=1, tstop=10.0)
+    a = simulate(sc)
+    b = simulate(dataclasses.replace(sc, v_init=np.nextafter(sc.v_init, 0.0)))
+    ga, ka = a.spikes()
+    gb, kb = b.spikes()
+    assert len(ga) > 50 and np.array_equal(ga, gb) and np.array_equal(ka, kb)
+    dv = np.max(np.abs(a.traces() - b.traces()))
+    ulp = np.spacing(65.0)
+    assert 100 * ulp < dv < 1e-9
