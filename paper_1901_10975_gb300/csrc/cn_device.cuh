@@ -28,7 +28,7 @@ enum : int32_t { kStatusEvOverflow = 1, kStatusBadState = 2 };
 
 struct EvRec {
   int32_t step;   // step offset inside the interval
-  int32_t syn;    // lane-local synapse row
+  int32_t syn;    // synapse element offset within the target's warp
   double w;       // uS
 };
 
@@ -52,6 +52,11 @@ constexpr int32_t kProotBit = 1 << 13;     // root of a child part (its parent r
 constexpr int kJmailShift = 14;            // bits 14-22: mailbox entry of the hanging part
 constexpr int kPmailShift = 23;            // bits 23-31: mailbox entry of this part root
 constexpr int32_t kMailMask = 511;
+
+// ExpSyn column entries: the first and last synapse of a target row's group
+constexpr int32_t kSynFirst = 1 << 29;
+constexpr int32_t kSynLast = 1 << 30;
+constexpr int32_t kSynTgtMask = kSynFirst - 1;
 
 // Channel types of the batched workload (CN_MECH_NA3H .. CN_MECH_KCA), their
 // gate-state arrays and their per-cell kinetic parameters (the table columns
@@ -94,7 +99,6 @@ struct DevModel {
   // per slot (group * 32 + lane)
   const int32_t* s_rows;
   const int32_t* s_nslot;
-  const int32_t* s_nsyn;
   const int32_t* s_nhh;
   const int32_t* s_nst;
   const int32_t* s_ngap;
@@ -114,8 +118,11 @@ struct DevModel {
   const int32_t* flags;
   // mechanism slots (rows carrying point processes or channels)
   const int32_t* slot_row;
-  // synapses (ExpSyn)
-  const int32_t* syn_row;      // warp row of the synapse (a lane's synapses by row, descending)
+  // synapses (ExpSyn), in warp columns: a warp's synapses grouped by target
+  // (owner lane, row) and spread evenly over its 32 lanes
+  const int32_t* syn_tgt;   // row * 32 + owner lane | kSynFirst | kSynLast; -1: empty
+  double* syn_ge0;          // ge and d0 of the target row (read at kSynFirst)
+  double* syn_d00;
   double* syn_g;
   const double* syn_s;      // 100 / (area cdt) of the synapse row
   const double* syn_e;

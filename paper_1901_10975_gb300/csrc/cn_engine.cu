@@ -86,7 +86,7 @@ struct cn_model {
   int32_t n_groups = 0, n_slots = 0, D = 0;
   std::vector<int32_t> cell_slot;             // gid -> slot
   std::vector<int64_t> g_node_base, g_syn_base, g_hh_base;
-  std::vector<int32_t> syn_slot, syn_q, hh_slot, hh_q;
+  std::vector<int32_t> hh_slot, hh_q;
   int64_t node_elems = 0, syn_elems = 0, hh_elems = 0, st_elems = 0, rec_elems = 0;
   int gate_bytes = 8;
   cn::DevModel dm{};
@@ -213,6 +213,79 @@ Rows interleave(const cn_model* m, const std::vector<int32_t>& inst_node, bool r
 int64_t elem_of(const Rows& r, size_t inst) {
   int s = r.inst_slot[inst];
   return r.g_base[s / cn::kLanes] + (int64_t)r.inst_q[inst] * cn::kLanes + s % cn::kLanes;
+}
+
+// ExpSyn instances in warp columns.  A warp's synapses are grouped by target
+// (owner lane, row); the groups are spread over the 32 columns longest first,
+// each onto the column that is shortest so far, so that every lane of the warp
+// sums about the same number of synapses whatever lane owns them.  One group
+// stays in one column, in consecutive positions, so its sum is one lane's.
+// tgt[e] = row * 32 + owner lane (plus kSynFirst / kSynLast), -1 if empty.
+struct SynPack {
+  std::vector<int32_t> g_rows;   // column height per group
+  std::vector<int64_t> g_base;
+  std::vector<int64_t> elem;     // instance -> element
+  std::vector<int32_t> tgt;      // per element
+  int64_t elems = 0;
+};
+
+SynPack pack_synapses(const cn_model* m) {
+  SynPack p;
+  const size_t n = m->syn_node.size();
+  p.elem.assign(n, 0);
+  p.g_rows.assign(m->n_groups, 0);
+  p.g_base.assign(m->n_groups, 0);
+  std::vector<std::vector<int64_t>> by_group(m->n_groups);
+  for (size_t i = 0; i < n; ++i) by_group[m->node_slot[m->syn_node[i]] / cn::kLanes].push_back((int64_t)i);
+  struct Pl { int col, pos; };
+  std::vector<std::vector<Pl>> place(m->n_groups);
+  std::vector<std::vector<std::pair<int64_t, int64_t>>> runs(m->n_groups);  // [begin, end) into by_group
+  for (int g = 0; g < m->n_groups; ++g) {
+    auto& v = by_group[g];
+    auto key = [&](int64_t i) {
+      return std::make_pair(m->node_slot[m->syn_node[i]] % cn::kLanes, m->node_row[m->syn_node[i]]);
+    };
+    std::stable_sort(v.begin(), v.end(), [&](int64_t x, int64_t y) { return key(x) < key(y); });
+    auto& r = runs[g];
+    for (size_t b = 0; b < v.size();) {
+      size_t e = b + 1;
+      while (e < v.size() && key(v[e]) == key(v[b])) ++e;
+      r.push_back({(int64_t)b, (int64_t)e});
+      b = e;
+    }
+    std::stable_sort(r.begin(), r.end(), [](const std::pair<int64_t, int64_t>& x, const std::pair<int64_t, int64_t>& y) {
+      return x.second - x.first > y.second - y.first;
+    });
+    int h[cn::kLanes] = {0};
+    place[g].resize(v.size());
+    for (auto& run : r) {
+      int c = 0;
+      for (int l = 1; l < cn::kLanes; ++l)
+        if (h[l] < h[c]) c = l;
+      for (int64_t t = run.first; t < run.second; ++t) place[g][t] = Pl{c, h[c]++};
+    }
+    for (int l = 0; l < cn::kLanes; ++l) p.g_rows[g] = std::max(p.g_rows[g], h[l]);
+  }
+  int64_t acc = 0;
+  for (int g = 0; g < m->n_groups; ++g) {
+    p.g_base[g] = acc;
+    acc += (int64_t)p.g_rows[g] * cn::kLanes;
+  }
+  p.elems = acc;
+  p.tgt.assign(std::max<int64_t>(acc, 1), -1);
+  for (int g = 0; g < m->n_groups; ++g) {
+    const auto& v = by_group[g];
+    for (auto& run : runs[g])
+      for (int64_t t = run.first; t < run.second; ++t) {
+        const int64_t i = v[t];
+        const int64_t e = p.g_base[g] + (int64_t)place[g][t].pos * cn::kLanes + place[g][t].col;
+        p.elem[i] = e;
+        const int lane = m->node_slot[m->syn_node[i]] % cn::kLanes;
+        p.tgt[e] = (m->node_row[m->syn_node[i]] * cn::kLanes + lane) | (t == run.first ? cn::kSynFirst : 0) |
+                   (t + 1 == run.second ? cn::kSynLast : 0);
+      }
+  }
+  return p;
 }
 
 template <class F>
@@ -899,8 +972,8 @@ cn_status finalize(cn_model* m) {
     for (size_t t = 0; t < lane_slot_rows[sl].size(); ++t)
       h_slot_row[g_slot_base[sl / cn::kLanes] + (int64_t)t * cn::kLanes + sl % cn::kLanes] = lane_slot_rows[sl][t];
   // synapses, HH, stimuli, records
-  Rows rs = interleave(m, m->syn_node, true), rh = interleave(m, m->hh_node), rt = interleave(m, m->st_node),
-       rr = interleave(m, m->rec_node);
+  SynPack rs = pack_synapses(m);
+  Rows rh = interleave(m, m->hh_node), rt = interleave(m, m->st_node), rr = interleave(m, m->rec_node);
   Rows rg = interleave(m, m->gap_node), rgs = interleave(m, gsrc_node);
   std::vector<int32_t> h_gap_slot(std::max<int64_t>(rg.elems, 1), 0), h_gap_src(std::max<int64_t>(rg.elems, 1), 0);
   std::vector<double> h_gap_area(std::max<int64_t>(rg.elems, 1), 1.0), h_gap_cm(std::max<int64_t>(rg.elems, 1), 1.0),
@@ -919,19 +992,15 @@ cn_status finalize(cn_model* m) {
     h_gsrc_row[e] = m->node_row[gsrc_node[i]];
     h_gsrc_id[e] = (int32_t)i;
   }
-  m->syn_slot = rs.inst_slot; m->syn_q = rs.inst_q;
-  m->syn_elem.resize(m->syn_node.size());
-  for (size_t i = 0; i < m->syn_node.size(); ++i) m->syn_elem[i] = elem_of(rs, i);
+  m->syn_elem = rs.elem;
   m->hh_slot = rh.inst_slot; m->hh_q = rh.inst_q;
   m->g_syn_base = rs.g_base;
   m->g_hh_base = rh.g_base;
   m->syn_elems = rs.elems; m->hh_elems = rh.elems; m->st_elems = rt.elems; m->rec_elems = rr.elems;
-  std::vector<int32_t> h_syn_row(rs.elems, -1);
   std::vector<double> h_syn_tau(rs.elems, 1.0), h_syn_e(rs.elems, 0.0), h_syn_area(rs.elems, 1.0),
       h_syn_cm(rs.elems, 1.0);
   for (size_t i = 0; i < m->syn_node.size(); ++i) {
-    int64_t e = elem_of(rs, i);
-    h_syn_row[e] = m->node_row[m->syn_node[i]];
+    const int64_t e = rs.elem[i];
     h_syn_tau[e] = m->syn_tau[i];
     h_syn_e[e] = m->syn_e[i];
     h_syn_area[e] = m->area[m->syn_node[i]];
@@ -967,12 +1036,16 @@ cn_status finalize(cn_model* m) {
     h_rec_row[e] = m->node_row[m->rec_node[i]];
     h_rec_id[e] = (int32_t)i;
   }
+  // an event names its synapse by the element offset within the target's warp
+  auto syn_off = [&](int32_t i) {
+    return (int32_t)(rs.elem[i] - rs.g_base[m->node_slot[m->syn_node[i]] / cn::kLanes]);
+  };
   // incoming NetCons per target slot, by (source gid, NetCon index)
   size_t nnc = m->nc_src.size();
   std::vector<int64_t> in_off(m->n_slots + 1, 0);
   std::vector<int32_t> nc_tslot(nnc);
   for (size_t j = 0; j < nnc; ++j) {
-    nc_tslot[j] = rs.inst_slot[m->nc_syn[j]];
+    nc_tslot[j] = m->node_slot[m->syn_node[m->nc_syn[j]]];
     in_off[nc_tslot[j] + 1]++;
   }
   for (int s = 0; s < m->n_slots; ++s) in_off[s + 1] += in_off[s];
@@ -987,7 +1060,7 @@ cn_status finalize(cn_model* m) {
   for (size_t q = 0; q < nnc; ++q) {
     int64_t j = nc_order[q];
     h_in_src[q] = m->nc_src[j];
-    h_in_syn[q] = rs.inst_q[m->nc_syn[j]];
+    h_in_syn[q] = syn_off(m->nc_syn[j]);
     h_in_ds[q] = nc_ds[j];
     h_in_w[q] = m->nc_w[j];
   }
@@ -997,7 +1070,7 @@ cn_status finalize(cn_model* m) {
   std::vector<int32_t> ev_tslot(nev);
   for (size_t e = 0; e < nev; ++e) {
     ev_step[e] = std::max<int64_t>(0, round_half_away(m->ev_t[e] / dt));
-    ev_tslot[e] = rs.inst_slot[m->ev_syn[e]];
+    ev_tslot[e] = m->node_slot[m->syn_node[m->ev_syn[e]]];
     x_off[ev_tslot[e] + 1]++;
   }
   for (int s = 0; s < m->n_slots; ++s) x_off[s + 1] += x_off[s];
@@ -1013,7 +1086,7 @@ cn_status finalize(cn_model* m) {
   for (size_t q = 0; q < nev; ++q) {
     int64_t e = ev_order[q];
     h_x_step[q] = ev_step[e];
-    h_x_syn[q] = rs.inst_q[m->ev_syn[e]];
+    h_x_syn[q] = syn_off(m->ev_syn[e]);
     h_x_w[q] = m->ev_w[e];
   }
 
@@ -1047,7 +1120,6 @@ cn_status finalize(cn_model* m) {
   CN_CHECK(upload(m, &p32, rr.g_rows)); dm.g_rec_rows = p32;
   CN_CHECK(upload(m, &p32, slot_rows)); dm.s_rows = p32;
   CN_CHECK(upload(m, &p32, slot_n)); dm.s_nslot = p32;
-  CN_CHECK(upload(m, &p32, rs.slot_n)); dm.s_nsyn = p32;
   CN_CHECK(upload(m, &p32, rh.slot_n)); dm.s_nhh = p32;
   CN_CHECK(upload(m, &p32, rt.slot_n)); dm.s_nst = p32;
   CN_CHECK(upload(m, &p64, rg.g_base)); dm.g_gap_base = p64;
@@ -1079,7 +1151,9 @@ cn_status finalize(cn_model* m) {
   CN_CHECK(zeros(m, &pd, acc)); dm.b = pd;
   CN_CHECK(upload(m, &p32, h_flags)); dm.flags = p32;
   CN_CHECK(upload(m, &p32, h_slot_row)); dm.slot_row = p32;
-  CN_CHECK(upload(m, &p32, h_syn_row)); dm.syn_row = p32;
+  CN_CHECK(upload(m, &p32, rs.tgt)); dm.syn_tgt = p32;
+  CN_CHECK(zeros(m, &pd, rs.elems)); dm.syn_ge0 = pd;
+  CN_CHECK(zeros(m, &pd, rs.elems)); dm.syn_d00 = pd;
   CN_CHECK(zeros(m, &pd, rs.elems)); dm.syn_g = pd;
   CN_CHECK(zeros(m, &pd, rs.elems)); dm.syn_s = pd;
   CN_CHECK(upload(m, &pd, h_syn_e)); dm.syn_e = pd;
@@ -1185,6 +1259,7 @@ cn_status finalize(cn_model* m) {
   CN_CHECK(launch_checked(m, [&] { cn::k_setup_geom<<<nbc, tb, 0, st>>>(dm, m->n_cells, d_off, d_parent, d_area, d_ri, d_cm, d_elem); }));
   CN_CHECK(launch_checked(m, [&] { cn::k_pas_apply<<<nb, tb, 0, st>>>(dm); }));
   CN_CHECK(launch_checked(m, [&] { cn::k_setup_syn<<<nb, tb, 0, st>>>(dm, d_syn_area, d_syn_cm, d_syn_tau); }));
+  CN_CHECK(launch_checked(m, [&] { cn::k_syn_consts<<<nb, tb, 0, st>>>(dm); }));
   CN_CHECK(launch_checked(m, [&] { cn::k_hh_params<<<nb, tb, 0, st>>>(dm); }));
   CN_CHECK(launch_checked(m, [&] { cn::k_setup_stim<<<nb, tb, 0, st>>>(dm, d_st_amp, d_st_area, d_st_cm); }));
   if (rg.elems > 0) {
@@ -2086,10 +2161,7 @@ cn_status cn_get_state(cn_model* m, int32_t type, int32_t col, double* out, size
     if (cap < n) return m->fail(CN_ERANGE, "buffer too small");
     std::vector<double> h(std::max<int64_t>(m->syn_elems, 1));
     CN_TRY_CUDA(m, cudaMemcpy(h.data(), m->dm.syn_g, h.size() * sizeof(double), cudaMemcpyDeviceToHost));
-    for (size_t i = 0; i < n; ++i) {
-      int s = m->syn_slot[i];
-      out[i] = h[m->g_syn_base[s / cn::kLanes] + (int64_t)m->syn_q[i] * cn::kLanes + s % cn::kLanes];
-    }
+    for (size_t i = 0; i < n; ++i) out[i] = h[m->syn_elem[i]];
     return CN_OK;
   }
   if (type >= CN_MECH_NA3H && type <= CN_MECH_KCA) {
@@ -2201,7 +2273,10 @@ cn_status cn_set_cell_param(cn_model* m, int32_t param, const double* values) {
     dfree_raw(m, d_val);
   }
   if (param < 2) CN_CHECK(launch_checked(m, [&] { cn::k_hh_params<<<nb, tb, 0, m->stream>>>(dm); }));
-  else CN_CHECK(launch_checked(m, [&] { cn::k_pas_apply<<<nb, tb, 0, m->stream>>>(dm); }));
+  else {
+    CN_CHECK(launch_checked(m, [&] { cn::k_pas_apply<<<nb, tb, 0, m->stream>>>(dm); }));
+    CN_CHECK(launch_checked(m, [&] { cn::k_syn_consts<<<nb, tb, 0, m->stream>>>(dm); }));
+  }
   CN_TRY_CUDA(m, cudaStreamSynchronize(m->stream));
   return CN_OK;
 }

@@ -123,27 +123,45 @@ __global__ void k_state_init(DevModel M, double v_init) {
     g_store(static_cast<S*>(M.hh_h) + i, ah / (ah + bh));
     g_store(static_cast<S*>(M.hh_n) + i, an / (an + bn));
   }
-  const int ns = M.s_nsyn[slot];
   const int64_t sb = M.g_syn_base[g] + lane;
-  for (int q = 0; q < ns; ++q) M.syn_g[sb + (int64_t)q * kLanes] = 0.0;
+  for (int q = 0; q < M.g_syn_rows[g]; ++q) M.syn_g[sb + (int64_t)q * kLanes] = 0.0;
   M.s_above[slot] = M.s_gid[slot] >= 0 && N > 0 && v_init > M.s_thresh[slot];
   M.ev_count[slot] = 0;
 }
 
 
 // ExpSyn constants: s = 100/(area cdt) (nA -> mA/cm2, row-scaled),
-// decay = exp(-dt/tau), g = 0.
+// decay = exp(-dt/tau), g = 0 (one thread per warp column).
 __global__ void k_setup_syn(DevModel M, const double* node_area, const double* node_cm, const double* tau) {
   const int slot = blockIdx.x * blockDim.x + threadIdx.x;
   if (slot >= M.n_slots) return;
   const int g = slot / kLanes, lane = slot % kLanes;
-  const int n = M.s_nsyn[slot];
   const int64_t base = M.g_syn_base[g] + lane;
-  for (int q = 0; q < n; ++q) {
+  for (int q = 0; q < M.g_syn_rows[g]; ++q) {
     const int64_t i = base + (int64_t)q * kLanes;
-    const_cast<double*>(M.syn_s)[i] = 100.0 / (node_area[i] * (1e-3 * node_cm[i] / M.dt));
-    const_cast<double*>(M.syn_decay)[i] = exp(-M.dt / tau[i]);
+    if (M.syn_tgt[i] >= 0) {
+      const_cast<double*>(M.syn_s)[i] = 100.0 / (node_area[i] * (1e-3 * node_cm[i] / M.dt));
+      const_cast<double*>(M.syn_decay)[i] = exp(-M.dt / tau[i]);
+    }
     M.syn_g[i] = 0.0;
+  }
+}
+
+// Copies of the target rows' ge and d0 beside the first synapse of each
+// group, so the per-step sum reads them with the synapse (coalesced).
+// Re-run whenever d0 or ge change.
+__global__ void k_syn_consts(DevModel M) {
+  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot >= M.n_slots) return;
+  const int g = slot / kLanes, lane = slot % kLanes;
+  const int64_t base = M.g_syn_base[g] + lane, nbw = M.g_node_base[g];
+  for (int q = 0; q < M.g_syn_rows[g]; ++q) {
+    const int64_t i = base + (int64_t)q * kLanes;
+    const int t = M.syn_tgt[i];
+    if (t >= 0 && (t & kSynFirst)) {
+      M.syn_ge0[i] = M.ge[nbw + (t & kSynTgtMask)];
+      M.syn_d00[i] = M.d0[nbw + (t & kSynTgtMask)];
+    }
   }
 }
 
@@ -572,8 +590,8 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, DENSE ? 2 : 4)
   const int32_t* const gfl = M.flags + nb;
 
   const int SLR = M.g_slot_rows[g], nslot = M.s_nslot[slot];
-  const int nsyn = M.s_nsyn[slot];
-  const int64_t sb = M.g_syn_base[g] + lane;
+  const int SYR = M.g_syn_rows[g];
+  const int64_t sb = M.g_syn_base[g] + lane;  // sb - lane, nb - lane: the warp's bases
   const int HR = M.g_hh_rows[g], nhh = M.s_nhh[slot];
   const int64_t hb = M.g_hh_base[g] + lane;
   const int STR = M.g_st_rows[g], nst = M.s_nst[slot];
@@ -635,46 +653,43 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, DENSE ? 2 : 4)
 
   for (int s = s_begin; s < s_end; ++s) {
     const int64_t k = T0 + s;
-    // (1) event delivery
+    // (1) event delivery (into the synapse's column, wherever it lies)
     while (ei < ne && ev[ei].step == s) {
-      M.syn_g[sb + (int64_t)ev[ei].syn * kLanes] += ev[ei].w;
+      M.syn_g[sb - lane + ev[ei].syn] += ev[ei].w;
       ++ei;
     }
-    // (2) nrn_cur.  ExpSyn: G = g s and G E of every synapse of the lane
-    //     (kSynBatch at a time, their loads in flight together), summed per
-    //     row onto the row's constants into ge_syn / d0_syn, which the
-    //     elimination streams; then the v-independent decay of g.  A lane's
-    //     synapses are sorted by row, so each row's sum is contiguous.
+    __syncwarp();
+    // (2) nrn_cur.  ExpSyn: G = g s and G E of every synapse of the warp,
+    //     each lane summing its column (kSynBatch entries at a time, their
+    //     loads in flight together) onto the target row's constants into
+    //     ge_syn / d0_syn, which the elimination streams; then the
+    //     v-independent decay of g.  A row's synapses are consecutive entries
+    //     of one column, between kSynFirst and kSynLast.
     {
-      constexpr int kSynBatch = 4;
-      int prow = -1;
+      constexpr int kSynBatch = 2;
       double age = 0.0, ad = 0.0;
-      for (int q0 = 0; q0 < nsyn; q0 += kSynBatch) {
+      for (int q0 = 0; q0 < SYR; q0 += kSynBatch) {
         double sg_[kSynBatch], ss_[kSynBatch], se_[kSynBatch], sd_[kSynBatch], cg[kSynBatch], cd[kSynBatch];
-        int sr_[kSynBatch];
+        int st_[kSynBatch];
 #pragma unroll
         for (int u = 0; u < kSynBatch; ++u) {
-          sr_[u] = -1;
-          if (q0 + u < nsyn) {
+          st_[u] = -1;
+          if (q0 + u < SYR) {
             const int64_t i = sb + (int64_t)(q0 + u) * kLanes;
-            sr_[u] = M.syn_row[i];
+            st_[u] = M.syn_tgt[i];
             sg_[u] = M.syn_g[i];
             ss_[u] = M.syn_s[i];
             se_[u] = M.syn_e[i];
             sd_[u] = M.syn_decay[i];
-            cg[u] = M.ge[nb + (int64_t)sr_[u] * kLanes];
-            cd[u] = M.d0[nb + (int64_t)sr_[u] * kLanes];
+            cg[u] = M.syn_ge0[i];
+            cd[u] = M.syn_d00[i];
           }
         }
 #pragma unroll
         for (int u = 0; u < kSynBatch; ++u) {
-          if (sr_[u] < 0) continue;
-          if (sr_[u] != prow) {
-            if (prow >= 0) {
-              M.ge_syn[nb + (int64_t)prow * kLanes] = age;
-              M.d0_syn[nb + (int64_t)prow * kLanes] = ad;
-            }
-            prow = sr_[u];
+          const int t = st_[u];
+          if (t < 0) continue;
+          if (t & kSynFirst) {
             age = cg[u];
             ad = cd[u];
           }
@@ -682,13 +697,14 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, DENSE ? 2 : 4)
           age = fma(G, se_[u], age);
           ad += G;
           M.syn_g[sb + (int64_t)(q0 + u) * kLanes] = sg_[u] * sd_[u];
+          if (t & kSynLast) {
+            M.ge_syn[nb - lane + (t & kSynTgtMask)] = age;
+            M.d0_syn[nb - lane + (t & kSynTgtMask)] = ad;
+          }
         }
       }
-      if (prow >= 0) {
-        M.ge_syn[nb + (int64_t)prow * kLanes] = age;
-        M.d0_syn[nb + (int64_t)prow * kLanes] = ad;
-      }
     }
+    __syncwarp();
     // start streaming the top rows (after this lane's row constants are final)
 #pragma unroll
     for (int u = 0; u < kElimRows; ++u) fetch_elim(R - 1 - u, u);
