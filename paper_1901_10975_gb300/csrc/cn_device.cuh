@@ -116,6 +116,7 @@ struct DevModel {
   const double* a;     // row p, column i coupling / cdt_p
   const double* b;     // row i, column p coupling / cdt_i
   const int32_t* flags;
+  const int32_t* pfar;         // far rows: rows down to the in-part parent (else 0)
   // mechanism slots (rows carrying point processes or channels)
   const int32_t* slot_row;
   // synapses (ExpSyn), in warp columns: a warp's synapses grouped by target
@@ -196,22 +197,25 @@ struct DevModel {
 };
 
 // Rows kept in flight by the per-lane cp.async rings.  Elimination streams
-// five FP64 arrays and the flags and spends ~10 FP64 instructions per row;
-// back substitution streams two arrays and the flags and spends one, so its
-// ring is deeper.  Each lane copies and reads only its own elements, so the
-// rings need no warp synchronisation.  The two rings share memory.
+// five FP64 arrays, the flags and the far-parent offsets and spends ~8 FP64
+// instructions per row; back substitution streams two arrays and the flags
+// and spends one, so its ring is deeper.  Each lane copies and reads only its
+// own elements, so the rings need no warp synchronisation.  The two rings
+// share memory.
 constexpr int kElimRows = 4;
 constexpr int kBackRows = 8;
 
 __host__ __device__ inline size_t ring_bytes(bool dense) {
-  // elimination: v, ge, d0, a, b (+ the channel G, G E) and flags per row
-  const size_t elim = (size_t)kElimRows * kLanes * ((dense ? 7 : 5) * sizeof(double) + sizeof(int32_t));
+  // elimination: v, ge, d0, a, b (+ the channel G, G E), flags, pfar per row
+  const size_t elim = (size_t)kElimRows * kLanes * ((dense ? 7 : 5) * sizeof(double) + 2 * sizeof(int32_t));
   const size_t back = (size_t)kBackRows * kLanes * (2 * sizeof(double) + sizeof(int32_t));
   return ((elim > back ? elim : back) + 15) / 16 * 16;
 }
-// Dynamic shared memory of one warp of the interval kernel: row rings, far
-// stack (+1 zero entry), slot buffer, channel reversal potentials and gate
-// kinetics (gate_bytes: 8 for FP64 gating, else 4), mailbox.
+// Dynamic shared memory of one warp of the interval kernel: row rings, the
+// per-lane stack (three words per entry: elimination keeps a pending
+// parent's two partial sums and its row, back substitution the parents'
+// voltages), slot buffer, channel reversal potentials and gate kinetics
+// (gate_bytes: 8 for FP64 gating, else 4), mailbox.
 __host__ __device__ inline size_t interval_smem_bytes(int stack_depth, int max_slots, bool dense, int n_mail,
                                                       int gate_bytes) {
   return ring_bytes(dense) + (size_t)(stack_depth + 1) * kLanes * 3 * sizeof(double) +

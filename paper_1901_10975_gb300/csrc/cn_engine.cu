@@ -354,6 +354,7 @@ struct CellPlan {
   std::vector<CellPart> parts;
   std::vector<int32_t> part_of, row_of;  // per local node: part, row within the part
   std::vector<uint8_t> far;              // per local node
+  std::vector<int32_t> pfar;             // per local far node: rows down to its in-part parent
   std::vector<int32_t> nfar;             // per local node (in-part far children)
   int depth = 1;                         // far-stack depth needed
   int span = 0;                          // max over parts of base + size
@@ -463,6 +464,7 @@ CellPlan plan_cell(const int32_t* parent, int n, int target) {
   }
   P.row_of.assign(n, -1);
   P.far.assign(n, 0);
+  P.pfar.assign(n, 0);
   P.nfar.assign(n, 0);
   std::vector<int32_t> cc, st;
   for (size_t q = 0; q < P.parts.size(); ++q) {
@@ -488,6 +490,7 @@ CellPlan plan_cell(const int32_t* parent, int n, int target) {
       const int u = pt.nodes[r];
       if (P.row_of[parent[u]] != r - 1) {
         P.far[u] = 1;
+        P.pfar[u] = r - P.row_of[parent[u]];
         P.nfar[parent[u]]++;
       }
     }
@@ -575,6 +578,7 @@ struct Layout {
   std::vector<int32_t> lane_cell;             // lane -> its only cell (-1: none or several)
   std::vector<int32_t> node_slot, node_row;   // global node -> lane, warp row
   std::vector<int32_t> node_flags;            // global node -> topology bits
+  std::vector<int32_t> node_pfar;             // global node -> rows down to the in-part parent (far nodes)
 };
 
 constexpr int kPackLookahead = 512;  // remaining cells tried per warp  // refusals after which a warp takes no more cells
@@ -792,6 +796,7 @@ bool build_layout(int32_t n_cells, const int32_t* off, const int32_t* parent, co
   L.node_slot.assign(nn, 0);
   L.node_row.assign(nn, 0);
   L.node_flags.assign(nn, 0);
+  L.node_pfar.assign(nn, 0);
   for (int c = 0; c < n_cells; ++c) {
     const CellPlan& P = L.plans[c];
     const int64_t p0 = cell_part0[c];
@@ -808,6 +813,7 @@ bool build_layout(int32_t n_cells, const int32_t* off, const int32_t* parent, co
       for (size_t q2 = 1; q2 < P.parts.size(); ++q2)
         if (P.parts[q2].jnode == li) f |= cn::kJuncBit | ((warp_mail0[c] + (int)q2 - 1) << cn::kJmailShift);
       L.node_flags[node] = f;
+      L.node_pfar[node] = P.pfar[li];
     }
   }
   return true;
@@ -943,12 +949,13 @@ cn_status finalize(cn_model* m) {
   m->smem_bytes = smem;
   // per-row flags (interleaved) and per-node geometry (node order)
   std::vector<double> h_gp(acc, 0.0), h_ep(acc, 0.0);
-  std::vector<int32_t> h_flags(acc, cn::kNoSlot);
+  std::vector<int32_t> h_flags(acc, cn::kNoSlot), h_pfar(acc, 0);
   std::vector<int64_t> h_elem(m->n_nodes);
   for (int64_t node = 0; node < m->n_nodes; ++node) {
     const int64_t e = node_elem(node);
     h_elem[node] = e;
     h_flags[e] = L.node_flags[node] | (row_slot[node] >= 0 ? row_slot[node] : cn::kNoSlot);
+    h_pfar[e] = L.node_pfar[node];
   }
   m->node_elem = h_elem;
   for (size_t q = 0; q < m->pas_node.size(); ++q) {
@@ -1150,6 +1157,7 @@ cn_status finalize(cn_model* m) {
   CN_CHECK(zeros(m, &pd, acc)); dm.a = pd;
   CN_CHECK(zeros(m, &pd, acc)); dm.b = pd;
   CN_CHECK(upload(m, &p32, h_flags)); dm.flags = p32;
+  CN_CHECK(upload(m, &p32, h_pfar)); dm.pfar = p32;
   CN_CHECK(upload(m, &p32, h_slot_row)); dm.slot_row = p32;
   CN_CHECK(upload(m, &p32, rs.tgt)); dm.syn_tgt = p32;
   CN_CHECK(zeros(m, &pd, rs.elems)); dm.syn_ge0 = pd;

@@ -553,14 +553,19 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, DENSE ? 2 : 4)
   double* const e_cge = e_cg + kElimRows * kLanes;
   int32_t* const e_fl =
       reinterpret_cast<int32_t*>(reinterpret_cast<double*>(smem) + (DENSE ? 7 : 5) * kElimRows * kLanes) + lane;
+  int32_t* const e_pf = e_fl + kElimRows * kLanes;
   double* const b_x = reinterpret_cast<double*>(smem) + lane;
   double* const b_bp = b_x + kBackRows * kLanes;
   int32_t* const b_fl = reinterpret_cast<int32_t*>(reinterpret_cast<double*>(smem) + 2 * kBackRows * kLanes) + lane;
   double* const wsm = reinterpret_cast<double*>(smem + ring_bytes(DENSE));
-  double* const st_a = wsm + lane;  // far stack [DS][32] each
-  double* const st_x = st_a + (DS + 1) * kLanes;  // entry DS stays zero: rows that pop nothing read it
-  double* const st_y = st_x + (DS + 1) * kLanes;
-  double* const sl_ge = st_y + (DS + 1) * kLanes;  // slot buffer [max_slots][32]
+  // per-lane stack [DS + 1][32] of three words.  Elimination: the partial
+  // sums of parents some of whose far children are done, with the parent's
+  // row; back substitution: the parents' voltages for their far children.
+  double* const st_r = wsm + lane;
+  double* const st_d = st_r + (DS + 1) * kLanes;
+  int32_t* const st_o = reinterpret_cast<int32_t*>(wsm + 2 * (DS + 1) * kLanes) + lane;
+  double* const st_x = st_r;
+  double* const sl_ge = st_r + 3 * (DS + 1) * kLanes;  // slot buffer [max_slots][32]
   double* const sl_d = sl_ge + M.max_slots * kLanes;
   // channel types: reversal potentials [6][32] (FP64) and the gate kinetics
   // [kChanParams][32] in the gate arithmetic's type
@@ -571,9 +576,6 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, DENSE ? 2 : 4)
   // mailbox [n_mail][4] shared by the warp: a part root leaves (-a, x, b/d)
   // for its junction row, the junction row leaves v for the part root
   double* const mail = reinterpret_cast<double*>(kin_base + (DENSE ? kChanParams * kLanes * sizeof(T) : 0));
-  st_a[DS * kLanes] = 0.0;
-  st_x[DS * kLanes] = 0.0;
-  st_y[DS * kLanes] = 0.0;
   const int chmask = DENSE ? M.g_chmask[g] : 0;
   if (DENSE) {
     for (int q = 0; q < kChanParams; ++q) kinT[q * kLanes] = (T)M.ch_kin[(int64_t)q * M.n_slots + slot];
@@ -629,6 +631,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, DENSE ? 2 : 4)
         cp_async8(e_cge + u * kLanes, M.ch_ge + nb + o);
       }
       cp_async4(e_fl + u * kLanes, gfl + o);
+      cp_async4(e_pf + u * kLanes, M.pfar + nb + o);
     }
     cp_async_commit();
   };
@@ -741,12 +744,15 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, DENSE ? 2 : 4)
         }
       }
     }
-    // (3) elimination, leaves to root.  Branch-free per row: a far child
-    //     pushes its raw (-a, x, b/d) onto the lane's stack and its parent
-    //     pops it into two FMAs (zero coefficients on rows that pop
-    //     nothing); the previous row's carry enters the same way.
-    double ca = 0.0, cx = 0.0, cb = 0.0, x = 0.0;
-    int top = 0;
+    // (3) elimination, leaves to root.  One FMA pair per row takes the
+    //     previous row's (-a, x, b/d): into this row when the previous row is
+    //     its child, or, when the previous row was a far child, into the
+    //     partial sums of that child's parent.  The row after a far child is
+    //     always a leaf (the last row of the preceding sibling's subtree), so
+    //     its own row needs no pair.  A parent's partial sums start from its
+    //     v and d0 and take their place when its row comes.
+    double ca = 0.0, cx = 0.0, cb = 0.0, x = 0.0, pv = 0.0, pd = 0.0;
+    int top = 0, pp = -1;
     for (int jb = R - 1; jb >= 0; jb -= kElimRows) {
 #pragma unroll
       for (int u = 0; u < kElimRows; ++u) {
@@ -757,8 +763,13 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, DENSE ? 2 : 4)
           const int f = e_fl[ro];
           const int sl = f & kNoSlot;
           const bool hs = sl != kNoSlot;
+          // this row's partial sums, if far children of it were folded
+          const int ti = (top > 0 ? top - 1 : 0) * kLanes;
+          const bool own = top > 0 && st_o[ti] == j;
+          const double v0 = own ? st_r[ti] : e_v[ro];
+          double dd0 = own ? st_d[ti] : e_d0[ro];
+          top -= own ? 1 : 0;
           double acc_ge = e_ge[ro];  // constants with this step's synaptic terms
-          double dd0 = e_d0[ro];
           if (__any_sync(0xffffffffu, hs)) {  // HH / IClamp rows (somas): add and clear the slot
             if (hs) {
               const int si = sl * kLanes;
@@ -768,25 +779,26 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, DENSE ? 2 : 4)
               sl_d[si] = 0.0;
             }
           }
-          const int np = (f >> kNFarShift) & kNFarMask;
-          const int tp = np > 0 ? top - 1 : top;
-          // a row that pops nothing reads the zero entry DS (no stale words reach the FMAs)
-          const int ti = (np > 0 ? min(max(tp, 0), DS - 1) : DS) * kLanes;
-          const double fa = st_a[ti];
-          const double fx = st_x[ti];
-          const double fb = st_y[ti];
-          top = tp;
-          double base = e_v[ro] + acc_ge;
+          double base = v0 + acc_ge;
           if (DENSE) {  // channel currents of this step (computed at the end of the previous one)
             base += e_cge[ro];
             dd0 += e_cg[ro];
           }
-          double rhs = fma(fa, fx, base);
-          double d = fma(fa, fb, dd0);
-          for (int q = 1; q < np; ++q) {  // third and further children (rare)
-            --top;
-            rhs = fma(st_a[top * kLanes], st_x[top * kLanes], rhs);
-            d = fma(st_a[top * kLanes], st_y[top * kLanes], d);
+          // the previous row's terms: into this row, or into its parent's
+          // partial sums (a new entry, or the top one if it is that parent's)
+          const bool fin = pp >= 0;
+          const int ai = (top > 0 ? top - 1 : 0) * kLanes;
+          const bool acc = fin && top > 0 && st_o[ai] == pp;
+          const double o_r = fma(ca, cx, fin ? (acc ? st_r[ai] : pv) : base);
+          const double o_d = fma(ca, cb, fin ? (acc ? st_d[ai] : pd) : dd0);
+          double rhs = fin ? base : o_r;
+          double d = fin ? dd0 : o_d;
+          if (fin) {
+            const int w = acc ? ai : top * kLanes;
+            st_r[w] = o_r;
+            st_d[w] = o_d;
+            st_o[w] = pp;
+            top += acc ? 0 : 1;
           }
           // a part of this cell hangs from this row: its root was eliminated
           // at a higher warp row and left (-a, x, b/d) in the mailbox
@@ -799,28 +811,27 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, DENSE ? 2 : 4)
               d = fma(q[0], q[2], d);
             }
           }
-          rhs = fma(ca, cx, rhs);
-          d = fma(ca, cb, d);
           const double r = rcp64(d);
           x = rhs * r;
           const double bp = e_b[ro] * r;
           gv[(int64_t)j * kLanes] = x;
           gbp[(int64_t)j * kLanes] = bp;
           const double na = -e_a[ro];
-          const bool far = (f & kFarBit) != 0;
-          if (far) {
-            st_a[top * kLanes] = na;
-            st_x[top * kLanes] = x;
-            st_y[top * kLanes] = bp;
-          }
           if (f & kProotBit) {  // the parent row lies below, possibly in another lane
             double* q = mail + 4 * (((uint32_t)f >> kPmailShift) & kMailMask);
             q[0] = na;
             q[1] = x;
             q[2] = bp;
           }
-          top += far ? 1 : 0;
-          ca = (far || (f & kProotBit)) ? 0.0 : na;
+          // a far child: its parent's v and d0 (not eliminated yet) start the
+          // parent's partial sums at the next row
+          const bool far = (f & kFarBit) != 0;
+          pp = far ? j - e_pf[ro] : -1;
+          if (far) {
+            pv = gv[(int64_t)pp * kLanes];
+            pd = gd0[(int64_t)pp * kLanes];
+          }
+          ca = (f & kProotBit) ? 0.0 : na;
           cx = x;
           cb = bp;
         }

@@ -4,8 +4,8 @@ cn_plan_layout returns, for every node, the lane and warp row the engine
 gives it and the topology bits the interval kernel reads.  These tests check
 the invariants the kernel relies on (Hines order inside every part, a part
 root above its junction row in the same warp with matching mailbox entries,
-one spike source per lane, far-child stack discipline within the reported
-depth), and then run the kernel's elimination schedule on random tree
+one spike source per lane, far-child partial sums within the reported
+stack depth), and then run the kernel's elimination schedule on random tree
 systems in NumPy, following only the placement: the solution must equal a
 direct sparse solve."""
 import numpy as np
@@ -80,9 +80,21 @@ def check_invariants(off, parent, L):
 
 def emulate_solve(off, parent, L, a, b, d, rhs):
     """The interval kernel's elimination and back substitution, warp row by
-    warp row, driven only by the placement and its flags."""
+    warp row, driven only by the placement and its flags.  Elimination takes
+    one (-a, x, b/d) term per row: the previous row's, into this row when
+    that row is its child; when that row was a far child, into the partial
+    sums of its parent (which start from the parent's own row and replace it
+    when the parent's row comes), on the row after it, which must be a leaf
+    of the same lane."""
     lane, row, fl = L["lane"], L["row"], L["flags"]
     n = parent.shape[0]
+    gpar = np.full(n, -1, np.int64)
+    has_child = np.zeros(n, bool)
+    for c in range(len(off) - 1):
+        for i in range(off[c] + 1, off[c + 1]):
+            gpar[i] = off[c] + parent[i]
+            if not fl[i] & PROOT:
+                has_child[gpar[i]] = True
     at = {}
     for i in range(n):
         at[(int(lane[i]), int(row[i]))] = i
@@ -97,43 +109,53 @@ def emulate_solve(off, parent, L, a, b, d, rhs):
         R = int(span[w])
         if R == 0:
             continue
-        stack = {l: [] for l in lanes}
+        stack = {l: [] for l in lanes}   # [parent row, partial rhs, partial d]
         carry = {l: None for l in lanes}
+        pend = {l: None for l in lanes}  # parent node of the previous row if it was far
         mail = {}
         maxtop = 0
         for j in range(R - 1, -1, -1):
             for l in lanes:
                 i = at.get((l, j))
                 if i is None:
+                    assert pend[l] is None, "the row after a far child is empty"
                     carry[l] = None
                     continue
                 f = int(fl[i])
-                r_, d_ = rhs[i], d[i]
-                for _ in range(nfar(f)):
-                    na, xx, bb = stack[l].pop()
+                if stack[l] and stack[l][-1][0] == j:
+                    _, r_, d_ = stack[l].pop()
+                else:
+                    r_, d_ = rhs[i], d[i]
+                if pend[l] is not None:
+                    assert not has_child[i], "the row after a far child has in-part children"
+                    p = pend[l]
+                    na, xx, bb = carry[l]
+                    if stack[l] and stack[l][-1][0] == row[p]:
+                        stack[l][-1][1] += na * xx
+                        stack[l][-1][2] += na * bb
+                    else:
+                        stack[l].append([int(row[p]), rhs[p] + na * xx, d[p] + na * bb])
+                        maxtop = max(maxtop, len(stack[l]))
+                elif carry[l] is not None:
+                    na, xx, bb = carry[l]
                     r_ += na * xx
                     d_ += na * bb
                 if f & JUNC:
                     na, xx, bb = mail.pop(jmail(f))
                     r_ += na * xx
                     d_ += na * bb
-                if carry[l] is not None:
-                    na, xx, bb = carry[l]
-                    r_ += na * xx
-                    d_ += na * bb
                 x[i] = r_ / d_
                 bp[i] = b[i] / d_
                 ent = (-a[i], x[i], bp[i])
-                carry[l] = None
-                if f & FAR:
-                    stack[l].append(ent)
-                    maxtop = max(maxtop, len(stack[l]))
-                elif f & PROOT:
+                if f & PROOT:
                     assert pmail(f) not in mail
                     mail[pmail(f)] = ent
+                    carry[l], pend[l] = None, None
                 else:
                     carry[l] = ent
+                    pend[l] = int(gpar[i]) if f & FAR else None
         assert all(len(s) == 0 for s in stack.values()) and not mail
+        assert all(p is None for p in pend.values())
         assert maxtop <= depth
         # back substitution, root to leaves
         vstack = {l: [] for l in lanes}
