@@ -291,6 +291,30 @@ __device__ __forceinline__ void hh_rates(T v, T& am, T& bm, T& ah, T& bh, T& an,
   bn = T(0.125) * dexp_(-(v + T(65.0)) / T(80.0));
 }
 
+// One HH rate by kind (0 am, 1 bm, 2 ah, 3 bh, 4 an, 5 bn) with the same
+// instruction sequence for every kind, so that the lanes of a warp can each
+// evaluate a different rate without diverging:
+//   rate = (c0 + c1 w)(c2 + c3 e) / (c4 + c5 e),  w = v - vh, e = exp(-w/k),
+// with coefficients 0, 1 and -1 that make each product and sum exact, so the
+// value rounds as the rate's own formula in hh_rates does (the vtrap kinds 0
+// and 4 keep their small-u limit).
+template <typename T>
+__device__ __forceinline__ T hh_rate(int kind, T v) {
+  const bool vt = kind == 0 || kind == 4;
+  const T vh = kind == 0 ? T(-40.0) : kind == 3 ? T(-35.0) : kind == 4 ? T(-55.0) : T(-65.0);
+  const T k = kind == 1 ? T(18.0) : kind == 2 ? T(20.0) : kind == 5 ? T(80.0) : T(10.0);
+  const T A = kind == 0 ? T(0.1) : kind == 4 ? T(0.01) : kind == 1 ? T(4.0) : kind == 2 ? T(0.07)
+                                                                  : kind == 5 ? T(0.125) : T(1.0);
+  const T w = v - vh;
+  const T u = w / k;
+  const T e = dexp_(-u);
+  if (vt && (u < T(0) ? -u : u) < (sizeof(T) == 8 ? T(1e-6) : T(1e-4))) return A * k * (T(1.0) + T(0.5) * u);
+  const T num = vt ? A * w : A;
+  const T fac = (kind == 1 || kind == 2 || kind == 5) ? e : T(1.0);
+  const T den = vt ? T(1.0) - e : kind == 3 ? T(1.0) + e : T(1.0);
+  return num * fac / den;
+}
+
 // cnexp: x <- x + (1 - exp(-dt (alpha+beta))) (alpha/(alpha+beta) - x)
 template <typename T>
 __device__ __forceinline__ T cnexp_step(T x, T al, T be, T dt) {

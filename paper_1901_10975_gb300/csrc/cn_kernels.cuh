@@ -901,25 +901,37 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, DENSE ? 2 : 4)
           if (fr[u]) dense_step<PREC>(M, chmask, nb + (int64_t)(j0 + u) * kLanes, vv[u], erev, kinT, in[u]);
       }
     }
-    // (4) nrn_state: HH gates (cnexp) at v_{k+1}
+    // (4) nrn_state: HH gates (cnexp) at v_{k+1}.  A warp holds few HH
+    //     instances (one per soma), so their work is spread over the lanes:
+    //     the six rates of every instance, one per lane, then the three gate
+    //     updates, one per lane.  Scratch lives in the row ring, idle here.
     for (int q = 0; q < HR; ++q) {
-      if (q < nhh) {
-        const int64_t i = hb + (int64_t)q * kLanes;
-        const int row = M.hh_row[i];
-        const T vv = (T)M.v[nb + (int64_t)row * kLanes];
-        T am, bm, ah, bh, an, bn;
-        hh_rates<T>(vv, am, bm, ah, bh, an, bn);
-        const T tdt = (T)dt;
-        g_store(gm + i, cnexp_step<T>(g_load(gm + i), am, bm, tdt));
-        g_store(gh + i, cnexp_step<T>(g_load(gh + i), ah, bh, tdt));
-        g_store(gn + i, cnexp_step<T>(g_load(gn + i), an, bn, tdt));
-        if (TRAJ) {
-          double* tg = M.traj_g + (k + 1 - M.traj_k0) * 3 * M.hh_elems + i;
-          tg[0] = (double)g_load(gm + i);
-          tg[M.hh_elems] = (double)g_load(gh + i);
-          tg[2 * M.hh_elems] = (double)g_load(gn + i);
-        }
+      const bool has = q < nhh;
+      const unsigned act = __ballot_sync(0xffffffffu, has);
+      const int nact = __popc(act);
+      T* const hv = reinterpret_cast<T*>(smem);                             // [32] soma v
+      int* const hl = reinterpret_cast<int*>(smem + kLanes * sizeof(double));  // [32] its lane
+      T* const hr = reinterpret_cast<T*>(smem + kLanes * (sizeof(double) + sizeof(int)));  // [6][32]
+      if (has) {
+        const int rk = __popc(act & ((1u << lane) - 1u));
+        hv[rk] = (T)M.v[nb + (int64_t)M.hh_row[hb + (int64_t)q * kLanes] * kLanes];
+        hl[rk] = lane;
       }
+      __syncwarp();
+      for (int t = lane; t < 6 * nact; t += kLanes) {
+        const int a = t / 6, kind = t - 6 * a;
+        hr[kind * kLanes + a] = hh_rate<T>(kind, hv[a]);
+      }
+      __syncwarp();
+      for (int t = lane; t < 3 * nact; t += kLanes) {
+        const int a = t / 3, gate = t - 3 * a;
+        const int64_t i = hb - lane + hl[a] + (int64_t)q * kLanes;
+        S* const gp = gate == 0 ? gm : gate == 1 ? gh : gn;
+        const T xn = cnexp_step<T>(g_load(gp + i), hr[2 * gate * kLanes + a], hr[(2 * gate + 1) * kLanes + a], (T)dt);
+        const double xs = (double)g_store_ret(gp + i, xn);
+        if (TRAJ) M.traj_g[(k + 1 - M.traj_k0) * 3 * M.hh_elems + gate * M.hh_elems + i] = xs;
+      }
+      __syncwarp();
     }
     // publish this lane's gap peer voltages of step k+1 (the other buffer:
     // lanes of other warps may still read the step-k values)
