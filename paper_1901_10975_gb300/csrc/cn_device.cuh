@@ -1,18 +1,18 @@
 // cn_device.cuh -- device data layout and kernels of the fixed-step engine.
 //
-// Layout ("one cell per thread", Section 4.4's interleaved idea, rebuilt for
-// sm_103a): cells are sorted by size and packed 32 to a warp ("group"); node
-// row j of lane l lives at element base_g + 32*j + l of every per-row array,
-// so the 32 lanes of a warp touch one contiguous 256-byte row of FP64 per
-// array.  Inside a cell, rows follow a depth-first preorder that visits the
-// smaller child subtree first: then a row's parent is the previous row except
-// for the "far" children of branch points, and far contributions nest
-// last-in-first-out, so a per-lane stack of depth <= log2(cell size) + 1 in
-// shared memory replaces every random parent access.  Each row of the tree
-// matrix is scaled by 1/cdt (cdt = 1e-3 cm/dt), so the right-hand side is
-// v + (sum g E)/cdt and no capacitance term is streamed.  Each thread owns
-// one cell for a whole minimum-delay interval: no communication between
-// threads inside the interval kernel.
+// Layout: cells are cut into subtrees ("parts") and the parts are placed on
+// the 32 lanes of warps ("groups"); row j of lane l lives at element
+// base_g + 32*j + l of every per-row array, so the 32 lanes of a warp touch
+// one contiguous 256-byte row of FP64 per array.  Inside a part, rows follow
+// a depth-first preorder, so a row's parent is the previous row except for
+// the "far" children of branch points, whose contributions are folded into
+// partial sums kept on a per-lane stack in shared memory; a part root hangs
+// from a junction row of its parent part at a lower warp row (possibly in
+// another lane of the warp) and passes its values through a per-warp
+// mailbox in shared memory.  Each row of the tree matrix is scaled by 1/cdt
+// (cdt = 1e-3 cm/dt), so the right-hand side is v + (sum g E)/cdt and no
+// capacitance term is streamed.  One warp advances its parts for a whole
+// minimum-delay interval.
 #pragma once
 #include <cstdint>
 #include <cuda_bf16.h>
@@ -32,13 +32,6 @@ struct EvRec {
   double w;       // uS
 };
 
-// Per-row flag word: mechanism slot, "far" bit (the in-lane parent is not the
-// previous row), count of far children, and the cross-lane links of cells
-// split over several lanes.
-// Bits: 0-11 slot, 12 far, 13-15 far children, 16 pas, 17 real row (not
-// padding), 18 junction (a part of the same cell hangs from this row), 19-23
-// the lane holding that part, 24 part root (the parent is in another lane),
-// 25-29 the lane holding the parent.
 constexpr int kMaxWarpsPerBlock = 4;  // warps (groups) per block of the interval kernel
 // Per-row flag word of the interval kernel.
 constexpr int32_t kNoSlot = 0x3f;          // bits 0-5: mechanism slot of the row (HH, IClamp); 63 = none
