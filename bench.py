@@ -172,7 +172,8 @@ def config_dict(args, sc, layout=None):
     if layout is not None:
         mp, wpb, nw, tuned = layout
         span = mp & ~(3 << 20)
-        tall = ", warps twice the largest span" if mp & (2 << 20) else ", tall warps" if mp & (1 << 20) else ""
+        tall = {1: ", tall warps", 2: ", warps twice the largest span", 3: ", warps 1.5 times the largest span"}.get(
+            (mp >> 20) & 3, "")
         d["layout"] = {"mapping": "one cell per lane" if mp == 1 else f"cells split to ~{span} rows per lane" + tall,
                        "warps_per_block": wpb, "warps": nw,
                        "chosen_by": "autotuner" if args.mapping == 2 else "fixed"}

@@ -122,12 +122,13 @@ typedef enum {
   CN_MAP_TALL = 1 << 20, /* flag on a target span: every warp as tall as the largest cell span, so
                             that more parts stack in a lane (default: a warp is as tall as the
                             span of the cell that opened it) */
-  CN_MAP_TALL2 = 1 << 21, /* flag on a target span: every warp twice the largest cell span */
+  CN_MAP_TALL2 = 1 << 21, /* flag on a target span: every warp twice the largest cell span
+                             (with CN_MAP_TALL as well: 1.5 times the largest span) */
   CN_MAP_AUTO = 0,       /* target span = mean cell size (no split when the adjoint is on) */
   CN_MAP_THREAD = 1,     /* one cell per lane, never split */
   CN_MAP_TUNE = 2        /* autotuned on first use: each candidate layout (one cell per lane; spans
-                            of 1/8, 1/4, 1/2 and 1 mean cell size, each also with CN_MAP_TALL and
-                            CN_MAP_TALL2)
+                            of 1/8, 1/4, 1/2 and 1 mean cell size, each also with CN_MAP_TALL,
+                            CN_MAP_TALL | CN_MAP_TALL2 and CN_MAP_TALL2)
                             with 1, 2 and 4 warps per block runs one timed interval from the
                             initial state; the fastest is kept */
 } cn_mapping;

@@ -516,8 +516,8 @@ CellPlan plan_cell(const int32_t* parent, int n, int target) {
 
 // Warp height policy of a mapping value: 0 = the opening cell's span,
 // 1 = the largest span, 2 = twice the largest span.
-int tall_factor(int32_t mapping) {
-  return (mapping & CN_MAP_TALL2) ? 2 : (mapping & CN_MAP_TALL) ? 1 : 0;
+int tall_factor(int32_t mapping) {  // warp height in half spans: TALL 2, TALL2 4, both 3
+  return ((mapping & CN_MAP_TALL) ? 2 : 0) + ((mapping & CN_MAP_TALL2) ? (mapping & CN_MAP_TALL ? 1 : 4) : 0);
 }
 
 // Target span (rows per lane) of a mapping value; 0 = never split.
@@ -633,6 +633,7 @@ bool build_layout(int32_t n_cells, const int32_t* off, const int32_t* parent, co
     int min_lev = 0;
     int H = 0;               // rows of this warp: the span of the cell that opened it
     int max_free = 1 << 30;  // longest free run of rows in any lane
+    int64_t free_rows = 0;   // free rows over all lanes
   };
   std::vector<Warp> warps;
   // per cell: part order (parents first), and the placement found
@@ -680,7 +681,11 @@ bool build_layout(int32_t n_cells, const int32_t* off, const int32_t* parent, co
     std::copy(own, own + cn::kLanes, w.owner);
     w.root[plane[qsp]] = true;
     w.max_free = 0;
-    for (int l = 0; l < cn::kLanes; ++l) w.max_free = std::max(w.max_free, w.H - w.lev[l]);
+    w.free_rows = 0;
+    for (int l = 0; l < cn::kLanes; ++l) {
+      w.max_free = std::max(w.max_free, w.H - w.lev[l]);
+      w.free_rows += w.H - w.lev[l];
+    }
     w.min_lev = cn::kMailMask + (1 << 30);
     for (int l = 0; l < cn::kLanes; ++l)
       if (!w.root[l]) w.min_lev = std::min(w.min_lev, w.lev[l]);  // where a spike-source part can go
@@ -693,7 +698,9 @@ bool build_layout(int32_t n_cells, const int32_t* off, const int32_t* parent, co
     }
     return true;
   };
-  auto set_order = [&](int c) {  // parts of cell c in part-tree order (parents first)
+  // per cell, once: parts in part-tree order (parents first), rows, largest part
+  std::vector<int32_t> cell_porder(cell_part0[n_cells]), cell_rows(n_cells), cell_maxpart(n_cells);
+  for (int c = 0; c < n_cells; ++c) {
     const CellPlan& P = L.plans[c];
     const int np = (int)P.parts.size();
     kids.assign(np, {});
@@ -702,6 +709,22 @@ bool build_layout(int32_t n_cells, const int32_t* off, const int32_t* parent, co
     porder.push_back(0);
     for (size_t h = 0; h < porder.size(); ++h)
       for (int k : kids[porder[h]]) porder.push_back(k);
+    std::copy(porder.begin(), porder.end(), cell_porder.begin() + cell_part0[c]);
+    cell_rows[c] = off[c + 1] - off[c];
+    cell_maxpart[c] = 0;
+    for (const CellPart& pt : P.parts) cell_maxpart[c] = std::max(cell_maxpart[c], (int)pt.nodes.size());
+  }
+  auto set_order = [&](int c) {
+    porder.assign(cell_porder.begin() + cell_part0[c], cell_porder.begin() + cell_part0[c + 1]);
+  };
+  // a cell cannot fit a warp with fewer free rows than it has, or without a
+  // free run as long as its largest part (cheap tests before a placement try)
+  // (nor, when its first part holds the spike source and so starts no lower
+  // than the lowest lane free of one, if the cell's span does not fit above)
+  auto may_fit = [&](int c, const Warp& w) {
+    const CellPlan& P = L.plans[c];
+    const bool src0 = P.part_of[spike_node ? spike_node[c] : 0] == 0;
+    return cell_rows[c] <= w.free_rows && cell_maxpart[c] <= w.max_free && (!src0 || w.min_lev + P.span <= w.H);
   };
   // Fill one warp at a time: it opens with the largest remaining cell and
   // takes, among the next kPackLookahead remaining cells of the same channel
@@ -720,7 +743,7 @@ bool build_layout(int32_t n_cells, const int32_t* off, const int32_t* parent, co
     std::fill(w.owner, w.owner + cn::kLanes, -1);
     std::fill(w.root, w.root + cn::kLanes, false);
     w.mask = mask(c0);
-    w.H = tall ? tall * H : P0.span;
+    w.H = tall ? tall * H / 2 : P0.span;
     warps.push_back(w);
     const int wi = (int)warps.size() - 1;
     set_order(c0);
@@ -747,7 +770,7 @@ bool build_layout(int32_t n_cells, const int32_t* off, const int32_t* parent, co
       const CellPlan& P = L.plans[c];
       const int size0 = (int)P.parts[P.part_of[spike_node ? spike_node[c] : 0]].nodes.size();
       bool ok = false;
-      if (ww.min_lev + size0 <= ww.H) {
+      if (ww.min_lev + size0 <= ww.H && may_fit(c, ww)) {
         set_order(c);
         ok = try_place(c, ww, wi);
       }
@@ -774,7 +797,7 @@ bool build_layout(int32_t n_cells, const int32_t* off, const int32_t* parent, co
       Warp& ww = warps[wi];
       const CellPlan& P = L.plans[c];
       const int size0 = (int)P.parts[P.part_of[spike_node ? spike_node[c] : 0]].nodes.size();
-      if (ww.min_lev + size0 > ww.H) continue;
+      if (ww.min_lev + size0 > ww.H || !may_fit(c, ww)) continue;
       set_order(c);
       if (try_place(c, ww, wi)) placed[c] = 1;
     }
@@ -1537,11 +1560,13 @@ cn_status release_device(cn_model* m) {
   return CN_OK;
 }
 
-// Mapping autotuner: lays the model out for each candidate target span (one
-// cell per lane, and spans of 1/4, 1/2, 1 and 2 mean cell sizes), and for
-// each runs one warm-up and one timed interval from the initial state with
-// 1, 2 and 4 warps per block; keeps the fastest and lays the model out
-// again with it.  Results do not depend on the choice beyond rounding.
+// Mapping autotuner: lays the model out for each candidate (one cell per
+// lane; target spans of 1/8, 1/4, 1/2 and 1 mean cell size, each with warps
+// as tall as the opening cell's span or as 1, 1.5 and 2 times the largest
+// span), and for each runs one warm-up and one timed interval from the
+// initial state with 1, 2 and 4 warps per block; keeps the fastest and lays
+// the model out again with it.  Results do not depend on the choice beyond
+// rounding.
 cn_status autotune(cn_model* m) {
   const int64_t mean = std::max<int64_t>(1, (m->n_nodes + m->n_cells - 1) / std::max(1, m->n_cells));
   std::vector<int32_t> cand{CN_MAP_THREAD};
@@ -1552,6 +1577,7 @@ cn_status autotune(cn_model* m) {
         cand.push_back(v);
         if (!m->dense) {
           cand.push_back(v | CN_MAP_TALL);
+          cand.push_back(v | CN_MAP_TALL | CN_MAP_TALL2);
           cand.push_back(v | CN_MAP_TALL2);
         }
       }

@@ -573,7 +573,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, DENSE ? 2 : 4)
   unsigned char* const kin_base = reinterpret_cast<unsigned char*>(
       wsm + (3 * (DS + 1) + 2 * M.max_slots + (DENSE ? kChanTypes : 0)) * kLanes);
   T* const kinT = reinterpret_cast<T*>(kin_base) + lane;
-  // mailbox [n_mail][4] shared by the warp: a part root leaves (-a, x, b/d)
+  // mailbox [n_mail][4] shared by the warp: a part root leaves (a, x, b/d)
   // for its junction row, the junction row leaves v for the part root
   double* const mail = reinterpret_cast<double*>(kin_base + (DENSE ? kChanParams * kLanes * sizeof(T) : 0));
   const int chmask = DENSE ? M.g_chmask[g] : 0;
@@ -789,8 +789,8 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, DENSE ? 2 : 4)
           const bool fin = pp >= 0;
           const int ai = (top > 0 ? top - 1 : 0) * kLanes;
           const bool acc = fin && top > 0 && st_o[ai] == pp;
-          const double o_r = fma(ca, cx, fin ? (acc ? st_r[ai] : pv) : base);
-          const double o_d = fma(ca, cb, fin ? (acc ? st_d[ai] : pd) : dd0);
+          const double o_r = fma(-ca, cx, fin ? (acc ? st_r[ai] : pv) : base);
+          const double o_d = fma(-ca, cb, fin ? (acc ? st_d[ai] : pd) : dd0);
           double rhs = fin ? base : o_r;
           double d = fin ? dd0 : o_d;
           if (fin) {
@@ -801,14 +801,14 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, DENSE ? 2 : 4)
             top += acc ? 0 : 1;
           }
           // a part of this cell hangs from this row: its root was eliminated
-          // at a higher warp row and left (-a, x, b/d) in the mailbox
+          // at a higher warp row and left (a, x, b/d) in the mailbox
           const bool jn = (f & kJuncBit) != 0;
           if (__any_sync(0xffffffffu, jn)) {
             __syncwarp();
             if (jn) {
               const double* q = mail + 4 * ((f >> kJmailShift) & kMailMask);
-              rhs = fma(q[0], q[1], rhs);
-              d = fma(q[0], q[2], d);
+              rhs = fma(-q[0], q[1], rhs);
+              d = fma(-q[0], q[2], d);
             }
           }
           const double r = rcp64(d);
@@ -816,7 +816,9 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, DENSE ? 2 : 4)
           const double bp = e_b[ro] * r;
           gv[(int64_t)j * kLanes] = x;
           gbp[(int64_t)j * kLanes] = bp;
-          const double na = -e_a[ro];
+          // a, negated inside the FMAs that use it (a separate negation would
+          // cost an FP64 instruction per row)
+          const double na = e_a[ro];
           if (f & kProotBit) {  // the parent row lies below, possibly in another lane
             double* q = mail + 4 * (((uint32_t)f >> kPmailShift) & kMailMask);
             q[0] = na;
