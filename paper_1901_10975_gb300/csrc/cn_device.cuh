@@ -234,24 +234,30 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 // --------------------------------------------------------------- arithmetic
-// Reciprocal of a positive FP64 number in [2^-126, 2^126] (always true for a
-// pivot of the cable matrix: cdt = 1e-3 cm/dt > 0 plus non-negative terms).
-// Newton-Raphson division (e.g. Markstein 1990): a float seed from the top
-// 23 mantissa bits of d, the hardware approximate reciprocal (~2^-22), then
-// one cubic step r' = r (1 + e + e^2), e = 1 - d r, which brings the relative
-// error to ~eps0^3 plus rounding (within 2 ulp of 1/d).  Costs 3 FP64
-// instructions instead of an IEEE division's ~6.
+// Reciprocal of a pivot d in [2^-1021, 2^1021] (a pivot of the cable matrix
+// is >= 1: 1 plus non-negative conductances over cdt).  Newton-Raphson
+// division (e.g. Markstein 1990) in three precisions, so that only two FP64
+// instructions are spent: the MUFU float reciprocal of d's leading mantissa
+// bits (~2^-22) is refined by one Newton step y1 = y0 + y0 (1 - m y0) in
+// 32-bit fixed point on the integer pipes (to ~2^-31), and one FP64 step
+// r + r (1 - d r) then brings it within 1 ulp of 1/d.
 __device__ __forceinline__ double rcp64(double d) {
-  const int hi = __double2hiint(d);
-  const int lo = __double2loint(d);
-  const unsigned fb = ((unsigned)(hi - (896 << 20)) << 3) | ((unsigned)lo >> 29);
+  const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+  const unsigned frac = hi & 0xfffffu;  // d = 2^E m, m = 1.frac in [1, 2)
   float rf;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(__uint_as_float(fb)));
-  const unsigned rb = __float_as_uint(rf);
-  const double r = __hiloint2double((int)((rb >> 3) + (896u << 20)), (int)(rb << 29));
-  const double e = fma(-d, r, 1.0);
-  const double t = fma(e, e, e);
-  return fma(r, t, r);
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(__uint_as_float(0x3f800000u | (frac << 3) | (lo >> 29))));
+  const unsigned rb = __float_as_uint(rf);  // ~1/m in (0.5, 1]
+  unsigned y0 = ((rb & 0x7fffffu) | 0x800000u) << 8;                    // 1/m in Q0.32
+  y0 = rb >= 0x3f800000u ? 0xffffffffu : rb < 0x3f000000u ? 0x80000000u : y0;
+  const unsigned mq = 0x80000000u | (frac << 11) | (lo >> 21);           // m in Q1.31
+  const unsigned long long p = (unsigned long long)mq * y0;              // m y0 in Q1.63
+  const long long e = (long long)(0x8000000000000000ull - p) >> 12;      // (1 - m y0) 2^51
+  long long y1 = (long long)y0 + (((long long)y0 * e) >> 51);
+  y1 = y1 > 0xffffffffll ? 0xffffffffll : y1 < 0x80000000ll ? 0x80000000ll : y1;
+  const unsigned yu = (unsigned)y1;  // 1/m in Q0.32, leading bit 31
+  const unsigned ex = 2045u - ((hi >> 20) & 0x7ffu);  // 1/d = 2^(-E-1) (yu / 2^31)
+  const double r = __hiloint2double((int)((ex << 20) | ((yu >> 11) & 0xfffffu)), (int)(yu << 21));
+  return fma(r, fma(-d, r, 1.0), r);
 }
 
 // alpha = A (v - vh) / (1 - exp(-(v - vh)/k)); limit A k (1 + u/2) near vh.
