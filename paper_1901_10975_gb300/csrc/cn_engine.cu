@@ -173,6 +173,37 @@ cn_status zeros(cn_model* m, T** dst, size_t n) {
 
 // Interleave per-instance lists: instance i of cell c becomes row q of slot
 // cell_slot[c].  Returns per-group row counts/bases and per-slot counts.
+// Runs fn(lo, hi) over [0, n) split into contiguous ranges on up to 16 host
+// threads (one range, inline, when n is small).
+template <class F>
+void parallel_ranges(int64_t n, int64_t min_per_thread, F&& fn) {
+  const int64_t hc = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+  const int64_t nt = std::max<int64_t>(1, std::min<int64_t>(hc, n / std::max<int64_t>(1, min_per_thread)));
+  if (nt <= 1) {
+    fn((int64_t)0, n);
+    return;
+  }
+  std::vector<std::thread> th;
+  for (int64_t t = 0; t < nt; ++t) th.emplace_back([&, t] { fn(n * t / nt, n * (t + 1) / nt); });
+  for (auto& x : th) x.join();
+}
+
+// Stable order of items by (bucket, key): a counting sort by bucket (off is
+// the buckets' CSR offsets), then a stable sort of each bucket's run by key,
+// the runs spread over host threads.
+template <class Key>
+std::vector<int64_t> order_by_bucket(const std::vector<int32_t>& bucket, const std::vector<int64_t>& off, Key key) {
+  std::vector<int64_t> order(bucket.size());
+  std::vector<int64_t> cur(off.begin(), off.end() - 1);
+  for (size_t i = 0; i < bucket.size(); ++i) order[cur[bucket[i]]++] = (int64_t)i;
+  parallel_ranges((int64_t)off.size() - 1, 256, [&](int64_t lo, int64_t hi) {
+    for (int64_t b = lo; b < hi; ++b)
+      std::stable_sort(order.begin() + off[b], order.begin() + off[b + 1],
+                       [&](int64_t x, int64_t y) { return key(x) < key(y); });
+  });
+  return order;
+}
+
 struct Rows {
   std::vector<int32_t> slot_n;   // per slot
   std::vector<int32_t> g_rows;   // per group
@@ -240,7 +271,8 @@ SynPack pack_synapses(const cn_model* m) {
   struct Pl { int col, pos; };
   std::vector<std::vector<Pl>> place(m->n_groups);
   std::vector<std::vector<std::pair<int64_t, int64_t>>> runs(m->n_groups);  // [begin, end) into by_group
-  for (int g = 0; g < m->n_groups; ++g) {
+  parallel_ranges(m->n_groups, 64, [&](int64_t g0, int64_t g1) {
+  for (int g = (int)g0; g < (int)g1; ++g) {
     auto& v = by_group[g];
     auto key = [&](int64_t i) {
       return std::make_pair(m->node_slot[m->syn_node[i]] % cn::kLanes, m->node_row[m->syn_node[i]]);
@@ -266,6 +298,7 @@ SynPack pack_synapses(const cn_model* m) {
     }
     for (int l = 0; l < cn::kLanes; ++l) p.g_rows[g] = std::max(p.g_rows[g], h[l]);
   }
+  });
   int64_t acc = 0;
   for (int g = 0; g < m->n_groups; ++g) {
     p.g_base[g] = acc;
@@ -589,21 +622,10 @@ bool build_layout(int32_t n_cells, const int32_t* off, const int32_t* parent, co
   L.plans.assign(n_cells, CellPlan{});
   L.depth = 1;
   int H = 1;
-  {  // cells are planned independently: spread them over the host's cores
-    const int nt = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
-    auto work = [&](int t) {
-      for (int c = (int)((int64_t)n_cells * t / nt); c < (int)((int64_t)n_cells * (t + 1) / nt); ++c)
-        L.plans[c] = plan_cell(parent + off[c], off[c + 1] - off[c], target);
-    };
-    if (nt == 1 || n_cells < 256) {
-      work(0);
-      for (int t = 1; t < nt; ++t) work(t);
-    } else {
-      std::vector<std::thread> th;
-      for (int t = 0; t < nt; ++t) th.emplace_back(work, t);
-      for (auto& x : th) x.join();
-    }
-  }
+  // cells are planned independently: spread them over the host's cores
+  parallel_ranges(n_cells, 256, [&](int64_t c0, int64_t c1) {
+    for (int64_t c = c0; c < c1; ++c) L.plans[c] = plan_cell(parent + off[c], off[c + 1] - off[c], target);
+  });
   for (int c = 0; c < n_cells; ++c) {
     const int n = off[c + 1] - off[c];
     L.depth = std::max(L.depth, L.plans[c].depth);
@@ -1079,12 +1101,7 @@ cn_status finalize(cn_model* m) {
     in_off[nc_tslot[j] + 1]++;
   }
   for (int s = 0; s < m->n_slots; ++s) in_off[s + 1] += in_off[s];
-  std::vector<int64_t> nc_order(nnc);
-  std::iota(nc_order.begin(), nc_order.end(), 0);
-  std::stable_sort(nc_order.begin(), nc_order.end(), [&](int64_t x, int64_t y) {
-    if (nc_tslot[x] != nc_tslot[y]) return nc_tslot[x] < nc_tslot[y];
-    return m->nc_src[x] < m->nc_src[y];
-  });
+  const std::vector<int64_t> nc_order = order_by_bucket(nc_tslot, in_off, [&](int64_t j) { return m->nc_src[j]; });
   std::vector<int32_t> h_in_src(nnc), h_in_syn(nnc), h_in_ds(nnc);
   std::vector<double> h_in_w(nnc);
   for (size_t q = 0; q < nnc; ++q) {
@@ -1104,12 +1121,7 @@ cn_status finalize(cn_model* m) {
     x_off[ev_tslot[e] + 1]++;
   }
   for (int s = 0; s < m->n_slots; ++s) x_off[s + 1] += x_off[s];
-  std::vector<int64_t> ev_order(nev);
-  std::iota(ev_order.begin(), ev_order.end(), 0);
-  std::stable_sort(ev_order.begin(), ev_order.end(), [&](int64_t x, int64_t y) {
-    if (ev_tslot[x] != ev_tslot[y]) return ev_tslot[x] < ev_tslot[y];
-    return ev_step[x] < ev_step[y];
-  });
+  const std::vector<int64_t> ev_order = order_by_bucket(ev_tslot, x_off, [&](int64_t e) { return ev_step[e]; });
   std::vector<int64_t> h_x_step(nev);
   std::vector<int32_t> h_x_syn(nev);
   std::vector<double> h_x_w(nev);

@@ -753,6 +753,10 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, DENSE ? 2 : 4)
     //     v and d0 and take their place when its row comes.
     double ca = 0.0, cx = 0.0, cb = 0.0, x = 0.0, pv = 0.0, pd = 0.0;
     int top = 0, pp = -1;
+    // the top stack entry lives in registers (tr, td, owner row to; -1 when
+    // the stack is empty); entries below it in st_r / st_d / st_o [0, top-1)
+    double tr = 0.0, td = 0.0;
+    int to = -1;
     for (int jb = R - 1; jb >= 0; jb -= kElimRows) {
 #pragma unroll
       for (int u = 0; u < kElimRows; ++u) {
@@ -764,11 +768,16 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, DENSE ? 2 : 4)
           const int sl = f & kNoSlot;
           const bool hs = sl != kNoSlot;
           // this row's partial sums, if far children of it were folded
-          const int ti = (top > 0 ? top - 1 : 0) * kLanes;
-          const bool own = top > 0 && st_o[ti] == j;
-          const double v0 = own ? st_r[ti] : e_v[ro];
-          double dd0 = own ? st_d[ti] : e_d0[ro];
-          top -= own ? 1 : 0;
+          const bool own = to == j;
+          const double v0 = own ? tr : e_v[ro];
+          double dd0 = own ? td : e_d0[ro];
+          if (own) {  // pop: the next entry comes back into registers
+            --top;
+            const int ti = (top > 0 ? top - 1 : 0) * kLanes;
+            tr = st_r[ti];
+            td = st_d[ti];
+            to = top > 0 ? st_o[ti] : -1;
+          }
           double acc_ge = e_ge[ro];  // constants with this step's synaptic terms
           if (__any_sync(0xffffffffu, hs)) {  // HH / IClamp rows (somas): add and clear the slot
             if (hs) {
@@ -787,18 +796,24 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, DENSE ? 2 : 4)
           // the previous row's terms: into this row, or into its parent's
           // partial sums (a new entry, or the top one if it is that parent's)
           const bool fin = pp >= 0;
-          const int ai = (top > 0 ? top - 1 : 0) * kLanes;
-          const bool acc = fin && top > 0 && st_o[ai] == pp;
-          const double o_r = fma(-ca, cx, fin ? (acc ? st_r[ai] : pv) : base);
-          const double o_d = fma(-ca, cb, fin ? (acc ? st_d[ai] : pd) : dd0);
+          const bool acc = fin && to == pp;
+          const double o_r = fma(-ca, cx, fin ? (acc ? tr : pv) : base);
+          const double o_d = fma(-ca, cb, fin ? (acc ? td : pd) : dd0);
           double rhs = fin ? base : o_r;
           double d = fin ? dd0 : o_d;
           if (fin) {
-            const int w = acc ? ai : top * kLanes;
-            st_r[w] = o_r;
-            st_d[w] = o_d;
-            st_o[w] = pp;
-            top += acc ? 0 : 1;
+            if (!acc) {  // push: the current top goes to shared memory
+              if (top > 0) {
+                const int w = (top - 1) * kLanes;
+                st_r[w] = tr;
+                st_d[w] = td;
+                st_o[w] = to;
+              }
+              ++top;
+            }
+            tr = o_r;
+            td = o_d;
+            to = pp;
           }
           // a part of this cell hangs from this row: its root was eliminated
           // at a higher warp row and left (a, x, b/d) in the mailbox
@@ -844,7 +859,12 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, DENSE ? 2 : 4)
     // back substitution, root to leaves (row 0: b = 0, so v_0 = x_0)
 #pragma unroll
     for (int u = 0; u < kBackRows; ++u) fetch_back(u, u);
-    double vprev = 0.0;
+    // The stack holds, per parent with far children still to come, its
+    // voltage and that count; the top entry lives in registers (tv, tc),
+    // the entries below it in st_x / st_c [0, top-1).
+    double vprev = 0.0, tv = 0.0;
+    int tc = 0;
+    int32_t* const st_c = st_o;
     for (int jb = 0; jb < R; jb += kBackRows) {
 #pragma unroll
       for (int u = 0; u < kBackRows; ++u) {
@@ -854,9 +874,13 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, DENSE ? 2 : 4)
           const int ro = u * kLanes;
           const int f = b_fl[ro];
           const bool far = (f & kFarBit) != 0;
-          const int tp = far ? top - 1 : top;
-          const double pv = st_x[(tp < DS ? tp : DS - 1) * kLanes];
-          double vp = far ? pv : vprev;
+          double vp = far ? tv : vprev;
+          if (far && --tc == 0) {  // the parent's last far child: pop
+            --top;
+            const int ti = (top > 0 ? top - 1 : 0) * kLanes;
+            tv = st_x[ti];
+            tc = top > 0 ? st_c[ti] : 0;
+          }
           // root of a part: its parent row was back-substituted at a lower
           // warp row and left v in the mailbox
           const bool pr = (f & kProotBit) != 0;
@@ -869,9 +893,16 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, DENSE ? 2 : 4)
           if (f & kJuncBit) mail[4 * ((f >> kJmailShift) & kMailMask) + 3] = vj;
           if (TRAJ) M.traj_v[(k + 1 - M.traj_k0) * M.node_elems + nb + (int64_t)j * kLanes] = vj;
           const int np = (f >> kNFarShift) & kNFarMask;
-          if (np > 0) st_x[tp * kLanes] = vj;
-          for (int q = 1; q < np; ++q) st_x[(tp + q) * kLanes] = vj;
-          top = tp + np;
+          if (np > 0) {  // push this row's voltage for its far children
+            if (top > 0) {
+              const int w = (top - 1) * kLanes;
+              st_x[w] = tv;
+              st_c[w] = tc;
+            }
+            ++top;
+            tv = vj;
+            tc = np;
+          }
           vprev = vj;
         }
         fetch_back(j + kBackRows, u);
