@@ -511,10 +511,11 @@ CellPlan plan_cell(const int32_t* parent, int n, int target) {
       cc.clear();
       for (int c : ch(u))
         if (P.part_of[c] == (int)q) cc.push_back(c);
-      std::stable_sort(cc.begin(), cc.end(), [&](int x, int y) {
-        if (leads[x] != leads[y]) return leads[x] > leads[y];
-        return sub[x] < sub[y];
-      });
+      // stable insertion sort (a node has a handful of children): children
+      // leading to junctions first, then smaller subtrees first
+      auto before = [&](int x, int y) { return leads[x] != leads[y] ? leads[x] > leads[y] : sub[x] < sub[y]; };
+      for (size_t a = 1; a < cc.size(); ++a)
+        for (size_t b = a; b > 0 && before(cc[b], cc[b - 1]); --b) std::swap(cc[b], cc[b - 1]);
       for (auto it = cc.rbegin(); it != cc.rend(); ++it) st.push_back(*it);
     }
     // far flags and stack depth of this part
