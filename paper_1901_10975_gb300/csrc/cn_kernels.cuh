@@ -779,7 +779,10 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, DENSE ? 2 : 4)
             to = top > 0 ? st_o[ti] : -1;
           }
           double acc_ge = e_ge[ro];  // constants with this step's synaptic terms
-          if (__any_sync(0xffffffffu, hs)) {  // HH / IClamp rows (somas): add and clear the slot
+          // one vote covers the rare rows: slot rows and junction rows
+          const bool jn = (f & kJuncBit) != 0;
+          const bool rare = __any_sync(0xffffffffu, hs || jn);
+          if (rare) {  // HH / IClamp rows (somas): add and clear the slot
             if (hs) {
               const int si = sl * kLanes;
               acc_ge += sl_ge[si];
@@ -817,8 +820,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, DENSE ? 2 : 4)
           }
           // a part of this cell hangs from this row: its root was eliminated
           // at a higher warp row and left (a, x, b/d) in the mailbox
-          const bool jn = (f & kJuncBit) != 0;
-          if (__any_sync(0xffffffffu, jn)) {
+          if (rare) {
             __syncwarp();
             if (jn) {
               const double* q = mail + 4 * ((f >> kJmailShift) & kMailMask);

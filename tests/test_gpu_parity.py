@@ -213,12 +213,13 @@ def test_event_buffer_overflow_reported(cn):
     assert e.value.status == cn.CN_ERANGE
 
 
-@pytest.mark.parametrize("mapping", [1, 40, 100, 16 | (1 << 20), 64 | (1 << 20)])
+@pytest.mark.parametrize("mapping", [1, 40, 100, 16 | (1 << 20), 64 | (1 << 20), 40 | (3 << 20), 24 | (2 << 20)])
 def test_split_cells_over_lanes(cn, mapping):
     """The same driven network with one cell per lane (mapping 1) and with
     cells cut into parts of about 40 or 100 rows spread over lanes of one
-    warp: the raster, voltages and states must match the oracle in every
-    layout."""
+    warp, in warps as tall as the opening cell or 1, 1.5 and 2 times the
+    largest span: the raster, voltages and states must match the oracle in
+    every layout."""
     sc = network(n_cells=96, tstop=30.0, w_median=0.03, bg_w=0.03, bg_rate_hz=30.0)
     ref = run_oracle(sc)
     assert len(ref["g"]) > 10

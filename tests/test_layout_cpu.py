@@ -215,7 +215,8 @@ CASES = {
 
 
 @pytest.mark.parametrize("case", sorted(CASES))
-@pytest.mark.parametrize("mapping", [1, 16, 40, 100, 300, 0, 16 | (1 << 20), 100 | (1 << 20)])
+@pytest.mark.parametrize("mapping", [1, 16, 40, 100, 300, 0, 16 | (1 << 20), 100 | (1 << 20), 40 | (3 << 20),
+                                     24 | (2 << 20)])
 def test_layout_invariants_and_emulated_solve(cn, case, mapping):
     off, parent = cells_of(CASES[case]())
     L = cn.cn_plan_layout(off, parent, mapping)
