@@ -75,7 +75,6 @@ struct DevModel {
   // per group
   const int64_t* g_node_base;  // element index of row 0, lane 0 (multiple of 64)
   const int32_t* g_rows;       // rows (even)
-  const int64_t* g_slot_base;
   const int32_t* g_slot_rows;
   const int64_t* g_syn_base;
   const int32_t* g_syn_rows;
@@ -110,8 +109,6 @@ struct DevModel {
   const double* b;     // row i, column p coupling / cdt_i
   const int32_t* flags;
   const int32_t* pfar;         // far rows: rows down to the in-part parent (else 0)
-  // mechanism slots (rows carrying point processes or channels)
-  const int32_t* slot_row;
   // synapses (ExpSyn), in warp columns: a warp's synapses grouped by target
   // (owner lane, row) and spread evenly over its 32 lanes
   const int32_t* syn_tgt;   // row * 32 + owner lane | kSynFirst | kSynLast; -1: empty

@@ -1010,20 +1010,11 @@ cn_status finalize(cn_model* m) {
     h_ep[e] = m->pas_e[q];
     h_flags[e] |= cn::kHasPasBit;
   }
-  // slot rows, interleaved
+  // slots per lane, and the most in any lane of each warp (the kernel clears
+  // that many slot-buffer entries)
   std::vector<int32_t> slot_n(m->n_slots, 0), g_slot_rows(m->n_groups, 0);
-  std::vector<int64_t> g_slot_base(m->n_groups, 0);
   for (int sl = 0; sl < m->n_slots; ++sl) slot_n[sl] = (int32_t)lane_slot_rows[sl].size();
   for (int s = 0; s < m->n_slots; ++s) g_slot_rows[s / cn::kLanes] = std::max(g_slot_rows[s / cn::kLanes], slot_n[s]);
-  int64_t sacc = 0;
-  for (int g = 0; g < m->n_groups; ++g) {
-    g_slot_base[g] = sacc;
-    sacc += (int64_t)g_slot_rows[g] * cn::kLanes;
-  }
-  std::vector<int32_t> h_slot_row(std::max<int64_t>(sacc, 1), 0);
-  for (int sl = 0; sl < m->n_slots; ++sl)
-    for (size_t t = 0; t < lane_slot_rows[sl].size(); ++t)
-      h_slot_row[g_slot_base[sl / cn::kLanes] + (int64_t)t * cn::kLanes + sl % cn::kLanes] = lane_slot_rows[sl][t];
   // synapses, HH, stimuli, records
   SynPack rs = pack_synapses(m);
   Rows rh = interleave(m, m->hh_node), rt = interleave(m, m->st_node), rr = interleave(m, m->rec_node);
@@ -1151,7 +1142,6 @@ cn_status finalize(cn_model* m) {
   double* pd;
   CN_CHECK(upload(m, &p64, m->g_node_base)); dm.g_node_base = p64;
   CN_CHECK(upload(m, &p32, g_rows)); dm.g_rows = p32;
-  CN_CHECK(upload(m, &p64, g_slot_base)); dm.g_slot_base = p64;
   CN_CHECK(upload(m, &p32, g_slot_rows)); dm.g_slot_rows = p32;
   CN_CHECK(upload(m, &p64, rs.g_base)); dm.g_syn_base = p64;
   CN_CHECK(upload(m, &p32, rs.g_rows)); dm.g_syn_rows = p32;
@@ -1194,7 +1184,6 @@ cn_status finalize(cn_model* m) {
   CN_CHECK(zeros(m, &pd, acc)); dm.b = pd;
   CN_CHECK(upload(m, &p32, h_flags)); dm.flags = p32;
   CN_CHECK(upload(m, &p32, h_pfar)); dm.pfar = p32;
-  CN_CHECK(upload(m, &p32, h_slot_row)); dm.slot_row = p32;
   CN_CHECK(upload(m, &p32, rs.tgt)); dm.syn_tgt = p32;
   CN_CHECK(zeros(m, &pd, rs.elems)); dm.syn_ge0 = pd;
   CN_CHECK(zeros(m, &pd, rs.elems)); dm.syn_d00 = pd;
