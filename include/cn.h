@@ -128,7 +128,8 @@ typedef enum {
   CN_MAP_THREAD = 1,     /* one cell per lane, never split */
   CN_MAP_TUNE = 2        /* autotuned on first use: each candidate layout (one cell per lane; spans
                             of 1/8, 1/4, 1/2 and 1 mean cell size, each also with CN_MAP_TALL,
-                            CN_MAP_TALL | CN_MAP_TALL2 and CN_MAP_TALL2)
+                            CN_MAP_TALL | CN_MAP_TALL2 and CN_MAP_TALL2; then 0.85, 0.9, 0.95
+                            and 1.1 times the best span)
                             with 1, 2 and 4 warps per block runs one timed interval from the
                             initial state; the fastest is kept */
 } cn_mapping;

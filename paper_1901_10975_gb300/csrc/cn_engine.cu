@@ -1565,10 +1565,10 @@ cn_status release_device(cn_model* m) {
 // Mapping autotuner: lays the model out for each candidate (one cell per
 // lane; target spans of 1/8, 1/4, 1/2 and 1 mean cell size, each with warps
 // as tall as the opening cell's span or as 1, 1.5 and 2 times the largest
-// span), and for each runs one warm-up and one timed interval from the
-// initial state with 1, 2 and 4 warps per block; keeps the fastest and lays
-// the model out again with it.  Results do not depend on the choice beyond
-// rounding.
+// span; then spans of 0.85, 0.9, 0.95 and 1.1 times the best one), and for
+// each runs one warm-up and one timed interval from the initial state with
+// 1, 2 and 4 warps per block; keeps the fastest and lays the model out again
+// with it.  Results do not depend on the choice beyond rounding.
 cn_status autotune(cn_model* m) {
   const int64_t mean = std::max<int64_t>(1, (m->n_nodes + m->n_cells - 1) / std::max(1, m->n_cells));
   std::vector<int32_t> cand{CN_MAP_THREAD};
@@ -1589,7 +1589,11 @@ cn_status autotune(cn_model* m) {
   const bool prof = m->profiling;
   m->profiling = false;
   cudaEvent_t e0 = take_event(m), e1 = take_event(m);
-  for (int32_t c : cand) {
+  std::vector<int32_t> tried;
+  bool refined = false;
+  for (size_t ci = 0; ci < cand.size(); ++ci) {
+    const int32_t c = cand[ci];
+    tried.push_back(c);
     m->opt.mapping = c;
     CN_CHECK(finalize(m));
     CN_CHECK(ensure_capacity(m, 2 * (int64_t)m->D));
@@ -1611,6 +1615,18 @@ cn_status autotune(cn_model* m) {
       }
     }
     CN_CHECK(release_device(m));
+    // after the coarse candidates, refine the best span: a slightly finer
+    // cut can fill the device's resident warps without a second wave
+    if (ci + 1 == cand.size() && best_map >= 16 && !refined) {
+      refined = true;
+      const int32_t flags = best_map & (CN_MAP_TALL | CN_MAP_TALL2), span = best_map & ~flags;
+      for (double f : {0.85, 0.9, 0.95, 1.1}) {
+        const int32_t v = (int32_t)std::max<int64_t>(16, (int64_t)(span * f + 0.5)) | flags;
+        if (std::find(tried.begin(), tried.end(), v) == tried.end() &&
+            std::find(cand.begin(), cand.end(), v) == cand.end())
+          cand.push_back(v);
+      }
+    }
   }
   m->ev_pool.push_back(e0);
   m->ev_pool.push_back(e1);
