@@ -52,11 +52,20 @@ def hbm_peak():
         return HBM_FALLBACK_GBS, "fallback"
 
 
+def code_only(text):
+    """Source text without comments and blank space, so that a digest changes
+    with the code only (string literals in these sources hold no comment
+    markers)."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def kernel_digest():
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, f), encoding="utf-8") as fh:
+            h.update(code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -504,23 +504,29 @@ __global__ void k_setup_dense(DevModel M, double v_init, bool scale_gbar) {
 }
 
 // ---------------------------------------------------------- interval kernel
-// Advances the 32 cells of one warp (one block) by steps [s_begin, s_end) of
-// interval J, one cell per lane.  Per step k = J D + s (Section 2's list):
+// Each warp advances the parts placed on its 32 lanes (whole cells, or parts
+// of cells split over lanes of the warp) by steps [s_begin, s_end) of
+// interval J; a block holds one to four warps.  Per step k = J D + s
+// (Section 2's list):
 //  1 deliver due events (g += w, in buffer order),
-//  2 nrn_cur: ExpSyn, HH and IClamp add G (diagonal) and G E (+ I_inj) (right
-//    side) into the per-lane slot buffer of their row, seeded with the row's
-//    constants,
+//  2 nrn_cur: ExpSyn G and G E summed per warp column onto the target rows'
+//    constants (ge_syn, d0_syn); HH, IClamp and gap terms into the per-lane
+//    slot buffer of their row; channel terms computed at the end of the
+//    previous step,
 //  3 matrix resolution: the row-scaled system (C + G + L) v_{k+1} = C v_k +
 //    G E + I_inj is eliminated leaves to root in Hines order and
 //    back-substituted root to leaves,
-//  4 nrn_state: HH gates by cnexp at v_{k+1}, ExpSyn decay,
-//  5 threshold detection at the cell's spike row, and recording.
+//  4 nrn_state: channel gates and calcium, then HH gates, by cnexp at
+//    v_{k+1}; the ExpSyn decay is applied with the sums of step 2,
+//  5 threshold detection at the lane's spike row, and recording.
 // Backward Euler with the gates frozen over a step makes every current linear
 // in v, so this is exactly the paper's linearised update
 // (C + G + L) dv = -I(v_k) - L v_k written for v_{k+1} instead of dv.
 // Row data streams through a per-lane shared-memory ring fed by cp.async, each
-// lane copying its own elements kElimRows rows ahead; parents come from a register
-// carry (previous row) or the per-lane far stack.
+// lane copying its own elements kElimRows rows ahead (kBackRows in the back
+// substitution); a row's child terms come from a register carry (previous
+// row), from partial sums on the per-lane stack (far children), or from the
+// warp's mailbox (a part hanging from the row).
 // TRAJ: adjoint recompute -- also store v and the HH gates of every step
 // into the trajectory buffers, and leave spikes, threshold flags and traces
 // untouched.
