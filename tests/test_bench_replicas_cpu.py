@@ -54,3 +54,16 @@ def test_reference_arm_under_torchrun_prints_once():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_kernel_digest_ignores_comments_only():
+    """The digest that ties the ncu traffic in profiles/ to the kernel hashes
+    code only: comments and blank space do not change it, code does."""
+    sys.path.insert(0, ROOT)
+    import bench
+    a = "int f(int x) { // the input\n  return x + 1; /* one more */ }\n"
+    b = "int f(int x) {\n\n  return x + 1;   }"
+    c = "int f(int x) { return x + 2; }"
+    assert bench.code_only(a) == bench.code_only(b)
+    assert bench.code_only(a) != bench.code_only(c)
+    assert "//" not in bench.code_only(a) and "/*" not in bench.code_only(a)
