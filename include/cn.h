@@ -151,7 +151,7 @@ cn_status cn_get_mapping(cn_model* m, int32_t* mapping, int32_t* warps_per_block
  * same warp, reached through a per-warp mailbox entry.
  *   n_cells, cell_offset[n_cells+1], parent[n_nodes]: as in cn_morph.
  *   mapping: a cn_mapping value or a target span (>= 16 rows), optionally
- *   with CN_MAP_TALL or CN_MAP_TALL2.
+ *   with CN_MAP_TALL, CN_MAP_TALL2 or both.
  * Outputs (caller-owned, each may be NULL):
  *   node_lane[n_nodes]  global lane = 32 * warp + lane of the node's part
  *   node_row[n_nodes]   warp row of the node
@@ -162,7 +162,9 @@ cn_status cn_get_mapping(cn_model* m, int32_t* mapping, int32_t* warps_per_block
  *                       14-22; 1<<13 part root with its mailbox entry in
  *                       bits 23-31 (bits 0-5 and 10 are filled at model
  *                       creation: mechanism slot, pas).
- *   n_warps, stack_depth: warps used; far-child stack words per lane.
+ *   n_warps, stack_depth: warps used; the most far children pending at
+ *                       once in any lane while it is eliminated (a bound on
+ *                       the entries of the kernel's per-lane stack).
  * Errors: CN_EINVAL on malformed trees or a node with more than 8 children. */
 cn_status cn_plan_layout(int32_t n_cells, const int32_t* cell_offset, const int32_t* parent, int32_t mapping,
                          int32_t* node_lane, int32_t* node_row, int32_t* node_flags, int32_t* n_warps,
