@@ -843,25 +843,29 @@ bool build_layout(int32_t n_cells, const int32_t* off, const int32_t* parent, co
   L.node_row.assign(nn, 0);
   L.node_flags.assign(nn, 0);
   L.node_pfar.assign(nn, 0);
-  for (int c = 0; c < n_cells; ++c) {
-    const CellPlan& P = L.plans[c];
-    const int64_t p0 = cell_part0[c];
-    L.cell_lane0[c] = part_lane_of_cell[p0];
-    for (int32_t li = 0; li < off[c + 1] - off[c]; ++li) {
-      const int64_t node = off[c] + li;
-      const int q = P.part_of[li];
-      L.node_slot[node] = part_lane_of_cell[p0 + q];
-      L.node_row[node] = part_start_of_cell[p0 + q] + P.row_of[li];
-      int32_t f = cn::kRealBit | (P.far[li] ? cn::kFarBit : 0) | (P.nfar[li] << cn::kNFarShift);
-      // mailbox entry of part q (q >= 1): warp_mail0 + q - 1
-      if (q > 0 && li == P.parts[q].root)
-        f |= cn::kProotBit | (int32_t)((uint32_t)(warp_mail0[c] + q - 1) << cn::kPmailShift);
+  // cells write disjoint node ranges: spread them over the host's cores
+  parallel_ranges(n_cells, 256, [&](int64_t c0, int64_t c1) {
+    for (int64_t c = c0; c < c1; ++c) {
+      const CellPlan& P = L.plans[c];
+      const int64_t p0 = cell_part0[c];
+      L.cell_lane0[c] = part_lane_of_cell[p0];
+      for (int32_t li = 0; li < off[c + 1] - off[c]; ++li) {
+        const int64_t node = off[c] + li;
+        const int q = P.part_of[li];
+        L.node_slot[node] = part_lane_of_cell[p0 + q];
+        L.node_row[node] = part_start_of_cell[p0 + q] + P.row_of[li];
+        int32_t f = cn::kRealBit | (P.far[li] ? cn::kFarBit : 0) | (P.nfar[li] << cn::kNFarShift);
+        // mailbox entry of part q (q >= 1): warp_mail0 + q - 1
+        if (q > 0 && li == P.parts[q].root)
+          f |= cn::kProotBit | (int32_t)((uint32_t)(warp_mail0[c] + q - 1) << cn::kPmailShift);
+        L.node_flags[node] = f;
+        L.node_pfar[node] = P.pfar[li];
+      }
+      // the junction of each part (a node carries at most one)
       for (size_t q2 = 1; q2 < P.parts.size(); ++q2)
-        if (P.parts[q2].jnode == li) f |= cn::kJuncBit | ((warp_mail0[c] + (int)q2 - 1) << cn::kJmailShift);
-      L.node_flags[node] = f;
-      L.node_pfar[node] = P.pfar[li];
+        L.node_flags[off[c] + P.parts[q2].jnode] |= cn::kJuncBit | ((warp_mail0[c] + (int)q2 - 1) << cn::kJmailShift);
     }
-  }
+  });
   return true;
 }
 
