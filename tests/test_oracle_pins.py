@@ -292,6 +292,40 @@ def test_ring_raster_composes_isolated_responses(weight, tstop):
         assert all(x == i % 16 for i, (x, _) in enumerate(got))
 
 
+def test_expsyn_converges_first_order_to_the_ode():
+    """One passive compartment with one ExpSyn (tau 2 ms, e 0 mV) kicked by a
+    0.005 uS event at 1 ms, against an independent high-accuracy integration
+    (DOP853, rtol 1e-12) of cm dv/dt = -g_l (v - e_l) - (100 G(t)/area)(v - e),
+    G(t) = w exp(-(t - 1)/tau): the backward-Euler error halves with dt.  A
+    wrong point-to-density scale (100/area), sign or decay would leave an
+    error that does not vanish."""
+    from scipy.integrate import solve_ivp
+    w, tau, es, T = 0.005, 2.0, 0.0, 10.0
+    area, gl, el, cm = math.pi * 20.0 * 20.0, 1e-4, -65.0, 1.0   # single_compartment: L = diam = 20 um
+
+    def rhs(t, v):
+        G = 100.0 * w * math.exp(-(t - 1.0) / tau) / area
+        return [-(1e3 / cm) * (gl * (v[0] - el) + G * (v[0] - es))]
+
+    errs = []
+    for dt in (0.025, 0.0125, 0.00625, 0.003125):
+        sc = single_compartment(mech="pas", tstop=T, dt=dt, pas_g=gl, pas_e=el, v_init=el)
+        sc.mechs.append(MechTable("expsyn", np.array([0], np.int32), {"tau": np.array([tau]), "e": np.array([es])}))
+        sc.ev_syn, sc.ev_t, sc.ev_w = np.array([0], np.int32), np.array([1.0]), np.array([w])
+        tr = simulate(sc, nthreads=1).trace(0)
+        ts = np.arange(tr.shape[0]) * dt
+        ref = np.full(ts.shape, el)
+        after = ts > 1.0
+        ref[after] = solve_ivp(rhs, (1.0, ts[-1]), [el], method="DOP853", rtol=1e-12, atol=1e-12,
+                               t_eval=ts[after]).y[0]
+        assert np.all(tr[~after] == el)          # nothing before the event
+        errs.append(np.max(np.abs(tr - ref)))
+    assert tr.max() > -45.0                      # a real depolarisation towards e
+    for e0, e1 in zip(errs, errs[1:]):
+        assert 1.95 < e0 / e1 < 2.05
+    assert errs[-1] < 0.01
+
+
 def test_netcon_delay_rounds_half_away_from_zero():
     """A 2.5-step delay (dt 0.25 ms, delay 0.625 ms) lands 3 steps after the
     spike: the target's voltage is untouched until that step's update."""
