@@ -344,10 +344,13 @@ cn_status cn_profile_read(cn_model* m, double* interval_ms, int64_t* interval_la
  * 0 <= parent[i] < i - first otherwise).  Row i has diagonal d[i] and
  * coupling b[i] to its parent p; row p has coupling a[i] to i.  Writes the
  * solution to x (which may not alias the inputs); inputs are not modified.
- * Allocates n_nodes doubles of scratch (stream-ordered) per call and
- * synchronizes the stream before returning.  Errors: CN_EINVAL (bad sizes,
- * NULL pointers or a bad parent index, detected on the device; that tree is
- * left unsolved), CN_ERANGE (a zero pivot), CN_ENOMEM, CN_ECUDA.           */
+ * offset must satisfy offset[0] = 0, offset[n_trees] = n_nodes and
+ * offset[t] <= offset[t+1]; this is checked on the device before any tree is
+ * touched, and a violation solves nothing.  Allocates n_nodes doubles of
+ * scratch (stream-ordered) per call and synchronizes the stream before
+ * returning.  Errors: CN_EINVAL (bad sizes, NULL pointers, bad offsets, or a
+ * bad parent index, detected on the device; such a tree is left unsolved),
+ * CN_ERANGE (a zero pivot), CN_ENOMEM, CN_ECUDA.                           */
 cn_status cn_solve_trees(int32_t n_trees, int64_t n_nodes, const int32_t* offset, const int32_t* parent,
                          const double* a, const double* b, const double* d, const double* rhs, double* x,
                          void* stream);
@@ -361,13 +364,25 @@ cn_status cn_solve_trees(int32_t n_trees, int64_t n_nodes, const int32_t* offset
  * 1,048,576 rows (n_nodes) per call (CN_ERANGE above that); every GPU that
  * loads the library holds that 8 MiB array until the process exits.  The
  * first call on a device looks up the array's device address (once per
- * device), so make that first call before any stream capture.  All calls on
+ * device), so make that first call before any stream capture.  That address
+ * belongs to the device's primary context: after cudaDeviceReset() of the
+ * device it is stale, so do not call this entry point again in a process
+ * that reset the device after its first call.  Each call clears its status
+ * word first, so an error in one call does not leak into the next.  All calls on
  * a device share the one array: calls whose execution overlaps on the GPU
  * (other streams, other host threads) race and must be serialized by the
  * caller.  Synchronizes the stream before returning; allocates nothing.    */
 cn_status cn_solve_trees_noalloc(int32_t n_trees, int64_t n_nodes, const int32_t* offset, const int32_t* parent,
                                  const double* a, const double* b, const double* d, const double* rhs, double* x,
                                  void* stream);
+
+/* The reciprocal the engine's solve takes of every pivot (diagnostics):
+ * out[i] = 1/d[i] for n DEVICE values d[i] in [2^-1021, 2^1021] (a pivot of
+ * the row-scaled cable matrix is >= 1), computed as the interval kernel does
+ * -- a float seed refined by Newton-Raphson steps (Markstein's division
+ * method) -- instead of an IEEE division; within 1 ulp of the correctly
+ * rounded 1/d.  Synchronizes the stream.  Errors: CN_EINVAL, CN_ECUDA.     */
+cn_status cn_pivot_reciprocal(int64_t n, const double* d, double* out, void* stream);
 
 /* Error text of the last failed call on m (or of the last failed
  * cn_model_create when m is NULL).  Valid until the next call on m.        */

@@ -859,6 +859,14 @@ void or_get_cai(void* h, double* out) {
   std::memcpy(out, M->cai.data(), sizeof(double) * M->cai.size());
 }
 
+// Overwrite [Ca]i of every node (a perturbation for the pins: without a
+// CAHVA instance nothing else changes cai, so the KCa gate then relaxes at
+// fixed rates).
+void or_set_cai(void* h, const double* in) {
+  Model* M = static_cast<Model*>(h);
+  std::memcpy(M->cai.data(), in, sizeof(double) * M->cai.size());
+}
+
 // state column `col` of mechanism `kind` (HH: m,h,n; expsyn: g; ...)
 int or_get_state(void* h, int32_t kind, int32_t col, double* out) {
   Model* M = static_cast<Model*>(h);

@@ -74,6 +74,7 @@ def lib():
         L.or_get_trace.argtypes = [C.c_void_p, C.c_int32, _P_F64]
         L.or_get_v.argtypes = [C.c_void_p, _P_F64]
         L.or_get_cai.argtypes = [C.c_void_p, _P_F64]
+        L.or_set_cai.argtypes = [C.c_void_p, _P_F64]
         L.or_get_state.argtypes = [C.c_void_p, C.c_int32, C.c_int32, _P_F64]
         L.or_get_state.restype = C.c_int
         L.or_get_geometry.argtypes = [C.c_void_p, _P_F64, _P_F64]
@@ -223,6 +224,11 @@ class OracleModel:
         out = np.empty(self.sc.n_nodes, np.float64)
         lib().or_get_cai(self._h, _p(out, _P_F64))
         return out
+
+    def set_cai(self, values) -> None:
+        """Overwrite [Ca]i of every node (test perturbation)."""
+        x = np.ascontiguousarray(np.broadcast_to(np.asarray(values, np.float64), (self.sc.n_nodes,)))
+        lib().or_set_cai(self._h, _p(x, _P_F64))
 
     def state(self, kind: str, col: int) -> np.ndarray:
         m = self.sc.mech(kind)

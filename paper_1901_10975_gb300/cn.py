@@ -133,6 +133,8 @@ def lib():
         L.cn_solve_trees.restype = st
         L.cn_solve_trees_noalloc.argtypes = list(L.cn_solve_trees.argtypes)
         L.cn_solve_trees_noalloc.restype = st
+        L.cn_pivot_reciprocal.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]
+        L.cn_pivot_reciprocal.restype = st
         L.cn_last_error.argtypes = [C.c_void_p]
         L.cn_last_error.restype = C.c_char_p
         L.cn_model_destroy.argtypes = [C.c_void_p]
@@ -202,6 +204,19 @@ def cn_solve_trees(offset, parent, a, b, d, rhs, device=0):
     if st != CN_OK:
         raise CNError(st, "cn_solve_trees failed")
     return t["x"].cpu().numpy()
+
+
+def cn_pivot_reciprocal(d, device=0):
+    """The interval kernel's pivot reciprocal of every value of d (host array
+    in, host array out)."""
+    import torch
+    x = torch.from_numpy(_f64(d)).to(f"cuda:{device}")
+    out = torch.empty_like(x)
+    stream = torch.cuda.current_stream(device).cuda_stream
+    st = lib().cn_pivot_reciprocal(x.numel(), x.data_ptr(), out.data_ptr(), stream)
+    if st != CN_OK:
+        raise CNError(st, "cn_pivot_reciprocal failed")
+    return out.cpu().numpy()
 
 
 def cn_solve_trees_noalloc(offset, parent, a, b, d, rhs, device=0):

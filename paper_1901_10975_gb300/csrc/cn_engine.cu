@@ -2572,6 +2572,16 @@ cn_status cn_run_adjoint(cn_model* m, const double* dj, double* grad) {
   return CN_OK;
 }
 
+cn_status cn_pivot_reciprocal(int64_t n, const double* d, double* out, void* stream) {
+  if (n < 0 || (n > 0 && (!d || !out))) return CN_EINVAL;
+  if (n == 0) return CN_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int tb = 256;
+  cn::k_rcp64<<<(unsigned)((n + tb - 1) / tb), tb, 0, st>>>(d, out, n);
+  if (cudaGetLastError() != cudaSuccess) return CN_ECUDA;
+  return cudaStreamSynchronize(st) == cudaSuccess ? CN_OK : CN_ECUDA;
+}
+
 const char* cn_last_error(const cn_model* m) {
   if (!m) return g_create_error.c_str();
   return m->err.c_str();

@@ -268,6 +268,13 @@ __global__ void k_pull_events(DevModel M, int64_t J, const int64_t* Jp) {
   M.ev_count[slot] = m;
 }
 
+// The solve's pivot reciprocal applied elementwise (diagnostics: lets the
+// reciprocal be compared with IEEE division).
+__global__ void k_rcp64(const double* __restrict__ d, double* __restrict__ out, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = rcp64(d[i]);
+}
+
 // Advances the device-side interval index after a complete interval.
 __global__ void k_next_interval(int64_t* Jp) { *Jp += 1; }
 

@@ -16,16 +16,34 @@
 
 namespace cn {
 
-enum : int32_t { kSolveBadParent = 1, kSolveZeroPivot = 2 };
+enum : int32_t { kSolveBadParent = 1, kSolveZeroPivot = 2, kSolveBadOffset = 4 };
+
+// Offsets are checked before any tree is touched: off[0] = 0,
+// off[n_trees] = n_nodes and off[t] <= off[t+1] for every t make the trees'
+// row ranges disjoint and inside [0, n_nodes).  Any violation sets
+// kSolveBadOffset, and then k_solve_trees solves nothing.
+__global__ void k_check_offsets(int32_t n_trees, int64_t n_nodes, const int32_t* __restrict__ off,
+                                int32_t* status) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t > n_trees) return;
+  const int32_t o = off[t];
+  bool bad = o < 0 || (int64_t)o > n_nodes;
+  if (t == 0) bad = bad || o != 0;
+  if (t == n_trees) bad = bad || (int64_t)o != n_nodes;
+  else bad = bad || off[t + 1] < o;
+  if (bad) atomicOr(status, kSolveBadOffset);
+}
 
 // dd: scratch of n_nodes doubles.  status: one int32, OR-ed with error bits;
-// a tree with a bad parent index or a zero pivot is left unsolved.
+// a tree with a bad parent index or a zero pivot is left unsolved, and
+// nothing is solved after a bad offset.
 __global__ void k_solve_trees(int32_t n_trees, const int32_t* __restrict__ off, const int32_t* __restrict__ parent,
                               const double* __restrict__ a, const double* __restrict__ b,
                               const double* __restrict__ d, const double* __restrict__ rhs, double* __restrict__ x,
                               double* __restrict__ dd, int32_t* status) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n_trees) return;
+  if (*(volatile int32_t*)status & kSolveBadOffset) return;
   const int32_t i0 = off[t], i1 = off[t + 1];
   if (i1 <= i0) return;
   if (parent[i0] != -1) {
@@ -61,8 +79,19 @@ __global__ void k_solve_trees(int32_t n_trees, const int32_t* __restrict__ off, 
   for (int32_t i = i0 + 1; i < i1; ++i) x[i] = (x[i] - b[i] * x[i0 + parent[i]]) / dd[i];
 }
 
+// The two launches of a solve on one stream: the offset check, then the
+// trees (which read the check's verdict from the status word).
+cudaError_t launch_solve(int32_t n_trees, int64_t n_nodes, const int32_t* off, const int32_t* parent,
+                         const double* a, const double* b, const double* d, const double* rhs, double* x,
+                         double* dd, int32_t* status, cudaStream_t st) {
+  const int tb = 128;
+  k_check_offsets<<<(n_trees + 1 + tb - 1) / tb, tb, 0, st>>>(n_trees, n_nodes, off, status);
+  k_solve_trees<<<(n_trees + tb - 1) / tb, tb, 0, st>>>(n_trees, off, parent, a, b, d, rhs, x, dd, status);
+  return cudaGetLastError();
+}
+
 cn_status solve_status(int32_t st) {
-  if (st & kSolveBadParent) return CN_EINVAL;
+  if (st & (kSolveBadParent | kSolveBadOffset)) return CN_EINVAL;
   if (st & kSolveZeroPivot) return CN_ERANGE;
   return CN_OK;
 }
@@ -88,11 +117,9 @@ cn_status cn_solve_trees(int32_t n_trees, int64_t n_nodes, const int32_t* offset
   }
   cn_status rc = CN_OK;
   if (cudaMemsetAsync(status, 0, sizeof(int32_t), st) != cudaSuccess) rc = CN_ECUDA;
-  if (rc == CN_OK) {
-    const int tb = 128;
-    cn::k_solve_trees<<<(n_trees + tb - 1) / tb, tb, 0, st>>>(n_trees, offset, parent, a, b, d, rhs, x, dd, status);
-    if (cudaGetLastError() != cudaSuccess) rc = CN_ECUDA;
-  }
+  if (rc == CN_OK && cn::launch_solve(n_trees, n_nodes, offset, parent, a, b, d, rhs, x, dd, status, st) !=
+                        cudaSuccess)
+    rc = CN_ECUDA;
   int32_t h = 0;
   if (rc == CN_OK && cudaMemcpyAsync(&h, status, sizeof(int32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess)
     rc = CN_ECUDA;
@@ -165,9 +192,8 @@ extern "C" cn_status cn_solve_trees_noalloc(int32_t n_trees, int64_t n_nodes, co
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   // The status word must start at zero; the diagonal is fully overwritten.
   if (cudaMemsetAsync(status, 0, sizeof(int32_t), st) != cudaSuccess) return CN_ECUDA;
-  const int tb = 128;
-  cn::k_solve_trees<<<(n_trees + tb - 1) / tb, tb, 0, st>>>(n_trees, offset, parent, a, b, d, rhs, x, dd, status);
-  if (cudaGetLastError() != cudaSuccess) return CN_ECUDA;
+  if (cn::launch_solve(n_trees, n_nodes, offset, parent, a, b, d, rhs, x, dd, status, st) != cudaSuccess)
+    return CN_ECUDA;
   int32_t h = 0;
   if (cudaMemcpyAsync(&h, status, sizeof(int32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess) return CN_ECUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return CN_ECUDA;

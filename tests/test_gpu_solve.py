@@ -71,3 +71,48 @@ def test_solve_trees_rejects_bad_parent(cn):
     with pytest.raises(cn.CNError) as e:
         cn.cn_solve_trees(off, parent, np.zeros(3), np.zeros(3), np.ones(3), np.ones(3))
     assert e.value.status == cn.CN_EINVAL
+
+
+@pytest.mark.parametrize("off", [[0, 3, 7],       # last offset past the 6 rows
+                                 [0, 4, 2, 6],    # a descending offset (overlapping ranges)
+                                 [1, 3, 6]])      # does not start at row 0
+def test_solve_trees_rejects_bad_offsets(cn, off):
+    """Offsets that disagree with n_nodes are refused before any row is
+    touched (every index stays inside the six-row arrays)."""
+    off = np.array(off, np.int32)
+    parent = np.array([-1, 0, 1, -1, 0, 1], np.int32)
+    with pytest.raises(cn.CNError) as e:
+        cn.cn_solve_trees(off, parent, np.full(6, -0.5), np.full(6, -0.5), np.full(6, 3.0), np.ones(6))
+    assert e.value.status == cn.CN_EINVAL
+
+
+def _pivot_sweep():
+    rng = np.random.default_rng(11)
+    e = np.arange(-1021, 1021)
+    p2 = np.ldexp(1.0, e)
+    vals = [
+        np.exp2(rng.uniform(-1021.0, 1021.0, 400_000)),           # the whole claimed range
+        rng.uniform(1.0, 100.0, 400_000),                          # pivots of the cable matrix
+        p2, np.nextafter(p2, 0.0), np.nextafter(p2, np.inf),       # powers of two and neighbours
+        np.ldexp(2.0 - 2.0 ** -52, e[:-1]),                        # mantissa of all ones
+        np.ldexp(1.0 + rng.integers(0, 2 ** 20, 100_000) * 2.0 ** -20, rng.integers(-1021, 1020, 100_000)),
+        np.array([2.0 ** -1021, 2.0 ** 1021, np.nextafter(2.0 ** 1021, 0.0), 1.0, 3.0, 1.0 + 2 ** -52]),
+    ]
+    d = np.concatenate(vals)
+    return d[(d >= 2.0 ** -1021) & (d <= 2.0 ** 1021)]
+
+
+def test_pivot_reciprocal_within_one_ulp_of_ieee(cn):
+    """The interval kernel's Newton-Raphson reciprocal (float seed, fixed-point
+    step, FP64 step) against IEEE 1/d (numpy, correctly rounded) over the
+    range the solve relies on, [2^-1021, 2^1021]: never more than 1 ulp off,
+    and exactly rounded in most cases."""
+    d = _pivot_sweep()
+    got = cn.cn_pivot_reciprocal(d)
+    ref = 1.0 / d
+    assert np.all(np.isfinite(got)) and np.all(got > 0)
+    ulps = np.abs(got.view(np.int64) - ref.view(np.int64))
+    exact = float(np.mean(ulps == 0))
+    print(f"pivot reciprocal: {d.size} values, exact {exact:.5f}, max {ulps.max()} ulp")
+    assert ulps.max() <= 1
+    assert exact >= 0.99

@@ -469,6 +469,75 @@ def test_calcium_decay_step():
     assert abs(m.cai()[0] - cai1) < 1e-15
 
 
+def test_kca_gate_relaxes_exponentially_at_fixed_calcium():
+    """KCa alone (no CAHVA, so nothing changes [Ca]i): the gate starts at its
+    steady state of the initial 5e-5 mM; after [Ca]i is moved to 2e-3 mM its
+    rates are fixed, alpha = A cai/(cai+kd) and beta = B, and cnexp gives
+    x(t) = x_inf + (x0 - x_inf) exp(-t (alpha+beta)) exactly.  A wrong alpha
+    form, a dropped kd or a swapped alpha/beta fails it."""
+    sc, p = _one_node("kca", 0.01, -65.0, 1e6, -30.0, tstop=2.0)
+    m = OracleModel(sc)
+    c0, c1 = 5e-5, 2e-3
+    m.set_cai(c1)
+    m.run(sc.nsteps, nthreads=1)
+    a0 = p["A"] * c0 / (c0 + p["kd"])
+    a1 = p["A"] * c1 / (c1 + p["kd"])
+    x0, xi = a0 / (a0 + p["B"]), a1 / (a1 + p["B"])
+    ref = xi + (x0 - xi) * math.exp(-sc.nsteps * sc.dt * (a1 + p["B"]))
+    assert abs(x0 - xi) > 0.1
+    assert abs(m.state("kca", 0)[0] - ref) < 1e-12
+    assert np.all(m.cai() == c1)
+
+
+def test_kca_reads_the_calcium_of_the_new_step():
+    """CAHVA and KCa on one compartment, two steps by hand.  Step k: the
+    currents use the gates of step k (ica_k = g_ca,k (v_k - eca)); the solve
+    gives v_{k+1}; CAHVA's gates move at v_{k+1}; [Ca]i moves with the drive
+    of ica_k; then the KCa gate moves with alpha at the NEW [Ca]i.  Reading
+    [Ca]i before its update would leave the KCa gate at its steady state
+    after the first step (it starts there), which this test rejects."""
+    v0, gp, ep = -10.0, 1e-4, -70.0
+    sc, pc = _one_node("cahva", 0.02, v0, gp, ep, tstop=0.05)
+    pk = _channel_params("kca", 0.01)
+    sc.mechs.append(MechTable("kca", np.array([0], np.int32), {k: np.array([pk[k]]) for k in MECH_PARAMS["kca"]}))
+    m = simulate(sc, nthreads=1)
+    assert sc.nsteps == 2
+    dt, cdt, F = sc.dt, 1e-3 * 1.0 / sc.dt, 96485.3321
+    gm = tuple(pc[f"m_{q}"] for q in ["A", "vh", "k", "B", "vh2", "k2"])
+    gh = tuple(pc[f"h_{q}"] for q in ["A", "vh", "k", "B", "vh2", "k2"])
+
+    def relax(x, al, be):                      # exact solution at fixed rates over dt
+        xi = al / (al + be)
+        return xi + (x - xi) * math.exp(-dt * (al + be))
+
+    def steady(g, v):
+        a, b = _gate_rates(g, v)
+        return a / (a + b)
+
+    def kca_alpha(c):
+        return pk["A"] * c / (c + pk["kd"])
+
+    v, cai = v0, pc["cainf"]
+    xm, xh = steady(gm, v0), steady(gh, v0)
+    xk = kca_alpha(cai) / (kca_alpha(cai) + pk["B"])
+    xk0 = xk
+    for _ in range(2):
+        gca = pc["gbar"] * xm * xm * xh
+        gk = pk["gbar"] * xk
+        ica = gca * (v - pc["erev"])
+        v1 = (cdt * v + gp * ep + gca * pc["erev"] + gk * pk["erev"]) / (cdt + gp + gca + gk)
+        xm, xh = relax(xm, *_gate_rates(gm, v1)), relax(xh, *_gate_rates(gh, v1))
+        drive = max(0.0, -1e4 * ica / (2 * F * pc["depth"]))
+        target = pc["cainf"] + drive * pc["taur"]
+        cai = target + (cai - target) * math.exp(-dt / pc["taur"])
+        xk = relax(xk, kca_alpha(cai), pk["B"])
+        v = v1
+    assert abs(xk - xk0) > 1e-9 * xk0                 # the step really moved the gate
+    assert abs(m.state("kca", 0)[0] - xk) < 1e-13 * max(1.0, xk)
+    assert abs(m.cai()[0] - cai) < 1e-11 * cai          # 1 - exp(-dt/taur) cancels ~3.5 digits
+    assert abs(m.v()[0] - v) < 1e-11
+
+
 # ---------------------------------------------------------------- adjoint
 def test_oracle_adjoint_matches_central_differences():
     """The discrete adjoint (reverse Hines solve + HH gate Jacobians, with

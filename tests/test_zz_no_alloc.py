@@ -60,3 +60,30 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(cn):
     st = cn.lib().cn_solve_trees_noalloc(1, (1 << 20) + 1, C.c_void_p(16), C.c_void_p(16), C.c_void_p(16),
                                          C.c_void_p(16), C.c_void_p(16), C.c_void_p(16), C.c_void_p(16), None)
     assert st == cn.CN_ERANGE
+
+
+def test_noalloc_reports_device_errors_and_recovers(cn):
+    """A bad parent gives CN_EINVAL and a zero pivot CN_ERANGE (both found on
+    the device); a valid solve right after each on the same stream succeeds
+    with the right answer, so the shared status word does not carry an error
+    into the next call.  Every index stays inside the arrays."""
+    off, parent, a, b, d, r = random_trees(3, 40, 60)
+    ref = cn.cn_solve_trees(off, parent, a, b, d, r)
+    bad_parent = np.array([-1, 0, 2], np.int32)           # parent[2] = 2 is not < 2
+    with pytest.raises(cn.CNError) as e:
+        cn.cn_solve_trees_noalloc(np.array([0, 3], np.int32), bad_parent, np.zeros(3), np.zeros(3),
+                                  np.ones(3), np.ones(3))
+    assert e.value.status == cn.CN_EINVAL
+    got = cn.cn_solve_trees_noalloc(off, parent, a, b, d, r)
+    assert np.max(np.abs(got - ref) / np.maximum(1.0, np.abs(ref))) <= REL_TOL
+    with pytest.raises(cn.CNError) as e:                   # leaf pivot 0
+        cn.cn_solve_trees_noalloc(np.array([0, 2], np.int32), np.array([-1, 0], np.int32),
+                                  np.array([0.0, -1.0]), np.array([0.0, -1.0]), np.array([2.0, 0.0]),
+                                  np.ones(2))
+    assert e.value.status == cn.CN_ERANGE
+    with pytest.raises(cn.CNError) as e:                   # offsets past n_nodes
+        cn.cn_solve_trees_noalloc(np.array([0, 2, 5], np.int32), np.array([-1, 0, -1, 0], np.int32),
+                                  np.full(4, -0.5), np.full(4, -0.5), np.full(4, 3.0), np.ones(4))
+    assert e.value.status == cn.CN_EINVAL
+    got = cn.cn_solve_trees_noalloc(off, parent, a, b, d, r)
+    assert np.max(np.abs(got - ref) / np.maximum(1.0, np.abs(ref))) <= REL_TOL
