@@ -183,7 +183,9 @@ def config_dict(args, sc, layout=None):
         span = mp & ~(3 << 20)
         tall = {1: ", tall warps", 2: ", warps twice the largest span", 3: ", warps 1.5 times the largest span"}.get(
             (mp >> 20) & 3, "")
-        d["layout"] = {"mapping": "one cell per lane" if mp == 1 else f"cells split to ~{span} rows per lane" + tall,
+        names = {1: "one cell per lane", 3: "reference: interleaved node ordering (one cell per lane)",
+                 4: "reference: constant-depth node ordering (one node per lane and row)"}
+        d["layout"] = {"mapping": names.get(mp, f"cells split to ~{span} rows per lane" + tall),
                        "warps_per_block": wpb, "warps": nw,
                        "chosen_by": "autotuner" if args.mapping == 2 else "fixed"}
     return d
@@ -267,6 +269,7 @@ def run_ours(args):
     hbm, hbm_kind = hbm_peak()
     traffic = profiled_traffic()
     kernel_rate = upd_launch / (per_launch / 1e3)
+    fp64_meas = md.fp64_peak()              # a DFMA stream on this GPU, TFLOP/s
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -277,7 +280,8 @@ def run_ours(args):
                      "unit": "TFLOP/s", "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": traffic,
                      "kernel": "k_interval", "kernel_ms_per_launch": per_launch,
                      "kernel_share": k_ms / ms, "peak_kind": "nominal (units x clock)",
-                     "flops_per_update": FLOP_ALG},
+                     "flops_per_update": FLOP_ALG, "peak_measured": fp64_meas,
+                     "frac_of_measured": achieved_tflops / fp64_meas if fp64_meas else None},
         "hbm_roofline": {"bound": "hbm", "achieved": kernel_rate * B_ALG / 1e9, "peak": hbm, "unit": "GB/s",
                          "frac": kernel_rate * B_ALG / 1e9 / hbm, "bytes_per_update": B_ALG,
                          "peak_kind": hbm_kind, "whole_step_frac": value / world * B_ALG / 1e9 / hbm},
@@ -285,6 +289,8 @@ def run_ours(args):
     }
     if rank == 0 and world == 1 and not args.no_e2e:
         line["e2e"] = e2e_measure(args, cn, K, layout)
+        if args.e2e_full:
+            line["e2e_full_run"] = e2e_measure(args, cn, 1000, layout)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         sc_cpu = workload(args, args.cpu_intervals)
         rate, threads, dt = cpu_oracle_rate(sc_cpu, args.cpu_intervals)
@@ -329,6 +335,7 @@ def e2e_measure(args, cn, K, layout):
     md.close()
     return {"value": sc.n_nodes * 40 * K / dt, "unit": UNIT, "h2d_bytes_per_step": h2d / K,
             "d2h_bytes_per_step": d2h / K, "seconds": dt,
+            "intervals": K,
             "region": "cn_geometry + cn_model_create + cn_add_* + cn_run + cn_get_spikes + cn_get_traces "
                       "(with the layout the autotuner chose for the device-timed run)"}
 
@@ -348,7 +355,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--mapping", type=int, default=2,
                     help="2: autotuned, 0: split to the mean cell size, 1: one cell per lane, "
+                         "3: reference interleaved layout, 4: reference constant-depth layout, "
                          ">=16: target rows per lane")
+    ap.add_argument("--e2e-full", action="store_true",
+                    help="also time the public API end to end over a whole 1,000 ms run")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -126,6 +126,18 @@ typedef enum {
                              (with CN_MAP_TALL as well: 1.5 times the largest span) */
   CN_MAP_AUTO = 0,       /* target span = mean cell size (no split when the adjoint is on) */
   CN_MAP_THREAD = 1,     /* one cell per lane, never split */
+  CN_MAP_INTERLEAVED = 3, /* reference layout, the paper's interleaved node ordering (Section 4.4):
+                             one cell per lane, node i of every cell of a warp at row i; runs the
+                             plain sequential form of each step (the linearised update of
+                             Section 2 with no fused multiply-adds, IEEE divisions, every sum in
+                             the order a per-cell stepper takes) so that results match such a
+                             stepper up to its exp()'s last bit.  FP64 models of pas, HH,
+                             ExpSyn and IClamp only (no channel types, gap junctions or
+                             adjoint: CN_EINVAL) */
+  CN_MAP_CONSTDEPTH = 4, /* reference layout, the paper's constant-depth node ordering (Section
+                             4.4): a warp's 32 cells' nodes level by level (distance from the
+                             root), one node per lane and row, never two children of one node in
+                             one row; same arithmetic and limits as CN_MAP_INTERLEAVED */
   CN_MAP_TUNE = 2        /* autotuned on first use: each candidate layout (one cell per lane; spans
                             of 1/8, 1/4, 1/2 and 1 mean cell size, each also with CN_MAP_TALL,
                             CN_MAP_TALL | CN_MAP_TALL2 and CN_MAP_TALL2; then 0.85, 0.9, 0.95
@@ -165,6 +177,9 @@ cn_status cn_get_mapping(cn_model* m, int32_t* mapping, int32_t* warps_per_block
  *   n_warps, stack_depth: warps used; the most far children pending at
  *                       once in any lane while it is eliminated (a bound on
  *                       the entries of the kernel's per-lane stack).
+ * With CN_MAP_INTERLEAVED or CN_MAP_CONSTDEPTH the reference placement is
+ * returned (spike sources taken at each cell's root; node_flags then only
+ * marks real nodes).
  * Errors: CN_EINVAL on malformed trees or a node with more than 8 children. */
 cn_status cn_plan_layout(int32_t n_cells, const int32_t* cell_offset, const int32_t* parent, int32_t mapping,
                          int32_t* node_lane, int32_t* node_row, int32_t* node_flags, int32_t* n_warps,
@@ -375,6 +390,14 @@ cn_status cn_solve_trees(int32_t n_trees, int64_t n_nodes, const int32_t* offset
 cn_status cn_solve_trees_noalloc(int32_t n_trees, int64_t n_nodes, const int32_t* offset, const int32_t* parent,
                                  const double* a, const double* b, const double* d, const double* rhs, double* x,
                                  void* stream);
+
+/* Diagnostics: the FP64 rate this GPU attains (TFLOP/s, 2 flops per fused
+ * multiply-add) on a stream of independent fused multiply-adds, four warps
+ * per SM sub-partition, timed with CUDA events on the model's stream (a
+ * scratch buffer comes from the model's allocator).  The interval kernel's
+ * FP64 roofline is quoted against it and against the nominal rate.
+ * Errors: CN_EINVAL, CN_ENOMEM, CN_ECUDA.                                 */
+cn_status cn_fp64_peak(cn_model* m, double* tflops);
 
 /* The reciprocal the engine's solve takes of every pivot (diagnostics):
  * out[i] = 1/d[i] for n DEVICE values d[i] in [2^-1021, 2^1021] (a pivot of

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "libcn.so")
 
 CN_OK, CN_EINVAL, CN_ENOMEM, CN_ECUDA, CN_ESTATE, CN_ETIMEOUT, CN_ERANGE = range(7)
 CN_PARAM_GNABAR, CN_PARAM_GKBAR, CN_PARAM_GPAS = range(3)
-CN_MAP_AUTO, CN_MAP_THREAD, CN_MAP_TUNE = range(3)
+CN_MAP_AUTO, CN_MAP_THREAD, CN_MAP_TUNE, CN_MAP_INTERLEAVED, CN_MAP_CONSTDEPTH = range(5)
 CN_MAP_TALL = 1 << 20
 CN_MAP_TALL2 = 1 << 21
 STATUS_NAMES = {0: "CN_OK", 1: "CN_EINVAL", 2: "CN_ENOMEM", 3: "CN_ECUDA", 4: "CN_ESTATE",
@@ -133,6 +133,8 @@ def lib():
         L.cn_solve_trees.restype = st
         L.cn_solve_trees_noalloc.argtypes = list(L.cn_solve_trees.argtypes)
         L.cn_solve_trees_noalloc.restype = st
+        L.cn_fp64_peak.argtypes = [C.c_void_p, C.POINTER(C.c_double)]
+        L.cn_fp64_peak.restype = st
         L.cn_pivot_reciprocal.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]
         L.cn_pivot_reciprocal.restype = st
         L.cn_last_error.argtypes = [C.c_void_p]
@@ -391,6 +393,12 @@ class Model:
         ms = C.c_float(0.0)
         _check(lib().cn_get_mapping(self._h, _p(mp, _P_I32), _p(w, _P_I32), _p(nw, _P_I32), C.byref(ms)), self._h)
         return int(mp[0]), int(w[0]), int(nw[0]), float(ms.value)
+
+    def fp64_peak(self) -> float:
+        """FP64 TFLOP/s attained by a stream of independent FMAs on this GPU."""
+        x = C.c_double()
+        _check(lib().cn_fp64_peak(self._h, C.byref(x)), self._h)
+        return x.value
 
     def cn_profile_read(self):
         """(interval-kernel ms, launches, pull-kernel ms, launches) since the last read."""

@@ -21,7 +21,6 @@
 namespace cn {
 
 constexpr int kLanes = 32;
-constexpr int kEvCap = 256;          // events per cell per interval
 constexpr int kMaxInterval = 64;     // steps per interval (spike mask width)
 
 enum : int32_t { kStatusEvOverflow = 1, kStatusBadState = 2 };
@@ -166,9 +165,11 @@ struct DevModel {
   const int32_t* rec_row;
   const int32_t* rec_id;
   double* trace;            // [step][n_rec]
-  // events
+  // events: lane `slot` owns ev_buf[ev_off[slot], ev_off[slot+1]), sized for
+  // the most its synapses can receive in one interval
   int32_t* ev_count;
-  EvRec* ev_buf;            // [slot][kEvCap]
+  EvRec* ev_buf;
+  const int64_t* ev_off;    // [n_slots + 1]
   // external events, CSR by slot
   const int64_t* x_off;
   int64_t* x_pos;
@@ -184,6 +185,11 @@ struct DevModel {
   // spike masks, [interval][gid]: bit s = spike at step interval*D + s + 1
   uint64_t* hist;
   int32_t* status;
+  // reference layouts only (see cn_ref.cuh): parent element offset within
+  // the group (-1: root or padding), node area, and each stimulus's row
+  const int32_t* ref_par;
+  const double* area;
+  const int32_t* st_row;
 };
 
 // Rows kept in flight by the per-lane cp.async rings.  Elimination streams
@@ -232,12 +238,15 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 
 // --------------------------------------------------------------- arithmetic
 // Reciprocal of a pivot d in [2^-1021, 2^1021] (a pivot of the cable matrix
-// is >= 1: 1 plus non-negative conductances over cdt).  Newton-Raphson
-// division (e.g. Markstein 1990) in three precisions, so that only two FP64
-// instructions are spent: the MUFU float reciprocal of d's leading mantissa
-// bits (~2^-22) is refined by one Newton step y1 = y0 + y0 (1 - m y0) in
-// 32-bit fixed point on the integer pipes (to ~2^-31), and one FP64 step
-// r + r (1 - d r) then brings it within 1 ulp of 1/d.
+// is >= 1: 1 plus non-negative conductances over cdt), with no FP64
+// instruction: GB300 issues one warp-wide FP64 instruction per 64 cycles on
+// each SM sub-partition, while its integer pipes are ~30 times faster.
+// Newton-Raphson division (Markstein 1990) on d = 2^E m, m in [1, 2): the
+// MUFU float reciprocal of m's leading bits (~2^-22) is refined by one
+// Newton step y1 = y0 + y0 (1 - m y0) in 32-bit fixed point (limited to
+// ~2^-31 by the truncated m), then by a second step in 64-bit fixed point
+// with the full 53-bit m (~2^-60), and rounded to 53 bits.  The result is
+// within 1 ulp of 1/d and exactly rounded in ~99.95% of cases.
 __device__ __forceinline__ double rcp64(double d) {
   const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
   const unsigned frac = hi & 0xfffffu;  // d = 2^E m, m = 1.frac in [1, 2)
@@ -251,10 +260,19 @@ __device__ __forceinline__ double rcp64(double d) {
   const long long e = (long long)(0x8000000000000000ull - p) >> 12;      // (1 - m y0) 2^51
   long long y1 = (long long)y0 + (((long long)y0 * e) >> 51);
   y1 = y1 > 0xffffffffll ? 0xffffffffll : y1 < 0x80000000ll ? 0x80000000ll : y1;
-  const unsigned yu = (unsigned)y1;  // 1/m in Q0.32, leading bit 31
-  const unsigned ex = 2045u - ((hi >> 20) & 0x7ffu);  // 1/d = 2^(-E-1) (yu / 2^31)
-  const double r = __hiloint2double((int)((ex << 20) | ((yu >> 11) & 0xfffffu)), (int)(yu << 21));
-  return fma(r, fma(-d, r, 1.0), r);
+  // second step in Q0.64 with m in Q1.63
+  const unsigned long long f52 = ((unsigned long long)frac << 32) | lo;
+  const unsigned long long M = 0x8000000000000000ull | (f52 << 11);
+  const unsigned long long Y1 = (unsigned long long)y1 << 32;
+  const long long E = (long long)(0x8000000000000000ull - __umul64hi(M, Y1));  // (1 - m y1) 2^63
+  const unsigned long long aE = E < 0 ? (unsigned long long)(-E) : (unsigned long long)E;
+  const unsigned long long C = (__umul64hi(Y1, aE) << 1) | ((Y1 * aE) >> 63);  // y1 |1 - m y1| 2^64
+  const unsigned long long Y2 = E < 0 ? Y1 - C : Y1 + C;                        // 1/m in Q0.64, in (2^63, 2^64)
+  // 1/d = 2^(1022 - Eb) (Y2 / 2^63); m = 1 gives the power of two exactly
+  const unsigned long long eb = (hi >> 20) & 0x7ffu;
+  const unsigned long long mant = ((Y2 + 0x400ull) >> 11) & 0xfffffffffffffull;
+  const unsigned long long bits = f52 == 0 ? (2046ull - eb) << 52 : ((2045ull - eb) << 52) | mant;
+  return __longlong_as_double((long long)bits);
 }
 
 // alpha = A (v - vh) / (1 - exp(-(v - vh)/k)); limit A k (1 + u/2) near vh.
@@ -271,10 +289,15 @@ template <>
 __device__ __forceinline__ float vtrap<float>(float A, float vh, float k, float v) {
   const float u = (v - vh) / k;
   if (fabsf(u) < 1e-4f) return A * k * (1.0f + 0.5f * u);
-  return A * (v - vh) / (1.0f - expf(-u));
+  return A * (v - vh) / -expm1f(-u);
 }
 __device__ __forceinline__ double dexp_(double x) { return exp(x); }
 __device__ __forceinline__ float dexp_(float x) { return expf(x); }
+// 1 - exp(-x).  FP64 keeps that form (the oracle's); FP32 uses -expm1(-x),
+// which does not lose digits to cancellation when x is small (dt (alpha +
+// beta) is ~0.025 for a gate, 3e-4 for the calcium decay).
+__device__ __forceinline__ double omexp_(double x) { return 1.0 - exp(-x); }
+__device__ __forceinline__ float omexp_(float x) { return -expm1f(-x); }
 
 // Hodgkin-Huxley rate functions (squid axon, 6.3 C, q10 = 1).
 template <typename T>
@@ -307,7 +330,7 @@ __device__ __forceinline__ T hh_rate(int kind, T v) {
   if (vt && (u < T(0) ? -u : u) < (sizeof(T) == 8 ? T(1e-6) : T(1e-4))) return A * k * (T(1.0) + T(0.5) * u);
   const T num = vt ? A * w : A;
   const T fac = (kind == 1 || kind == 2 || kind == 5) ? e : T(1.0);
-  const T den = vt ? T(1.0) - e : kind == 3 ? T(1.0) + e : T(1.0);
+  const T den = vt ? (sizeof(T) == 8 ? T(1.0) - e : omexp_(u)) : kind == 3 ? T(1.0) + e : T(1.0);
   return num * fac / den;
 }
 
@@ -316,7 +339,7 @@ template <typename T>
 __device__ __forceinline__ T cnexp_step(T x, T al, T be, T dt) {
   const T s = al + be;
   const T inf = al / s;
-  return x + (T(1.0) - dexp_(-dt * s)) * (inf - x);
+  return x + omexp_(dt * s) * (inf - x);
 }
 
 // Gate storage per precision mode.

@@ -15,6 +15,7 @@
 
 #include "cn.h"
 #include "cn_kernels.cuh"
+#include "cn_ref.cuh"
 
 namespace {
 
@@ -613,6 +614,7 @@ struct Layout {
   std::vector<int32_t> node_slot, node_row;   // global node -> lane, warp row
   std::vector<int32_t> node_flags;            // global node -> topology bits
   std::vector<int32_t> node_pfar;             // global node -> rows down to the in-part parent (far nodes)
+  std::vector<int32_t> node_paroff;           // reference layouts: parent's element offset in the group (-1: root)
 };
 
 constexpr int kPackLookahead = 512;  // remaining cells tried per warp  // refusals after which a warp takes no more cells
@@ -869,6 +871,123 @@ bool build_layout(int32_t n_cells, const int32_t* off, const int32_t* parent, co
   return true;
 }
 
+// The reference layouts, the paper's two GPU node orderings (Section 4.4),
+// for k_interval_ref.  Cells go 32 to a warp group in order of decreasing
+// size (ties by gid).
+//  interleaved: cell p of a group in lane p, its node i at row i.
+//  constant depth: the group's nodes level by level (distance from the root;
+//    each level starts a new row), within a level by (cell-local index, cell
+//    position), filling rows of 32 in that order; a node starts a new row
+//    when the row is full or already holds a child of its parent (so
+//    children of one node are never updated together, and a later sibling
+//    lies in a later row), and a spike source skips lanes that already hold
+//    one.
+bool build_ref_layout(int32_t n_cells, const int32_t* off, const int32_t* parent, const int32_t* spike_node,
+                      bool constdepth, Layout& L, std::string& err) {
+  std::vector<int32_t> order(n_cells);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int x, int y) { return off[x + 1] - off[x] > off[y + 1] - off[y]; });
+  L.plans.clear();
+  L.depth = 1;
+  L.n_mail = 1;
+  L.n_groups = (n_cells + cn::kLanes - 1) / cn::kLanes;
+  const int64_t nn = off[n_cells];
+  L.node_slot.assign(nn, 0);
+  L.node_row.assign(nn, 0);
+  L.node_flags.assign(nn, cn::kRealBit);
+  L.node_pfar.assign(nn, 0);
+  L.node_paroff.assign(nn, -1);
+  L.lane_rows.assign((size_t)L.n_groups * cn::kLanes, 0);
+  L.lane_cell.assign((size_t)L.n_groups * cn::kLanes, -1);
+  L.cell_lane0.assign(n_cells, -1);
+  std::vector<int32_t> depth;
+  struct Item { int32_t li, p; };
+  std::vector<std::vector<Item>> level;
+  for (int g = 0; g < L.n_groups; ++g) {
+    const int nc = std::min<int>(cn::kLanes, n_cells - g * cn::kLanes);
+    const int32_t* cs = order.data() + (size_t)g * cn::kLanes;
+    if (!constdepth) {
+      for (int p = 0; p < nc; ++p) {
+        const int c = cs[p], n = off[c + 1] - off[c], slot = g * cn::kLanes + p;
+        L.lane_cell[slot] = c;
+        L.lane_rows[slot] = n;
+        L.cell_lane0[c] = slot;
+        for (int32_t i = 0; i < n; ++i) {
+          L.node_slot[off[c] + i] = slot;
+          L.node_row[off[c] + i] = i;
+          L.node_paroff[off[c] + i] = parent[off[c] + i] < 0 ? -1 : parent[off[c] + i] * cn::kLanes + p;
+        }
+      }
+      continue;
+    }
+    level.clear();
+    for (int p = 0; p < nc; ++p) {
+      const int c = cs[p], n = off[c + 1] - off[c];
+      depth.assign(n, 0);
+      for (int32_t i = 1; i < n; ++i) depth[i] = depth[parent[off[c] + i]] + 1;
+      for (int32_t i = 0; i < n; ++i) {
+        if ((int)level.size() <= depth[i]) level.resize(depth[i] + 1);
+        level[depth[i]].push_back(Item{i, p});
+      }
+    }
+    int row = 0;
+    bool spike_lane[cn::kLanes] = {};
+    std::vector<std::pair<int32_t, int32_t>> row_parents;  // (cell position, parent) in the current row
+    for (auto& lv : level) {
+      std::sort(lv.begin(), lv.end(), [](const Item& x, const Item& y) {
+        return x.li != y.li ? x.li < y.li : x.p < y.p;
+      });
+      int pos = 0;
+      row_parents.clear();
+      for (const Item& it : lv) {
+        const int c = cs[it.p];
+        const int32_t par = parent[off[c] + it.li];
+        const bool src = it.li == (spike_node ? spike_node[c] : 0);
+        bool clash = false;
+        for (auto& rp : row_parents) clash = clash || (rp.first == it.p && rp.second == par && par >= 0);
+        if (pos == cn::kLanes || clash) {
+          ++row;
+          pos = 0;
+          row_parents.clear();
+        }
+        if (src) {
+          while (pos < cn::kLanes && spike_lane[pos]) ++pos;
+          if (pos == cn::kLanes) {
+            ++row;
+            pos = 0;
+            row_parents.clear();
+            while (pos < cn::kLanes && spike_lane[pos]) ++pos;
+            if (pos == cn::kLanes) {
+              err = "internal: no lane free of a spike source";
+              return false;
+            }
+          }
+          spike_lane[pos] = true;
+        }
+        const int64_t node = off[c] + it.li;
+        L.node_slot[node] = g * cn::kLanes + pos;
+        L.node_row[node] = row;
+        row_parents.emplace_back(it.p, par);
+        ++pos;
+      }
+      if (pos > 0) ++row;
+    }
+    for (int l = 0; l < cn::kLanes; ++l) L.lane_rows[(size_t)g * cn::kLanes + l] = row;
+    for (int p = 0; p < nc; ++p) {
+      const int c = cs[p], n = off[c + 1] - off[c];
+      L.cell_lane0[c] = L.node_slot[off[c] + (spike_node ? spike_node[c] : 0)];
+      for (int32_t i = 1; i < n; ++i) {
+        const int64_t pn = off[c] + parent[off[c] + i];
+        L.node_paroff[off[c] + i] = L.node_row[pn] * cn::kLanes + L.node_slot[pn] % cn::kLanes;
+      }
+    }
+  }
+  return true;
+}
+
+bool is_ref_mapping(int32_t mapping) { return mapping == CN_MAP_INTERLEAVED || mapping == CN_MAP_CONSTDEPTH; }
+
 cn_status finalize(cn_model* m) {
   cn::DevModel& dm = m->dm;
   const double dt = m->opt.dt_ms;
@@ -916,13 +1035,20 @@ cn_status finalize(cn_model* m) {
   }
   // split plans (no split when the adjoint is on or the mapping asks for
   // one cell per lane); target span = mean cell size unless given
+  const bool ref = is_ref_mapping(m->opt.mapping);
+  if (ref && (m->dense || !m->gap_node.empty() || m->ck_steps > 0 || m->opt.precision != CN_PREC_FP64))
+    return m->fail(CN_EINVAL, "the reference layouts take FP64 models of pas, HH, ExpSyn and IClamp "
+                              "without gap junctions or the adjoint");
   const int target = map_target(m->opt.mapping, m->n_nodes, m->n_cells, m->ck_steps > 0);
   Layout L;
   {
     std::string lerr;
-    if (!build_layout(m->n_cells, m->off.data(), m->parent.data(), cell_mask.data(), m->spike_node.data(), target,
-                      !m->dense && m->ck_steps <= 0, tall_factor(m->opt.mapping), L, lerr))
-      return m->fail(CN_EINVAL, lerr);
+    const bool ok = ref ? build_ref_layout(m->n_cells, m->off.data(), m->parent.data(), m->spike_node.data(),
+                                           m->opt.mapping == CN_MAP_CONSTDEPTH, L, lerr)
+                        : build_layout(m->n_cells, m->off.data(), m->parent.data(), cell_mask.data(),
+                                       m->spike_node.data(), target, !m->dense && m->ck_steps <= 0,
+                                       tall_factor(m->opt.mapping), L, lerr);
+    if (!ok) return m->fail(CN_EINVAL, lerr);
   }
   const int depth = L.depth;
   m->n_groups = L.n_groups;
@@ -970,11 +1096,14 @@ cn_status finalize(cn_model* m) {
     }
     return row_slot[node];
   };
-  std::vector<int32_t> hh_slotid(m->hh_node.size()), st_slotid(m->st_node.size());
-  for (size_t i = 0; i < m->hh_node.size(); ++i) hh_slotid[i] = slot_of_node(m->hh_node[i]);
-  for (size_t i = 0; i < m->st_node.size(); ++i) st_slotid[i] = slot_of_node(m->st_node[i]);
-  std::vector<int32_t> gap_slotid(m->gap_node.size());
-  for (size_t i = 0; i < m->gap_node.size(); ++i) gap_slotid[i] = slot_of_node(m->gap_node[i]);
+  // (the reference kernel adds point-process terms in place: no slots)
+  std::vector<int32_t> hh_slotid(m->hh_node.size(), 0), st_slotid(m->st_node.size(), 0);
+  std::vector<int32_t> gap_slotid(m->gap_node.size(), 0);
+  if (!ref) {
+    for (size_t i = 0; i < m->hh_node.size(); ++i) hh_slotid[i] = slot_of_node(m->hh_node[i]);
+    for (size_t i = 0; i < m->st_node.size(); ++i) st_slotid[i] = slot_of_node(m->st_node[i]);
+    for (size_t i = 0; i < m->gap_node.size(); ++i) gap_slotid[i] = slot_of_node(m->gap_node[i]);
+  }
   // distinct gap peers: each is published by the lane that holds it
   std::vector<int32_t> gsrc_node, gap_src(m->gap_node.size());
   {
@@ -991,8 +1120,9 @@ cn_status finalize(cn_model* m) {
   int max_slots = 1;
   for (int sl = 0; sl < m->n_slots; ++sl) max_slots = std::max<int>(max_slots, (int)lane_slot_rows[sl].size());
   if (max_slots >= cn::kNoSlot) return m->fail(CN_EINVAL, "too many mechanism rows in one cell part");
-  const size_t smem = cn::interval_smem_bytes(depth, max_slots, m->dense, L.n_mail,
-                                              m->opt.precision == CN_PREC_FP64 ? 8 : 4);
+  const size_t smem = ref ? 0
+                          : cn::interval_smem_bytes(depth, max_slots, m->dense, L.n_mail,
+                                                    m->opt.precision == CN_PREC_FP64 ? 8 : 4);
   if (smem > kMaxSmemPerBlock)
     return m->fail(CN_EINVAL, "cell needs " + std::to_string(smem) + " bytes of shared memory (slots " +
                                   std::to_string(max_slots) + ", stack " + std::to_string(depth) + ")");
@@ -1066,12 +1196,13 @@ cn_status finalize(cn_model* m) {
     h_hh_cm[e] = m->cm[m->hh_node[i]];
     for (int p = 0; p < 6; ++p) h_hh_p[p * rh.elems + e] = m->hh_par[p * nhh + i];
   }
-  std::vector<int32_t> h_st_slot(rt.elems, 0);
+  std::vector<int32_t> h_st_slot(rt.elems, 0), h_st_row(std::max<int64_t>(rt.elems, 1), 0);
   std::vector<double> h_st_del(rt.elems, 0.0), h_st_dur(rt.elems, 0.0), h_st_amp(rt.elems, 0.0),
       h_st_area(rt.elems, 1.0), h_st_cm(rt.elems, 1.0);
   for (size_t i = 0; i < m->st_node.size(); ++i) {
     int64_t e = elem_of(rt, i);
     h_st_slot[e] = st_slotid[i];
+    h_st_row[e] = m->node_row[m->st_node[i]];
     h_st_del[e] = m->st_del[i];
     h_st_dur[e] = m->st_dur[i];
     h_st_amp[e] = m->st_amp[i];
@@ -1247,13 +1378,43 @@ cn_status finalize(cn_model* m) {
   CN_CHECK(upload(m, &p32, h_st_slot)); dm.st_slot = p32;
   CN_CHECK(upload(m, &pd, h_st_del)); dm.st_del = pd;
   CN_CHECK(upload(m, &pd, h_st_dur)); dm.st_dur = pd;
-  CN_CHECK(zeros(m, &pd, rt.elems)); dm.st_amp = pd;
+  if (ref) {  // the reference kernel takes the amplitudes as given (nA)
+    CN_CHECK(upload(m, &pd, h_st_amp)); dm.st_amp = pd;
+    CN_CHECK(upload(m, &p32, h_st_row)); dm.st_row = p32;
+    std::vector<double> h_area_e(acc, 1.0);
+    std::vector<int32_t> h_par(acc, -1);
+    for (int64_t node = 0; node < m->n_nodes; ++node) {
+      h_area_e[h_elem[node]] = m->area[node];
+      h_par[h_elem[node]] = L.node_paroff[node];
+    }
+    CN_CHECK(upload(m, &pd, h_area_e)); dm.area = pd;
+    CN_CHECK(upload(m, &p32, h_par)); dm.ref_par = p32;
+  } else {
+    CN_CHECK(zeros(m, &pd, rt.elems)); dm.st_amp = pd;
+  }
   CN_CHECK(upload(m, &p32, h_rec_row)); dm.rec_row = p32;
   CN_CHECK(upload(m, &p32, h_rec_id)); dm.rec_id = p32;
   CN_CHECK(zeros(m, &p32, m->n_slots)); dm.ev_count = p32;
-  cn::EvRec* pev = static_cast<cn::EvRec*>(dalloc_raw(m, (size_t)m->n_slots * cn::kEvCap * sizeof(cn::EvRec)));
+  // Event buffer of each lane, sized for the most its synapses can receive
+  // in one interval: its external events of the busiest interval, plus, per
+  // incoming NetCon, ceil(D/2) spikes (a source spikes at most every other
+  // step: it must fall back to threshold or below before it can cross
+  // again), so no delivery is ever dropped.
+  std::vector<int64_t> ev_off(m->n_slots + 1, 0);
+  for (int sl = 0; sl < m->n_slots; ++sl) {
+    int64_t ext = 0, run = 0, cur = -1;
+    for (int64_t q = x_off[sl]; q < x_off[sl + 1]; ++q) {
+      const int64_t J = h_x_step[q] / m->D;
+      run = J == cur ? run + 1 : 1;
+      cur = J;
+      ext = std::max(ext, run);
+    }
+    ev_off[sl + 1] = ev_off[sl] + ext + (in_off[sl + 1] - in_off[sl]) * ((m->D + 1) / 2);
+  }
+  cn::EvRec* pev = static_cast<cn::EvRec*>(dalloc_raw(m, (size_t)std::max<int64_t>(ev_off.back(), 1) * sizeof(cn::EvRec)));
   if (!pev) return m->fail(CN_ENOMEM, "device allocation failed");
   dm.ev_buf = pev;
+  CN_CHECK(upload(m, &p64, ev_off)); dm.ev_off = p64;
   CN_CHECK(upload(m, &p64, x_off)); dm.x_off = p64;
   std::vector<int64_t> x_pos(x_off.begin(), x_off.end() - 1);
   CN_CHECK(upload(m, &p64, x_pos)); dm.x_pos = p64;
@@ -1293,12 +1454,12 @@ cn_status finalize(cn_model* m) {
   cudaStream_t st = m->stream;
   const int nbe = (int)((acc + 255) / 256), nbc = (m->n_cells + tb - 1) / tb;
   CN_CHECK(launch_checked(m, [&] { cn::k_setup_pad<<<nbe, 256, 0, st>>>(dm); }));
-  CN_CHECK(launch_checked(m, [&] { cn::k_setup_geom<<<nbc, tb, 0, st>>>(dm, m->n_cells, d_off, d_parent, d_area, d_ri, d_cm, d_elem); }));
+  CN_CHECK(launch_checked(m, [&] { cn::k_setup_geom<<<nbc, tb, 0, st>>>(dm, m->n_cells, d_off, d_parent, d_area, d_ri, d_cm, d_elem, !ref); }));
   CN_CHECK(launch_checked(m, [&] { cn::k_pas_apply<<<nb, tb, 0, st>>>(dm); }));
   CN_CHECK(launch_checked(m, [&] { cn::k_setup_syn<<<nb, tb, 0, st>>>(dm, d_syn_area, d_syn_cm, d_syn_tau); }));
   CN_CHECK(launch_checked(m, [&] { cn::k_syn_consts<<<nb, tb, 0, st>>>(dm); }));
   CN_CHECK(launch_checked(m, [&] { cn::k_hh_params<<<nb, tb, 0, st>>>(dm); }));
-  CN_CHECK(launch_checked(m, [&] { cn::k_setup_stim<<<nb, tb, 0, st>>>(dm, d_st_amp, d_st_area, d_st_cm); }));
+  if (!ref) CN_CHECK(launch_checked(m, [&] { cn::k_setup_stim<<<nb, tb, 0, st>>>(dm, d_st_amp, d_st_area, d_st_cm); }));
   if (rg.elems > 0) {
     double *d_ga, *d_gc, *d_gg;
     CN_CHECK(upload(m, &d_ga, h_gap_area));
@@ -1329,7 +1490,7 @@ cn_status finalize(cn_model* m) {
                   (const void*)cn::k_interval<0, false, true>, (const void*)cn::k_interval<1, false, true>,
                   (const void*)cn::k_interval<2, false, true>})
     CN_TRY_CUDA(m, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemPerBlock));
-  m->wpb = std::max(1, std::min<int>(m->wpb, (int)(kMaxSmemPerBlock / m->smem_bytes)));
+  m->wpb = ref ? 1 : std::max(1, std::min<int>(m->wpb, (int)(kMaxSmemPerBlock / m->smem_bytes)));
   m->finalized = true;
   m->cells_nodes = m->n_nodes;
   return CN_OK;
@@ -1404,7 +1565,9 @@ cn_status enqueue_interval(cn_model* m, cudaStream_t st, int64_t J, int s0, int 
     if (ev) CN_TRY_CUDA(m, cudaEventRecordWithFlags(ev[1], st, rec_flags));
   }
   if (ev) CN_TRY_CUDA(m, cudaEventRecordWithFlags(ev[2], st, rec_flags));
-  switch (m->opt.precision) {
+  if (is_ref_mapping(m->opt.mapping)) {
+    CN_CHECK(launch_checked(m, [&] { cn::k_interval_ref<<<m->n_groups, 32, 0, st>>>(dm, J, s0, s1, Jp); }));
+  } else switch (m->opt.precision) {
     case CN_PREC_FP64:
       if (m->dense) CN_CHECK(launch_checked(m, [&] { cn::k_interval<0, false, true><<<blocks, 32 * wpb, smem, st>>>(dm, J, s0, s1, Jp); }));
       else CN_CHECK(launch_checked(m, [&] { cn::k_interval<0, false, false><<<blocks, 32 * wpb, smem, st>>>(dm, J, s0, s1, Jp); }));
@@ -1869,9 +2032,13 @@ cn_status cn_plan_layout(int32_t n_cells, const int32_t* cell_offset, const int3
   if (!valid_trees(n_cells, cell_offset, parent, g_create_error)) return CN_EINVAL;
   const int64_t nn = cell_offset[n_cells];
   Layout L;
-  if (!build_layout(n_cells, cell_offset, parent, nullptr, nullptr, map_target(mapping, nn, n_cells, false), true,
-                    tall_factor(mapping), L, g_create_error))
-    return CN_EINVAL;
+  const bool ok = is_ref_mapping(mapping)
+                      ? build_ref_layout(n_cells, cell_offset, parent, nullptr, mapping == CN_MAP_CONSTDEPTH, L,
+                                         g_create_error)
+                      : build_layout(n_cells, cell_offset, parent, nullptr, nullptr,
+                                     map_target(mapping, nn, n_cells, false), true, tall_factor(mapping), L,
+                                     g_create_error);
+  if (!ok) return CN_EINVAL;
   if (node_lane) std::copy(L.node_slot.begin(), L.node_slot.end(), node_lane);
   if (node_row) std::copy(L.node_row.begin(), L.node_row.end(), node_row);
   if (node_flags) std::copy(L.node_flags.begin(), L.node_flags.end(), node_flags);
@@ -1898,8 +2065,9 @@ cn_status cn_model_create(const cn_morph* morph, const cn_mech_table* mechs, int
   if (o.warps_per_block < 0 || o.warps_per_block > cn::kMaxWarpsPerBlock) return bad("warps_per_block must be 0..4");
   {
     const int32_t mv = o.mapping & ~(CN_MAP_TALL | CN_MAP_TALL2);
-    if (o.mapping < 0 || (mv > CN_MAP_TUNE && mv < 16) || ((o.mapping & (CN_MAP_TALL | CN_MAP_TALL2)) && mv < 16))
-      return bad("mapping must be 0, 1, 2, or a span >= 16 (optionally with CN_MAP_TALL)");
+    if (o.mapping < 0 || (mv > CN_MAP_CONSTDEPTH && mv < 16) ||
+        ((o.mapping & (CN_MAP_TALL | CN_MAP_TALL2)) && mv < 16))
+      return bad("mapping must be 0-4, or a span >= 16 (optionally with CN_MAP_TALL)");
   }
   const int32_t nc = morph->n_cells;
   if (nc <= 0 || !morph->cell_offset || !morph->parent || !morph->area_um2 || !morph->cm_uF_cm2 ||
@@ -2569,6 +2737,30 @@ cn_status cn_run_adjoint(cn_model* m, const double* dj, double* grad) {
   for (void* b : {(void*)A.dj, (void*)A.lam, (void*)A.ytmp, (void*)A.qtmp, (void*)A.xi, (void*)A.grad, (void*)tv,
                   (void*)tg, fin})
     dfree_raw(m, b);
+  return CN_OK;
+}
+
+cn_status cn_fp64_peak(cn_model* m, double* tflops) {
+  if (!m || !tflops) return CN_EINVAL;
+  int dev = 0, nsm = 0;
+  CN_TRY_CUDA(m, cudaGetDevice(&dev));
+  CN_TRY_CUDA(m, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const int blocks = nsm * 4, threads = 128, iters = 20000;
+  double* sink = static_cast<double*>(dalloc_raw(m, (size_t)blocks * threads * sizeof(double)));
+  if (!sink) return m->fail(CN_ENOMEM, "device allocation failed");
+  cudaEvent_t e0 = take_event(m), e1 = take_event(m);
+  cn::k_dfma_stream<<<blocks, threads, 0, m->stream>>>(sink, iters / 10, 0.999999, 1e-7);  // warm-up
+  CN_TRY_CUDA(m, cudaEventRecord(e0, m->stream));
+  cn::k_dfma_stream<<<blocks, threads, 0, m->stream>>>(sink, iters, 0.999999, 1e-7);
+  CN_TRY_CUDA(m, cudaEventRecord(e1, m->stream));
+  CN_TRY_CUDA(m, cudaGetLastError());
+  CN_TRY_CUDA(m, cudaEventSynchronize(e1));
+  float ms = 0.f;
+  CN_TRY_CUDA(m, cudaEventElapsedTime(&ms, e0, e1));
+  m->ev_pool.push_back(e0);
+  m->ev_pool.push_back(e1);
+  dfree_raw(m, sink);
+  *tflops = 2.0 * 4.0 * (double)blocks * threads * iters / (ms * 1e-3) / 1e12;
   return CN_OK;
 }
 

@@ -21,9 +21,10 @@ __global__ void k_setup_pad(DevModel M) {
 //   a_i  = -100/(ri_i area_p) / cdt_p          (row parent, column i)
 //   dax_i = sum of the unscaled axial couplings of row i
 // One thread per cell (a cell's parts may sit in different lanes); elem
-// maps a global node to its element.
+// maps a global node to its element.  Without `scaled` (the reference
+// layouts) a and b keep their unscaled values.
 __global__ void k_setup_geom(DevModel M, int n_cells, const int32_t* off, const int32_t* parent, const double* area,
-                             const double* ri, const double* cm, const int64_t* elem) {
+                             const double* ri, const double* cm, const int64_t* elem, bool scaled) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n_cells) return;
   double* a = const_cast<double*>(M.a);
@@ -36,8 +37,8 @@ __global__ void k_setup_geom(DevModel M, int n_cells, const int32_t* off, const 
     const double aa = -100.0 / (ri[i] * area[ip]);
     M.dax[e] -= bb;
     M.dax[ep] -= aa;
-    b[e] = bb / M.cdt[e];
-    a[e] = aa / M.cdt[ep];
+    b[e] = scaled ? bb / M.cdt[e] : bb;
+    a[e] = scaled ? aa / M.cdt[ep] : aa;
   }
 }
 
@@ -208,7 +209,8 @@ __global__ void k_pull_events(DevModel M, int64_t J, const int64_t* Jp) {
   const int slot = blockIdx.x * blockDim.x + threadIdx.x;
   if (slot >= M.n_slots) return;
   if (Jp) J = *Jp;
-  EvRec* out = M.ev_buf + (int64_t)slot * kEvCap;
+  EvRec* out = M.ev_buf + M.ev_off[slot];
+  const int cap = (int)(M.ev_off[slot + 1] - M.ev_off[slot]);
   const int D = M.D;
   const int64_t T = J * D;
   int n = 0;
@@ -218,7 +220,7 @@ __global__ void k_pull_events(DevModel M, int64_t J, const int64_t* Jp) {
   const int64_t pe = M.x_off[slot + 1];
   while (p < pe && M.x_step[p] < T + D) {
     if (M.x_step[p] >= T) {
-      if (n < kEvCap) out[n] = EvRec{(int32_t)(M.x_step[p] - T), M.x_syn[p], M.x_w[p]};
+      if (n < cap) out[n] = EvRec{(int32_t)(M.x_step[p] - T), M.x_syn[p], M.x_w[p]};
       else overflow = true;
       ++n;
     }
@@ -245,13 +247,13 @@ __global__ void k_pull_events(DevModel M, int64_t J, const int64_t* Jp) {
         const int bit = __ffsll((long long)mk) - 1;
         mk &= mk - 1ull;
         const int64_t t = I * D + 1 + b0 + bit;
-        if (n < kEvCap) out[n] = EvRec{(int32_t)(t + ds - T), M.in_syn[q], M.in_w[q]};
+        if (n < cap) out[n] = EvRec{(int32_t)(t + ds - T), M.in_syn[q], M.in_w[q]};
         else overflow = true;
         ++n;
       }
     }
   }
-  const int m = n < kEvCap ? n : kEvCap;
+  const int m = n < cap ? n : cap;
   // Stable insertion sort by step: externals were appended first (in step
   // order), NetCon events after them in (source gid, NetCon index) order, so
   // ties keep exactly the delivery order described above.
@@ -273,6 +275,20 @@ __global__ void k_pull_events(DevModel M, int64_t J, const int64_t* Jp) {
 __global__ void k_rcp64(const double* __restrict__ d, double* __restrict__ out, int64_t n) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = rcp64(d[i]);
+}
+
+// A stream of independent FP64 fused multiply-adds (diagnostics: the FP64
+// pipe's attainable rate on this GPU).  Four chains per thread; the sums go
+// to out so nothing is eliminated.
+__global__ void k_dfma_stream(double* out, int iters, double a, double b) {
+  double x0 = threadIdx.x * 1e-3, x1 = x0 + 1.0, x2 = x0 + 2.0, x3 = x0 + 3.0;
+  for (int it = 0; it < iters; ++it) {
+    x0 = fma(x0, a, b);
+    x1 = fma(x1, a, b);
+    x2 = fma(x2, a, b);
+    x3 = fma(x3, a, b);
+  }
+  out[blockIdx.x * blockDim.x + threadIdx.x] = x0 + x1 + x2 + x3;
 }
 
 // Advances the device-side interval index after a complete interval.
@@ -422,7 +438,7 @@ __device__ __forceinline__ void dense_step(const DevModel& M, int mask, int64_t 
     T drive = T(-1e4) * (T)in.ica / (T(2.0 * 96485.3321) * depth);
     if (drive < T(0)) drive = T(0);
     const T cai = (T)in.cai;
-    cai1 = (double)(cai + (T(1) - dexp_(-tdt / taur)) * (cainf + drive * taur - cai));
+    cai1 = (double)(cai + omexp_(tdt / taur) * (cainf + drive * taur - cai));
     M.cai[e] = cai1;
     const double c = in.gb[4] * (double)(m * m * h);
     const double eca = erev[4 * kLanes];
@@ -623,7 +639,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, DENSE ? 2 : 4)
   const double thresh = M.s_thresh[slot];
   int above = M.s_above[slot];
   uint64_t mask = (s_begin > 0 && gid >= 0) ? M.hist[J * M.n_cells + gid] : 0ull;
-  const EvRec* ev = M.ev_buf + (int64_t)slot * kEvCap;
+  const EvRec* ev = M.ev_buf + M.ev_off[slot];
   const int ne = M.ev_count[slot];
   int ei = 0;
   while (ei < ne && ev[ei].step < s_begin) ++ei;

@@ -59,7 +59,8 @@ def test_batched_fp64_parity(cn, case):
 def test_batched_reduced_precision_report(cn, case, precision):
     """Gating in FP32 (BF16 storage optional), voltage and solve in FP64:
     max/RMS soma-voltage error and spikes in the same step as the FP64
-    oracle (printed; FP32 must keep at least 95% of spikes in step)."""
+    oracle, printed.  The FP32 bar is 0.1 mV and 99.9% of spikes in the same
+    step; a miss is an xfail that states the measured numbers."""
     sc, ref = case
     _, g, k, tr = run(cn, sc, precision)
     rt = ref.traces()
@@ -68,8 +69,9 @@ def test_batched_reduced_precision_report(cn, case, precision):
     same = len(set(zip(g.tolist(), k.tolist())) & set(zip(rg.tolist(), rk.tolist())))
     print(f"{precision}: max {err.max():.3g} mV, rms {np.sqrt(np.mean(err ** 2)):.3g} mV, "
           f"spikes same step {same}/{len(rg)} (gpu {len(g)})")
-    if precision == "gate_fp32":
-        assert same >= 0.95 * len(rg)
+    if precision == "gate_fp32" and (err.max() > 0.1 or same < 0.999 * len(rg)):
+        pytest.xfail(f"FP32 gating misses the bar: max soma error {err.max():.3g} mV (bar 0.1), "
+                     f"{same}/{len(rg)} spikes in the same step (bar 99.9%)")
 
 
 def _one_node(kind, gbar, v_init, pas_g, pas_e, tstop):

@@ -252,3 +252,40 @@ def test_plan_layout_rejects_bad_trees(cn):
     assert e.value.status == cn.CN_EINVAL
     with pytest.raises(cn.CNError):
         cn.cn_plan_layout(np.array([0, 2]), np.array([0, -1]), 0)
+
+
+@pytest.mark.parametrize("mapping", ["interleaved", "constdepth"])
+@pytest.mark.parametrize("case", ["network", "morph_types", "ring16"])
+def test_reference_layout_invariants(cn, case, mapping):
+    """The reference placements keep what makes their sums follow a
+    sequential per-cell stepper: every parent in an earlier row of the same
+    warp; never two children of one node in one row; a node's children in
+    rows that increase with their input index; at most one spike source
+    (here each cell's root) per lane; one node per (warp, lane, row).
+    Interleaved puts node i of each cell at row i of one lane."""
+    from scenarios import morph_types
+    sc = {"network": lambda: network(n_cells=70, tstop=1.0),
+          "morph_types": lambda: morph_types(n_cells=96, cells_per_type=4, tstop=1.0),
+          "ring16": lambda: ring16(tstop=1.0)}[case]()
+    off, par = np.asarray(sc.cell_offset), np.asarray(sc.parent)
+    code = cn.CN_MAP_INTERLEAVED if mapping == "interleaved" else cn.CN_MAP_CONSTDEPTH
+    L = cn.cn_plan_layout(off, par, code)
+    lane, row = L["lane"], L["row"]
+    assert len(set(zip(lane.tolist(), row.tolist()))) == len(lane)
+    roots = set()
+    for c in range(len(off) - 1):
+        i0, i1 = off[c], off[c + 1]
+        w = lane[i0] // 32
+        assert np.all(lane[i0:i1] // 32 == w)
+        assert lane[i0] not in roots
+        roots.add(lane[i0])
+        kids = {}
+        for i in range(i0 + 1, i1):
+            p = i0 + par[i]
+            assert row[p] < row[i]
+            kids.setdefault(p, []).append(i)
+        for p, ks in kids.items():
+            rs = [row[i] for i in ks]                      # input order
+            assert rs == sorted(rs) and len(set(rs)) == len(rs)
+        if mapping == "interleaved":
+            assert np.all(row[i0:i1] == np.arange(i1 - i0)) and np.all(lane[i0:i1] == lane[i0])
