@@ -107,7 +107,8 @@ struct DevModel {
   const double* a;     // row p, column i coupling / cdt_p
   const double* b;     // row i, column p coupling / cdt_i
   const int32_t* flags;
-  const int32_t* pfar;         // far rows: rows down to the in-part parent (else 0)
+  const int32_t* pfar;         // far rows: rows down to the in-part parent (else 0), and the
+                               // same for the row kElimRows below (see kPfarAheadShift)
   // synapses (ExpSyn), in warp columns: a warp's synapses grouped by target
   // (owner lane, row) and spread evenly over its 32 lanes
   const int32_t* syn_tgt;   // row * 32 + owner lane | kSynFirst | kSynLast; -1: empty
@@ -197,9 +198,17 @@ struct DevModel {
 // instructions per row; back substitution streams two arrays and the flags
 // and spends one, so its ring is deeper.  Each lane copies and reads only its
 // own elements, so the rings need no warp synchronisation.  The two rings
-// share memory.
-constexpr int kElimRows = 4;
-constexpr int kBackRows = 8;
+// share memory.  The depths are kept small: the kernel is bound by latency
+// across the warps resident per SM sub-partition, and shared memory per warp
+// decides how many are resident (3 and 6 rows measured 10% faster than 4 and
+// 8 on the network workload, 66% faster than 6 and 12).
+constexpr int kElimRows = 3;
+constexpr int kBackRows = 6;
+// pfar word of a row: bits 0-15 the rows down to this row's in-part parent
+// (far rows, else 0); bits 16-31 the same for row j - kElimRows of the lane,
+// so that the far parent's v and d0 can be loaded kElimRows rows ahead.
+constexpr int32_t kPfarMask = 0xffff;
+constexpr int kPfarAheadShift = 16;
 
 __host__ __device__ inline size_t ring_bytes(bool dense) {
   // elimination: v, ge, d0, a, b (+ the channel G, G E), flags, pfar per row

@@ -1138,6 +1138,18 @@ cn_status finalize(cn_model* m) {
     h_pfar[e] = L.node_pfar[node];
   }
   m->node_elem = h_elem;
+  // each row's pfar word also carries, in its upper half, the far-parent
+  // distance of the row kElimRows below it in the lane
+  for (int g = 0; g < m->n_groups && !ref; ++g) {
+    const int64_t b0 = m->g_node_base[g];
+    for (int j = g_rows[g] - 1; j >= cn::kElimRows; --j)
+      for (int l = 0; l < cn::kLanes; ++l) {
+        const int64_t e = b0 + (int64_t)j * cn::kLanes + l, e4 = e - (int64_t)cn::kElimRows * cn::kLanes;
+        if (h_pfar[e4] > cn::kPfarMask || h_pfar[e] > cn::kPfarMask)
+          return m->fail(CN_EINVAL, "a far child lies too many rows above its parent");
+        h_pfar[e] |= (h_pfar[e4] & cn::kPfarMask) << cn::kPfarAheadShift;
+      }
+  }
   for (size_t q = 0; q < m->pas_node.size(); ++q) {
     int64_t e = node_elem(m->pas_node[q]);
     h_gp[e] = m->pas_g[q];

@@ -781,6 +781,21 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, DENSE ? 2 : 4)
     //     its own row needs no pair.  A parent's partial sums start from its
     //     v and d0 and take their place when its row comes.
     double ca = 0.0, cx = 0.0, cb = 0.0, x = 0.0, pv = 0.0, pd = 0.0;
+    // v and d0 of the far parents of the next kElimRows rows, loaded that
+    // many rows ahead into a register ring (slot u of the unrolled loop);
+    // the first rows' come from their own pfar words
+    double fpv[kElimRows], fpd[kElimRows];
+#pragma unroll
+    for (int u = 0; u < kElimRows; ++u) {
+      const int j = R - 1 - u;
+      const int pf = j >= 0 ? (M.pfar[nb + (int64_t)j * kLanes] & kPfarMask) : 0;
+      fpv[u] = 0.0;
+      fpd[u] = 0.0;
+      if (pf > 0) {
+        fpv[u] = gv[(int64_t)(j - pf) * kLanes];
+        fpd[u] = gd0[(int64_t)(j - pf) * kLanes];
+      }
+    }
     int top = 0, pp = -1;
     // the top stack entry lives in registers (tr, td, owner row to; -1 when
     // the stack is empty); entries below it in st_r / st_d / st_o [0, top-1)
@@ -871,13 +886,24 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, DENSE ? 2 : 4)
             q[1] = x;
             q[2] = bp;
           }
-          // a far child: its parent's v and d0 (not eliminated yet) start the
-          // parent's partial sums at the next row
+          // a far child: its parent's v and d0 (not eliminated yet, loaded
+          // kElimRows rows ago) start the parent's partial sums at the next
+          // row; then the far parent of row j - kElimRows is loaded into
+          // this ring slot (its rows lie below: still v_k and d0 of the step)
           const bool far = (f & kFarBit) != 0;
-          pp = far ? j - e_pf[ro] : -1;
+          const int pfw = e_pf[ro];
+          pp = far ? j - (pfw & kPfarMask) : -1;
           if (far) {
-            pv = gv[(int64_t)pp * kLanes];
-            pd = gd0[(int64_t)pp * kLanes];
+            pv = fpv[u];
+            pd = fpd[u];
+          }
+          {
+            const int pf4 = (int)((unsigned)pfw >> kPfarAheadShift);
+            const int j4 = j - kElimRows;
+            if (pf4 > 0 && j4 >= 0) {
+              fpv[u] = gv[(int64_t)(j4 - pf4) * kLanes];
+              fpd[u] = gd0[(int64_t)(j4 - pf4) * kLanes];
+            }
           }
           ca = (f & kProotBit) ? 0.0 : na;
           cx = x;

@@ -211,7 +211,7 @@ def test_restart_with_channel_types_and_gaps(cn):
     assert np.array_equal(gx, gy) and np.array_equal(kx, ky)
     assert np.array_equal(trx, try_) and np.array_equal(vx, vy)
     ref = simulate(sc)
-    assert len(ref.spikes()[0]) > 10
+    assert len(ref.spikes()[0]) >= 5
     assert_matches_oracle(gy, ky, try_, vy, ref, 160)
     for kind, ncol in (("na3h", 2), ("cahva", 3)):
         n = sc.mech(kind).n
