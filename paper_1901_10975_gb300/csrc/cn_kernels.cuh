@@ -310,6 +310,18 @@ __device__ __forceinline__ void gate_ab(const T* kin, T v, T& al, T& be) {
   be = B * dexp_(-(v - vh2) / k2);
 }
 
+// One gate's cnexp update at v from its kinetics (alpha, beta as above).  It
+// is kept out of line so that one copy of its exponential and division
+// sequences serves all nine gates: inlined per gate, the channel update's
+// code outgrew the instruction cache (ncu: 13.8 cycles per issue waiting on
+// instruction fetch) and the interval ran 28% (FP64) / 18% (FP32) slower.
+template <typename T>
+__device__ __noinline__ T gate_next(const T* kin, T v, T x, T dt) {
+  T al, be;
+  gate_ab<T>(kin, v, al, be);
+  return cnexp_step<T>(x, al, be, dt);
+}
+
 // Channel conductance G and sum of g E of row e at voltage v from the stored
 // gates (the nrn_cur of the channel types), and ica for the calcium update.
 template <int PREC>
@@ -397,10 +409,8 @@ __device__ __forceinline__ void dense_step(const DevModel& M, int mask, int64_t 
   // the gate powers are formed in the gate type; gbar times that product
   // and the sums that enter the matrix are FP64
   auto upd = [&](int gi, const T* k6) -> T {
-    T al, be;
-    gate_ab<T>(k6, v, al, be);
     S* p = static_cast<S*>(M.ch_gate[gi]) + e;
-    return g_store_ret(p, cnexp_step<T>(in.x[gi], al, be, tdt));
+    return g_store_ret(p, gate_next<T>(k6, v, in.x[gi], tdt));
   };
   double g = 0.0, ge = 0.0;
   if (mask & 1) {  // NA3H: m^3 h
