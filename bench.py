@@ -180,9 +180,11 @@ def config_dict(args, sc, layout=None):
          "precision": args.precision}
     if layout is not None:
         mp, wpb, nw, tuned = layout
-        span = mp & ~(3 << 20)
+        span, height = mp & ((1 << 20) - 1), (mp >> 22) & 0x1ff
         tall = {1: ", tall warps", 2: ", warps twice the largest span", 3: ", warps 1.5 times the largest span"}.get(
             (mp >> 20) & 3, "")
+        if height:
+            tall = f", warps {height} rows tall"
         names = {1: "one cell per lane", 3: "reference: interleaved node ordering (one cell per lane)",
                  4: "reference: constant-depth node ordering (one node per lane and row)"}
         d["layout"] = {"mapping": names.get(mp, f"cells split to ~{span} rows per lane" + tall),

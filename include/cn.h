@@ -141,10 +141,25 @@ typedef enum {
   CN_MAP_TUNE = 2        /* autotuned on first use: each candidate layout (one cell per lane; spans
                             of 1/8, 1/4, 1/2 and 1 mean cell size, each also with CN_MAP_TALL,
                             CN_MAP_TALL | CN_MAP_TALL2 and CN_MAP_TALL2; then 0.85, 0.9, 0.95
-                            and 1.1 times the best span)
+                            and 1.1 times the best span; then, when the best has CN_MAP_TALL
+                            alone, warp heights (CN_MAP_HEIGHT) at the best span and 3/4 of
+                            it: the lowest height whose warps all fit on the device at once,
+                            and that height + 4 rows)
                             with 1, 2 and 4 warps per block runs one timed interval from the
                             initial state; the fastest is kept */
 } cn_mapping;
+
+/* Warp height field of a mapping value (bits 22-30), with CN_MAP_TALL and a
+ * target span: every warp is h rows tall (16 <= h <= 511) instead of the
+ * largest cell span.  Cells whose span exceeds h are cut again with finer
+ * targets (down to 4 rows per part) and open warps of their own span if
+ * they still exceed it.  Parts then also fill the free runs of rows that a
+ * part root's junction constraint leaves below a lane's top, and a part
+ * goes where it leaves the least padding (four rows of padding weigh as one
+ * row of delay), else at the earliest row that fits.                      */
+#define CN_MAP_HEIGHT_SHIFT 22
+#define CN_MAP_HEIGHT_MASK ((int32_t)0x1ff << CN_MAP_HEIGHT_SHIFT)
+#define CN_MAP_HEIGHT(h) ((int32_t)(h) << CN_MAP_HEIGHT_SHIFT)
 
 /* The layout in use (after the first cn_run, or after the autotuner):
  * mapping (CN_MAP_THREAD or the target span), warps per block, warps in all,
@@ -163,7 +178,8 @@ cn_status cn_get_mapping(cn_model* m, int32_t* mapping, int32_t* warps_per_block
  * same warp, reached through a per-warp mailbox entry.
  *   n_cells, cell_offset[n_cells+1], parent[n_nodes]: as in cn_morph.
  *   mapping: a cn_mapping value or a target span (>= 16 rows), optionally
- *   with CN_MAP_TALL, CN_MAP_TALL2 or both.
+ *   with CN_MAP_TALL, CN_MAP_TALL2 or both, or CN_MAP_TALL with a warp
+ *   height CN_MAP_HEIGHT(h).
  * Outputs (caller-owned, each may be NULL):
  *   node_lane[n_nodes]  global lane = 32 * warp + lane of the node's part
  *   node_row[n_nodes]   warp row of the node

@@ -19,6 +19,12 @@ CN_PARAM_GNABAR, CN_PARAM_GKBAR, CN_PARAM_GPAS = range(3)
 CN_MAP_AUTO, CN_MAP_THREAD, CN_MAP_TUNE, CN_MAP_INTERLEAVED, CN_MAP_CONSTDEPTH = range(5)
 CN_MAP_TALL = 1 << 20
 CN_MAP_TALL2 = 1 << 21
+CN_MAP_HEIGHT_SHIFT = 22
+
+
+def CN_MAP_HEIGHT(h):
+    """Warp height field of a mapping value (with CN_MAP_TALL and a span)."""
+    return int(h) << CN_MAP_HEIGHT_SHIFT
 STATUS_NAMES = {0: "CN_OK", 1: "CN_EINVAL", 2: "CN_ENOMEM", 3: "CN_ECUDA", 4: "CN_ESTATE",
                 5: "CN_ETIMEOUT", 6: "CN_ERANGE"}
 MECH = {"pas": 0, "hh": 1, "expsyn": 2, "na3h": 3, "kdr4": 4, "ka": 5, "ih": 6, "cahva": 7, "kca": 8}

@@ -555,9 +555,22 @@ int tall_factor(int32_t mapping) {  // warp height in half spans: TALL 2, TALL2 
   return ((mapping & CN_MAP_TALL) ? 2 : 0) + ((mapping & CN_MAP_TALL2) ? (mapping & CN_MAP_TALL ? 1 : 4) : 0);
 }
 
+// Warp height of a mapping value (CN_MAP_HEIGHT field); 0 = none.
+int map_height(int32_t mapping) { return (mapping & CN_MAP_HEIGHT_MASK) >> CN_MAP_HEIGHT_SHIFT; }
+
+// A cn_mapping value, or a span >= 16 with CN_MAP_TALL / CN_MAP_TALL2, or
+// with CN_MAP_TALL alone and a warp height of at least 16 rows.
+bool valid_mapping(int32_t mapping) {
+  const int32_t span = mapping & ~(CN_MAP_TALL | CN_MAP_TALL2 | CN_MAP_HEIGHT_MASK);
+  const int h = map_height(mapping);
+  if (mapping < 0 || (span > CN_MAP_CONSTDEPTH && span < 16)) return false;
+  if ((mapping & (CN_MAP_TALL | CN_MAP_TALL2)) && span < 16) return false;
+  return h == 0 || (h >= 16 && (mapping & CN_MAP_TALL) && !(mapping & CN_MAP_TALL2));
+}
+
 // Target span (rows per lane) of a mapping value; 0 = never split.
 int map_target(int32_t mapping, int64_t n_nodes, int32_t n_cells, bool adjoint) {
-  mapping &= ~(CN_MAP_TALL | CN_MAP_TALL2);
+  mapping &= ~(CN_MAP_TALL | CN_MAP_TALL2 | CN_MAP_HEIGHT_MASK);
   if (mapping >= 16) return mapping;
   if (mapping == CN_MAP_AUTO && !adjoint && n_cells > 0)
     return (int)std::max<int64_t>(16, (n_nodes + n_cells - 1) / n_cells);
@@ -615,24 +628,47 @@ struct Layout {
   std::vector<int32_t> node_flags;            // global node -> topology bits
   std::vector<int32_t> node_pfar;             // global node -> rows down to the in-part parent (far nodes)
   std::vector<int32_t> node_paroff;           // reference layouts: parent's element offset in the group (-1: root)
+  int max_span = 0;                           // largest cell span of the split plans
 };
 
-constexpr int kPackLookahead = 512;  // remaining cells tried per warp  // refusals after which a warp takes no more cells
+// Split plans of every cell (in parallel over the host's cores); with a
+// warp height, a cell whose span exceeds it is planned again with finer
+// targets, keeping its lowest span.
+void plan_cells(int32_t n_cells, const int32_t* off, const int32_t* parent, int target, int height,
+                std::vector<CellPlan>& plans) {
+  plans.assign(n_cells, CellPlan{});
+  parallel_ranges(n_cells, 256, [&](int64_t c0, int64_t c1) {
+    for (int64_t c = c0; c < c1; ++c) {
+      const int n = off[c + 1] - off[c];
+      plans[c] = plan_cell(parent + off[c], n, target);
+      for (int t = target - 2; height > 0 && target > 0 && plans[c].span > height && t >= 4; t -= 2) {
+        CellPlan P = plan_cell(parent + off[c], n, t);
+        if (P.span < plans[c].span) plans[c] = std::move(P);
+      }
+    }
+  });
+}
 
+constexpr int kPackLookahead = 512;  // remaining cells tried per warp
+constexpr int kHoles = 4;            // free runs below a lane's top kept per lane (warp height given)
+constexpr int kHoleWeight = 4;       // rows of delay one row of padding is worth (warp height given)
+
+// With a warp height (height > 0, tall warps): cells whose span exceeds it
+// are planned again with finer targets, warps are `height` rows tall (or
+// the span of a taller cell that opens one), and parts may fill the free
+// runs below a lane's top.
 bool build_layout(int32_t n_cells, const int32_t* off, const int32_t* parent, const int32_t* cell_mask,
-                  const int32_t* spike_node, int target, bool stack, int tall, Layout& L, std::string& err) {
+                  const int32_t* spike_node, int target, bool stack, int tall, int height, Layout& L,
+                  std::string& err) {
   auto mask = [&](int c) { return cell_mask ? cell_mask[c] : 0; };
-  L.plans.assign(n_cells, CellPlan{});
+  plan_cells(n_cells, off, parent, target, height, L.plans);
   L.depth = 1;
   int H = 1;
-  // cells are planned independently: spread them over the host's cores
-  parallel_ranges(n_cells, 256, [&](int64_t c0, int64_t c1) {
-    for (int64_t c = c0; c < c1; ++c) L.plans[c] = plan_cell(parent + off[c], off[c + 1] - off[c], target);
-  });
   for (int c = 0; c < n_cells; ++c) {
     const int n = off[c + 1] - off[c];
     L.depth = std::max(L.depth, L.plans[c].depth);
     H = std::max(H, L.plans[c].span);
+    L.max_span = H;
     for (int32_t li = 0; li < n; ++li)
       if (L.plans[c].nfar[li] > (int)cn::kNFarMask) {
         err = "a node has more than 8 children";
@@ -659,6 +695,10 @@ bool build_layout(int32_t n_cells, const int32_t* off, const int32_t* parent, co
     int H = 0;               // rows of this warp: the span of the cell that opened it
     int max_free = 1 << 30;  // longest free run of rows in any lane
     int64_t free_rows = 0;   // free rows over all lanes
+    // with a warp height: free runs [hs, he) below a lane's top, left where
+    // a part root had to start above its junction row
+    int nh[cn::kLanes];
+    int hs[cn::kLanes][kHoles], he[cn::kLanes][kHoles];
   };
   std::vector<Warp> warps;
   // per cell: part order (parents first), and the placement found
@@ -670,50 +710,109 @@ bool build_layout(int32_t n_cells, const int32_t* off, const int32_t* parent, co
   part_lane_of_cell.assign(cell_part0[n_cells], -1);
   part_start_of_cell.assign(cell_part0[n_cells], 0);
   std::vector<int> cell_warp(n_cells, -1), warp_mail0(n_cells, 0);
-  auto try_place = [&](int c, Warp& w, int wi) -> bool {
+  // Places cell c's parts in warp w (parents first).  Each part goes to the
+  // lane, and with a warp height to the free run or lane top, where it
+  // starts earliest (ties: least padding left below it); with `pad_rule`,
+  // where padding x kHoleWeight + delay past its release row is least.
+  auto place = [&](int c, Warp& w, bool pad_rule) -> bool {
     const CellPlan& P = L.plans[c];
     const int np = (int)P.parts.size();
     if (w.n_mail + np - 1 > cn::kMailMask + 1) return false;
     const int qsp = P.part_of[spike_node ? spike_node[c] : 0];  // the part holding the spike source
-    int lev[cn::kLanes], own[cn::kLanes];
+    int lev[cn::kLanes], own[cn::kLanes], nh[cn::kLanes], hs[cn::kLanes][kHoles], he[cn::kLanes][kHoles];
     std::copy(w.lev, w.lev + cn::kLanes, lev);
     std::copy(w.owner, w.owner + cn::kLanes, own);
+    std::copy(w.nh, w.nh + cn::kLanes, nh);
+    std::copy(&w.hs[0][0], &w.hs[0][0] + cn::kLanes * kHoles, &hs[0][0]);
+    std::copy(&w.he[0][0], &w.he[0][0] + cn::kLanes * kHoles, &he[0][0]);
+    // a new free run [a, b) of lane l (only with a warp height); when the
+    // lane's list is full the shortest run stays padding
+    auto add_hole = [&](int l, int a, int b) {
+      if (height <= 0 || b <= a) return;
+      int s = nh[l];
+      if (s == kHoles) {
+        s = 0;
+        for (int h = 1; h < kHoles; ++h)
+          if (he[l][h] - hs[l][h] < he[l][s] - hs[l][s]) s = h;
+        if (he[l][s] - hs[l][s] >= b - a) return;
+      } else {
+        ++nh[l];
+      }
+      hs[l][s] = a;
+      he[l][s] = b;
+    };
     pstart.assign(np, 0);
     plane.assign(np, -1);
     for (int q : porder) {
       const int size = (int)P.parts[q].nodes.size();
-      int best = -1, bstart = 0, bgap = 0;
       const int release = q == 0 ? 0 : pstart[P.parts[q].parent_part] + P.row_of[P.parts[q].jnode] + 1;
+      int best = -1, bhole = -1, bstart = 0, bgap = 0;
+      auto consider = [&](int l, int h, int st, int gap) {
+        bool better = best < 0;
+        if (!better && pad_rule) {
+          const int cst = kHoleWeight * gap + st, cb = kHoleWeight * bgap + bstart;
+          better = cst < cb || (cst == cb && st < bstart);
+        } else if (!better) {
+          better = st < bstart || (st == bstart && gap < bgap);
+        }
+        if (better) {
+          best = l;
+          bhole = h;
+          bstart = st;
+          bgap = gap;
+        }
+      };
       for (int l = 0; l < cn::kLanes; ++l) {
         if (q == qsp && w.root[l]) continue;
         if (!stack && own[l] != -1 && own[l] != c) continue;
         const int st = std::max(lev[l], release);
-        const int gap = st - lev[l];
-        if (st + size > w.H) continue;
-        if (best < 0 || st < bstart || (st == bstart && gap < bgap)) {
-          best = l;
-          bstart = st;
-          bgap = gap;
+        if (st + size <= w.H) consider(l, -1, st, st - lev[l]);
+        for (int h = 0; h < nh[l]; ++h) {
+          const int sh = std::max(hs[l][h], release);
+          if (sh + size <= he[l][h]) consider(l, h, sh, sh - hs[l][h]);
         }
       }
       if (best < 0) return false;
       plane[q] = best;
       pstart[q] = bstart;
-      lev[best] = bstart + size;
+      if (bhole < 0) {
+        add_hole(best, lev[best], bstart);
+        lev[best] = bstart + size;
+      } else {  // the run splits into what is left below and above the part
+        const int a = hs[best][bhole], b = he[best][bhole];
+        --nh[best];
+        hs[best][bhole] = hs[best][nh[best]];
+        he[best][bhole] = he[best][nh[best]];
+        add_hole(best, a, bstart);
+        add_hole(best, bstart + size, b);
+      }
       own[best] = (own[best] == -1 || own[best] == c) ? c : -2;
     }
     std::copy(lev, lev + cn::kLanes, w.lev);
     std::copy(own, own + cn::kLanes, w.owner);
+    std::copy(nh, nh + cn::kLanes, w.nh);
+    std::copy(&hs[0][0], &hs[0][0] + cn::kLanes * kHoles, &w.hs[0][0]);
+    std::copy(&he[0][0], &he[0][0] + cn::kLanes * kHoles, &w.he[0][0]);
     w.root[plane[qsp]] = true;
     w.max_free = 0;
     w.free_rows = 0;
+    w.min_lev = cn::kMailMask + (1 << 30);
     for (int l = 0; l < cn::kLanes; ++l) {
       w.max_free = std::max(w.max_free, w.H - w.lev[l]);
       w.free_rows += w.H - w.lev[l];
+      int lo = w.lev[l];
+      for (int h = 0; h < w.nh[l]; ++h) {
+        w.max_free = std::max(w.max_free, w.he[l][h] - w.hs[l][h]);
+        w.free_rows += w.he[l][h] - w.hs[l][h];
+        lo = std::min(lo, w.hs[l][h]);
+      }
+      if (!w.root[l]) w.min_lev = std::min(w.min_lev, lo);  // where a spike-source part can go
     }
-    w.min_lev = cn::kMailMask + (1 << 30);
-    for (int l = 0; l < cn::kLanes; ++l)
-      if (!w.root[l]) w.min_lev = std::min(w.min_lev, w.lev[l]);  // where a spike-source part can go
+    return true;
+  };
+  auto try_place = [&](int c, Warp& w, int wi) -> bool {
+    if (!(height > 0 && place(c, w, true)) && !place(c, w, false)) return false;
+    const int np = (int)L.plans[c].parts.size();
     warp_mail0[c] = w.n_mail;
     w.n_mail += np - 1;
     cell_warp[c] = wi;
@@ -767,8 +866,9 @@ bool build_layout(int32_t n_cells, const int32_t* off, const int32_t* parent, co
     std::fill(w.lev, w.lev + cn::kLanes, 0);
     std::fill(w.owner, w.owner + cn::kLanes, -1);
     std::fill(w.root, w.root + cn::kLanes, false);
+    std::fill(w.nh, w.nh + cn::kLanes, 0);
     w.mask = mask(c0);
-    w.H = tall ? tall * H / 2 : P0.span;
+    w.H = !tall ? P0.span : height > 0 ? std::max(height, P0.span) : tall * H / 2;
     warps.push_back(w);
     const int wi = (int)warps.size() - 1;
     set_order(c0);
@@ -1047,7 +1147,7 @@ cn_status finalize(cn_model* m) {
                                            m->opt.mapping == CN_MAP_CONSTDEPTH, L, lerr)
                         : build_layout(m->n_cells, m->off.data(), m->parent.data(), cell_mask.data(),
                                        m->spike_node.data(), target, !m->dense && m->ck_steps <= 0,
-                                       tall_factor(m->opt.mapping), L, lerr);
+                                       tall_factor(m->opt.mapping), map_height(m->opt.mapping), L, lerr);
     if (!ok) return m->fail(CN_EINVAL, lerr);
   }
   const int depth = L.depth;
@@ -1741,13 +1841,33 @@ cn_status release_device(cn_model* m) {
   return CN_OK;
 }
 
+// Warps of the interval kernel (non-dense instantiation of the model's
+// precision) resident on the whole device at once, in blocks of wpb warps of
+// smem_warp bytes of shared memory each.
+int resident_warps(cn_model* m, size_t smem_warp, int wpb) {
+  const void* fn = m->opt.precision == CN_PREC_FP64        ? (const void*)cn::k_interval<0, false, false>
+                   : m->opt.precision == CN_PREC_GATE_FP32 ? (const void*)cn::k_interval<1, false, false>
+                                                           : (const void*)cn::k_interval<2, false, false>;
+  int per_sm = 0, sms = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 32 * wpb, (size_t)wpb * smem_warp) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->opt.device) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  return per_sm * wpb * sms;
+}
+
 // Mapping autotuner: lays the model out for each candidate (one cell per
 // lane; target spans of 1/8, 1/4, 1/2 and 1 mean cell size, each with warps
 // as tall as the opening cell's span or as 1, 1.5 and 2 times the largest
 // span; then spans of 0.85, 0.9, 0.95 and 1.1 times the best one), and for
 // each runs one warm-up and one timed interval from the initial state with
-// 1, 2 and 4 warps per block; keeps the fastest and lays the model out again
-// with it.  Results do not depend on the choice beyond rounding.
+// 1, 2 and 4 warps per block; keeps the fastest.  When the fastest has warps
+// as tall as the largest span, a last round tries warp heights: for the best
+// span and 3/4 of it, the lowest height (found by bisection on host-only
+// layouts) at which every warp, in blocks of four, is resident on the device
+// at once, and that height + 4.  The model is then laid out again with the
+// winner.  Results do not depend on the choice beyond rounding.
 cn_status autotune(cn_model* m) {
   const int64_t mean = std::max<int64_t>(1, (m->n_nodes + m->n_cells - 1) / std::max(1, m->n_cells));
   std::vector<int32_t> cand{CN_MAP_THREAD};
@@ -1764,14 +1884,12 @@ cn_status autotune(cn_model* m) {
       }
     }
   float best = 0.f;
-  int32_t best_map = CN_MAP_THREAD, best_wpb = 1;
+  int32_t best_map = CN_MAP_THREAD, best_wpb = 1, best_slots = 1;
   const bool prof = m->profiling;
   m->profiling = false;
   cudaEvent_t e0 = take_event(m), e1 = take_event(m);
   std::vector<int32_t> tried;
-  bool refined = false;
-  for (size_t ci = 0; ci < cand.size(); ++ci) {
-    const int32_t c = cand[ci];
+  auto measure = [&](int32_t c) -> cn_status {
     tried.push_back(c);
     m->opt.mapping = c;
     CN_CHECK(finalize(m));
@@ -1791,9 +1909,14 @@ cn_status autotune(cn_model* m) {
         best = ms;
         best_map = c;
         best_wpb = w;
+        best_slots = m->dm.max_slots;
       }
     }
-    CN_CHECK(release_device(m));
+    return release_device(m);
+  };
+  bool refined = false;
+  for (size_t ci = 0; ci < cand.size(); ++ci) {
+    CN_CHECK(measure(cand[ci]));
     // after the coarse candidates, refine the best span: a slightly finer
     // cut can fill the device's resident warps without a second wave
     if (ci + 1 == cand.size() && best_map >= 16 && !refined) {
@@ -1806,6 +1929,51 @@ cn_status autotune(cn_model* m) {
           cand.push_back(v);
       }
     }
+  }
+  // warp heights for tall warps: the lowest height whose warps, in blocks of
+  // four, are all resident at once (the warp count falls as the height grows)
+  if (!m->dense && m->ck_steps <= 0 && best_map >= 16 &&
+      (best_map & (CN_MAP_TALL | CN_MAP_TALL2)) == CN_MAP_TALL) {
+    const int32_t span = best_map & ~CN_MAP_TALL;
+    const int gate_bytes = m->opt.precision == CN_PREC_FP64 ? 8 : 4;
+    auto fits = [&](int32_t target, int h) -> int {  // 1 fits, 0 not, -1 layout failed
+      Layout L;
+      std::string lerr;
+      if (!build_layout(m->n_cells, m->off.data(), m->parent.data(), nullptr, m->spike_node.data(), target, true, 2,
+                        h, L, lerr))
+        return -1;
+      const size_t smem = cn::interval_smem_bytes(L.depth, best_slots, false, L.n_mail, gate_bytes);
+      return L.n_groups <= resident_warps(m, smem, cn::kMaxWarpsPerBlock) ? 1 : 0;
+    };
+    std::vector<int32_t> hc;
+    for (int32_t target : {span, std::max<int32_t>(16, (3 * span + 2) / 4)}) {
+      std::vector<CellPlan> plans;
+      plan_cells(m->n_cells, m->off.data(), m->parent.data(), target, 0, plans);
+      int top = 0;  // the largest span: heights below it are the candidates
+      for (const CellPlan& P : plans) top = std::max(top, P.span);
+      if (top > 511) continue;
+      // lo does not fit, hi is taken to (a height that does not fit leaves
+      // no candidate below the largest span)
+      int lo = std::max(16, (3 * top) / 4), hi = top;
+      const int r0 = fits(target, lo);
+      if (r0 < 0) continue;
+      if (r0 == 1) hi = lo;
+      bool ok = true;
+      while (hi - lo > 2) {
+        const int mid = (lo + hi) / 2;
+        const int r = fits(target, mid);
+        if (r < 0) {
+          ok = false;
+          break;
+        }
+        (r == 1 ? hi : lo) = mid;
+      }
+      if (!ok) continue;
+      for (int h : {hi, hi + 4})
+        if (h < top) hc.push_back(target | CN_MAP_TALL | CN_MAP_HEIGHT(h));
+    }
+    for (int32_t c : hc)
+      if (std::find(tried.begin(), tried.end(), c) == tried.end()) CN_CHECK(measure(c));
   }
   m->ev_pool.push_back(e0);
   m->ev_pool.push_back(e1);
@@ -2042,14 +2210,18 @@ cn_status cn_plan_layout(int32_t n_cells, const int32_t* cell_offset, const int3
     return CN_EINVAL;
   }
   if (!valid_trees(n_cells, cell_offset, parent, g_create_error)) return CN_EINVAL;
+  if (!valid_mapping(mapping)) {
+    g_create_error = "bad mapping";
+    return CN_EINVAL;
+  }
   const int64_t nn = cell_offset[n_cells];
   Layout L;
   const bool ok = is_ref_mapping(mapping)
                       ? build_ref_layout(n_cells, cell_offset, parent, nullptr, mapping == CN_MAP_CONSTDEPTH, L,
                                          g_create_error)
                       : build_layout(n_cells, cell_offset, parent, nullptr, nullptr,
-                                     map_target(mapping, nn, n_cells, false), true, tall_factor(mapping), L,
-                                     g_create_error);
+                                     map_target(mapping, nn, n_cells, false), true, tall_factor(mapping),
+                                     map_height(mapping), L, g_create_error);
   if (!ok) return CN_EINVAL;
   if (node_lane) std::copy(L.node_slot.begin(), L.node_slot.end(), node_lane);
   if (node_row) std::copy(L.node_row.begin(), L.node_row.end(), node_row);
@@ -2076,10 +2248,9 @@ cn_status cn_model_create(const cn_morph* morph, const cn_mech_table* mechs, int
   if ((o.alloc == nullptr) != (o.free == nullptr)) return bad("alloc and free must be given together");
   if (o.warps_per_block < 0 || o.warps_per_block > cn::kMaxWarpsPerBlock) return bad("warps_per_block must be 0..4");
   {
-    const int32_t mv = o.mapping & ~(CN_MAP_TALL | CN_MAP_TALL2);
-    if (o.mapping < 0 || (mv > CN_MAP_CONSTDEPTH && mv < 16) ||
-        ((o.mapping & (CN_MAP_TALL | CN_MAP_TALL2)) && mv < 16))
-      return bad("mapping must be 0-4, or a span >= 16 (optionally with CN_MAP_TALL)");
+    if (!valid_mapping(o.mapping))
+      return bad("mapping must be 0-4, or a span >= 16 (optionally with CN_MAP_TALL and/or CN_MAP_TALL2, "
+                 "or with CN_MAP_TALL and a warp height of 16-511 rows)");
   }
   const int32_t nc = morph->n_cells;
   if (nc <= 0 || !morph->cell_offset || !morph->parent || !morph->area_um2 || !morph->cm_uF_cm2 ||

@@ -313,13 +313,15 @@ def test_event_buffers_sized_for_every_delivery(cn):
     assert_parity(run_gpu(cn, sc), ref)
 
 
-@pytest.mark.parametrize("mapping", [1, 40, 100, 16 | (1 << 20), 64 | (1 << 20), 40 | (3 << 20), 24 | (2 << 20)])
+@pytest.mark.parametrize("mapping", [1, 40, 100, 16 | (1 << 20), 64 | (1 << 20), 40 | (3 << 20), 24 | (2 << 20),
+                                     32 | (1 << 20) | (56 << 22), 16 | (1 << 20) | (24 << 22)])
 def test_split_cells_over_lanes(cn, mapping):
     """The same driven network with one cell per lane (mapping 1) and with
     cells cut into parts of about 40 or 100 rows spread over lanes of one
     warp, in warps as tall as the opening cell or 1, 1.5 and 2 times the
-    largest span: the raster, voltages and states must match the oracle in
-    every layout."""
+    largest span, or of a given height (parts filling free runs below lane
+    tops; cells cut finer, or in warps of their own, where they exceed it):
+    the raster, voltages and states must match the oracle in every layout."""
     sc = network(n_cells=96, tstop=30.0, w_median=0.03, bg_w=0.03, bg_rate_hz=30.0)
     ref = run_oracle(sc)
     assert len(ref["g"]) > 10

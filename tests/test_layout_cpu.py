@@ -214,9 +214,13 @@ CASES = {
 }
 
 
+HEIGHT = 22  # bit of the warp height field
+
+
 @pytest.mark.parametrize("case", sorted(CASES))
 @pytest.mark.parametrize("mapping", [1, 16, 40, 100, 300, 0, 16 | (1 << 20), 100 | (1 << 20), 40 | (3 << 20),
-                                     24 | (2 << 20)])
+                                     24 | (2 << 20), 32 | (1 << 20) | (48 << HEIGHT), 16 | (1 << 20) | (24 << HEIGHT),
+                                     100 | (1 << 20) | (200 << HEIGHT)])
 def test_layout_invariants_and_emulated_solve(cn, case, mapping):
     off, parent = cells_of(CASES[case]())
     L = cn.cn_plan_layout(off, parent, mapping)
@@ -244,6 +248,40 @@ def test_split_spreads_large_cells(cn):
     assert np.unique(split["lane"]).shape[0] >= 4 and split["row"].max() < sizes[c] // 2
     off, parent = cells_of(passive_cable(700, L=1400.0, tstop=1.0))
     assert np.unique(cn.cn_plan_layout(off, parent, 40)["lane"]).shape[0] == 1
+
+
+def warp_rows(L):
+    """Rows per warp (its highest used row + 1) and the lane tops."""
+    span = np.zeros(L["n_warps"], np.int64)
+    np.maximum.at(span, L["lane"] // 32, L["row"].astype(np.int64) + 1)
+    return span
+
+
+def test_warp_height_packs_tighter(cn):
+    """A warp height below the largest cell span: every warp is that tall
+    unless a cell that cannot be cut below it opens one (then as tall as
+    that cell's span), and the parts, which may now fill the free runs
+    below a lane's top, take fewer warp rows in all than warps as tall as
+    the largest span at the same target."""
+    off, parent = cells_of(network(n_cells=2048, tstop=1.0))
+    tall = cn.cn_plan_layout(off, parent, 43 | (1 << 20))
+    top = int(warp_rows(tall).max())
+    h = (9 * top) // 10
+    capped = cn.cn_plan_layout(off, parent, 43 | (1 << 20) | (h << HEIGHT))
+    check_invariants(off, parent, capped)
+    rows = warp_rows(capped)
+    assert np.all(rows <= top)
+    assert np.mean(rows <= h) > 0.95
+    assert rows.sum() < 0.95 * warp_rows(tall).sum()
+
+
+def test_plan_layout_rejects_bad_mappings(cn):
+    off, parent = cells_of(ring16(tstop=1.0))
+    for mp in [32 | (64 << HEIGHT), 32 | (3 << 20) | (64 << HEIGHT), 32 | (1 << 20) | (8 << HEIGHT),
+               8 | (1 << 20), 10]:
+        with pytest.raises(cn.CNError) as e:
+            cn.cn_plan_layout(off, parent, mp)
+        assert e.value.status == cn.CN_EINVAL
 
 
 def test_plan_layout_rejects_bad_trees(cn):
