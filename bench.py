@@ -69,9 +69,12 @@ def kernel_digest():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
-    """DRAM bytes per interval-kernel launch from the committed ncu summary,
-    or None when the kernel source changed since the capture."""
+def profiled_traffic(args, mapping):
+    """DRAM bytes per interval-kernel launch from the committed ncu summary of
+    the full FP64 network workload, or None when this run is another workload
+    or layout, or the kernel source changed since the capture."""
+    if args.workload != "network" or args.cells not in (0, 16384) or args.precision != "fp64":
+        return None
     p = os.path.join(ROOT, "profiles", "k_interval_network16k.md")
     try:
         txt = open(p).read()
@@ -79,7 +82,8 @@ def profiled_traffic():
         return None
     m = re.search(r"kernel_digest:\s*([0-9a-f]+)", txt)
     t = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
-    if not m or not t or m.group(1) != kernel_digest():
+    lay = re.search(r"layout_mapping:\s*([0-9]+)", txt)
+    if not m or not t or not lay or m.group(1) != kernel_digest() or int(lay.group(1)) != mapping:
         return None
     return float(t.group(1))
 
@@ -270,7 +274,7 @@ def run_ours(args):
     upd_launch = sc.n_nodes * 40
     achieved_tflops = FLOP_ALG * upd_launch / (per_launch / 1e3) / 1e12
     hbm, hbm_kind = hbm_peak()
-    traffic = profiled_traffic()
+    traffic = profiled_traffic(args, layout[0] if layout is not None else -1)
     kernel_rate = upd_launch / (per_launch / 1e3)
     fp64_meas = md.fp64_peak()              # a DFMA stream on this GPU, TFLOP/s
     line = {
