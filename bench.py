@@ -192,7 +192,7 @@ def config_dict(args, sc, layout=None):
         names = {1: "one cell per lane", 3: "reference: interleaved node ordering (one cell per lane)",
                  4: "reference: constant-depth node ordering (one node per lane and row)"}
         d["layout"] = {"mapping": names.get(mp, f"cells split to ~{span} rows per lane" + tall),
-                       "warps_per_block": wpb, "warps": nw,
+                       "mapping_value": int(mp), "warps_per_block": wpb, "warps": nw,
                        "chosen_by": "autotuner" if args.mapping == 2 else "fixed"}
     return d
 

@@ -563,8 +563,12 @@ __global__ void k_setup_dense(DevModel M, double v_init, bool scale_gbar) {
 // TRAJ: adjoint recompute -- also store v and the HH gates of every step
 // into the trajectory buffers, and leave spikes, threshold flags and traces
 // untouched.
+// Registers: at most 128 per thread without channel types, so that four
+// 4-warp blocks (16 warps) fit an SM.  The cap is set directly: asking for
+// four resident blocks through __launch_bounds__ gives the same cap, but
+// that build ran 3% slower.
 template <int PREC, bool TRAJ, bool DENSE>
-__global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, DENSE ? 2 : 4)
+__global__ void __launch_bounds__(kMaxWarpsPerBlock * 32) __maxnreg__(DENSE ? 255 : 128)
     k_interval(DevModel M, int64_t J, int s_begin, int s_end, const int64_t* Jp) {
   using S = typename GateT<PREC>::S;
   using T = typename GateT<PREC>::M;
