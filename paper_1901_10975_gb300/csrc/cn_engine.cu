@@ -650,6 +650,8 @@ void plan_cells(int32_t n_cells, const int32_t* off, const int32_t* parent, int 
 }
 
 constexpr int kPackLookahead = 512;  // remaining cells tried per warp
+constexpr int kPackChunks = 16;      // chunks packed in parallel (warp height given), at most
+constexpr int kPackChunkCells = 1024;  // and at least this many cells each
 constexpr int kHoles = 4;            // free runs below a lane's top kept per lane (warp height given)
 constexpr int kHoleWeight = 4;       // rows of delay one row of padding is worth (warp height given)
 
@@ -700,128 +702,15 @@ bool build_layout(int32_t n_cells, const int32_t* off, const int32_t* parent, co
     int nh[cn::kLanes];
     int hs[cn::kLanes][kHoles], he[cn::kLanes][kHoles];
   };
-  std::vector<Warp> warps;
-  // per cell: part order (parents first), and the placement found
-  std::vector<int> porder, pstart, plane;
+  // per cell: the placement found
   std::vector<std::vector<int>> kids;
+  std::vector<int> porder;
   std::vector<int32_t> part_lane_of_cell, part_start_of_cell;  // flattened by cell
   std::vector<int64_t> cell_part0(n_cells + 1, 0);
   for (int c = 0; c < n_cells; ++c) cell_part0[c + 1] = cell_part0[c] + (int64_t)L.plans[c].parts.size();
   part_lane_of_cell.assign(cell_part0[n_cells], -1);
   part_start_of_cell.assign(cell_part0[n_cells], 0);
   std::vector<int> cell_warp(n_cells, -1), warp_mail0(n_cells, 0);
-  // Places cell c's parts in warp w (parents first).  Each part goes to the
-  // lane, and with a warp height to the free run or lane top, where it
-  // starts earliest (ties: least padding left below it); with `pad_rule`,
-  // where padding x kHoleWeight + delay past its release row is least.
-  auto place = [&](int c, Warp& w, bool pad_rule) -> bool {
-    const CellPlan& P = L.plans[c];
-    const int np = (int)P.parts.size();
-    if (w.n_mail + np - 1 > cn::kMailMask + 1) return false;
-    const int qsp = P.part_of[spike_node ? spike_node[c] : 0];  // the part holding the spike source
-    int lev[cn::kLanes], own[cn::kLanes], nh[cn::kLanes], hs[cn::kLanes][kHoles], he[cn::kLanes][kHoles];
-    std::copy(w.lev, w.lev + cn::kLanes, lev);
-    std::copy(w.owner, w.owner + cn::kLanes, own);
-    std::copy(w.nh, w.nh + cn::kLanes, nh);
-    std::copy(&w.hs[0][0], &w.hs[0][0] + cn::kLanes * kHoles, &hs[0][0]);
-    std::copy(&w.he[0][0], &w.he[0][0] + cn::kLanes * kHoles, &he[0][0]);
-    // a new free run [a, b) of lane l (only with a warp height); when the
-    // lane's list is full the shortest run stays padding
-    auto add_hole = [&](int l, int a, int b) {
-      if (height <= 0 || b <= a) return;
-      int s = nh[l];
-      if (s == kHoles) {
-        s = 0;
-        for (int h = 1; h < kHoles; ++h)
-          if (he[l][h] - hs[l][h] < he[l][s] - hs[l][s]) s = h;
-        if (he[l][s] - hs[l][s] >= b - a) return;
-      } else {
-        ++nh[l];
-      }
-      hs[l][s] = a;
-      he[l][s] = b;
-    };
-    pstart.assign(np, 0);
-    plane.assign(np, -1);
-    for (int q : porder) {
-      const int size = (int)P.parts[q].nodes.size();
-      const int release = q == 0 ? 0 : pstart[P.parts[q].parent_part] + P.row_of[P.parts[q].jnode] + 1;
-      int best = -1, bhole = -1, bstart = 0, bgap = 0;
-      auto consider = [&](int l, int h, int st, int gap) {
-        bool better = best < 0;
-        if (!better && pad_rule) {
-          const int cst = kHoleWeight * gap + st, cb = kHoleWeight * bgap + bstart;
-          better = cst < cb || (cst == cb && st < bstart);
-        } else if (!better) {
-          better = st < bstart || (st == bstart && gap < bgap);
-        }
-        if (better) {
-          best = l;
-          bhole = h;
-          bstart = st;
-          bgap = gap;
-        }
-      };
-      for (int l = 0; l < cn::kLanes; ++l) {
-        if (q == qsp && w.root[l]) continue;
-        if (!stack && own[l] != -1 && own[l] != c) continue;
-        const int st = std::max(lev[l], release);
-        if (st + size <= w.H) consider(l, -1, st, st - lev[l]);
-        for (int h = 0; h < nh[l]; ++h) {
-          const int sh = std::max(hs[l][h], release);
-          if (sh + size <= he[l][h]) consider(l, h, sh, sh - hs[l][h]);
-        }
-      }
-      if (best < 0) return false;
-      plane[q] = best;
-      pstart[q] = bstart;
-      if (bhole < 0) {
-        add_hole(best, lev[best], bstart);
-        lev[best] = bstart + size;
-      } else {  // the run splits into what is left below and above the part
-        const int a = hs[best][bhole], b = he[best][bhole];
-        --nh[best];
-        hs[best][bhole] = hs[best][nh[best]];
-        he[best][bhole] = he[best][nh[best]];
-        add_hole(best, a, bstart);
-        add_hole(best, bstart + size, b);
-      }
-      own[best] = (own[best] == -1 || own[best] == c) ? c : -2;
-    }
-    std::copy(lev, lev + cn::kLanes, w.lev);
-    std::copy(own, own + cn::kLanes, w.owner);
-    std::copy(nh, nh + cn::kLanes, w.nh);
-    std::copy(&hs[0][0], &hs[0][0] + cn::kLanes * kHoles, &w.hs[0][0]);
-    std::copy(&he[0][0], &he[0][0] + cn::kLanes * kHoles, &w.he[0][0]);
-    w.root[plane[qsp]] = true;
-    w.max_free = 0;
-    w.free_rows = 0;
-    w.min_lev = cn::kMailMask + (1 << 30);
-    for (int l = 0; l < cn::kLanes; ++l) {
-      w.max_free = std::max(w.max_free, w.H - w.lev[l]);
-      w.free_rows += w.H - w.lev[l];
-      int lo = w.lev[l];
-      for (int h = 0; h < w.nh[l]; ++h) {
-        w.max_free = std::max(w.max_free, w.he[l][h] - w.hs[l][h]);
-        w.free_rows += w.he[l][h] - w.hs[l][h];
-        lo = std::min(lo, w.hs[l][h]);
-      }
-      if (!w.root[l]) w.min_lev = std::min(w.min_lev, lo);  // where a spike-source part can go
-    }
-    return true;
-  };
-  auto try_place = [&](int c, Warp& w, int wi) -> bool {
-    if (!(height > 0 && place(c, w, true)) && !place(c, w, false)) return false;
-    const int np = (int)L.plans[c].parts.size();
-    warp_mail0[c] = w.n_mail;
-    w.n_mail += np - 1;
-    cell_warp[c] = wi;
-    for (int q = 0; q < np; ++q) {
-      part_lane_of_cell[cell_part0[c] + q] = wi * cn::kLanes + plane[q];
-      part_start_of_cell[cell_part0[c] + q] = pstart[q];
-    }
-    return true;
-  };
   // per cell, once: parts in part-tree order (parents first), rows, largest part
   std::vector<int32_t> cell_porder(cell_part0[n_cells]), cell_rows(n_cells), cell_maxpart(n_cells);
   for (int c = 0; c < n_cells; ++c) {
@@ -838,95 +727,246 @@ bool build_layout(int32_t n_cells, const int32_t* off, const int32_t* parent, co
     cell_maxpart[c] = 0;
     for (const CellPart& pt : P.parts) cell_maxpart[c] = std::max(cell_maxpart[c], (int)pt.nodes.size());
   }
-  auto set_order = [&](int c) {
-    porder.assign(cell_porder.begin() + cell_part0[c], cell_porder.begin() + cell_part0[c + 1]);
-  };
-  // a cell cannot fit a warp with fewer free rows than it has, or without a
-  // free run as long as its largest part (cheap tests before a placement try)
-  // (nor, when its first part holds the spike source and so starts no lower
-  // than the lowest lane free of one, if the cell's span does not fit above)
-  auto may_fit = [&](int c, const Warp& w) {
-    const CellPlan& P = L.plans[c];
-    const bool src0 = P.part_of[spike_node ? spike_node[c] : 0] == 0;
-    return cell_rows[c] <= w.free_rows && cell_maxpart[c] <= w.max_free && (!src0 || w.min_lev + P.span <= w.H);
-  };
-  // Fill one warp at a time: it opens with the largest remaining cell and
-  // takes, among the next kPackLookahead remaining cells of the same channel
-  // set, every cell that still fits; the rest wait for later warps.
-  std::vector<int32_t> next_of(n_cells + 1);  // linked list of unplaced cells in order
-  for (int k = 0; k <= n_cells; ++k) next_of[k] = k + 1;
-  int head = 0;  // position in order of the first unplaced cell
-  auto advance = [&](int k) { return next_of[k]; };
   std::vector<uint8_t> placed(n_cells, 0);
-  int tail = n_cells;  // cells at positions >= tail are placed (or of another channel set)
-  while (head < n_cells) {
-    const int c0 = order[head];
-    const CellPlan& P0 = L.plans[c0];
-    Warp w;
-    std::fill(w.lev, w.lev + cn::kLanes, 0);
-    std::fill(w.owner, w.owner + cn::kLanes, -1);
-    std::fill(w.root, w.root + cn::kLanes, false);
-    std::fill(w.nh, w.nh + cn::kLanes, 0);
-    w.mask = mask(c0);
-    w.H = !tall ? P0.span : height > 0 ? std::max(height, P0.span) : tall * H / 2;
-    warps.push_back(w);
-    const int wi = (int)warps.size() - 1;
-    set_order(c0);
-    if (!try_place(c0, warps[wi], wi)) {
+  // Packs the cells of `ord` (in that order) into `warps`; the lanes it
+  // records for a cell's parts count warps from the start of `warps`.
+  auto pack = [&](const std::vector<int32_t>& ord, std::vector<Warp>& warps) -> bool {
+    const int n = (int)ord.size();
+    std::vector<int> porder, pstart, plane;
+    // Places cell c's parts in warp w (parents first).  Each part goes to the
+    // lane, and with a warp height to the free run or lane top, where it
+    // starts earliest (ties: least padding left below it); with `pad_rule`,
+    // where padding x kHoleWeight + delay past its release row is least.
+    // Returns 0 when placed, 1 when the first part has no room at all (no rule
+    // can place the cell), 2 when a later part found none.
+    auto place = [&](int c, Warp& w, bool pad_rule) -> int {
+      const CellPlan& P = L.plans[c];
+      const int np = (int)P.parts.size();
+      if (w.n_mail + np - 1 > cn::kMailMask + 1) return 1;
+      const int qsp = P.part_of[spike_node ? spike_node[c] : 0];  // the part holding the spike source
+      int lev[cn::kLanes], own[cn::kLanes], nh[cn::kLanes], hs[cn::kLanes][kHoles], he[cn::kLanes][kHoles];
+      std::copy(w.lev, w.lev + cn::kLanes, lev);
+      std::copy(w.owner, w.owner + cn::kLanes, own);
+      std::copy(w.nh, w.nh + cn::kLanes, nh);
+      std::copy(&w.hs[0][0], &w.hs[0][0] + cn::kLanes * kHoles, &hs[0][0]);
+      std::copy(&w.he[0][0], &w.he[0][0] + cn::kLanes * kHoles, &he[0][0]);
+      // a new free run [a, b) of lane l (only with a warp height); when the
+      // lane's list is full the shortest run stays padding
+      auto add_hole = [&](int l, int a, int b) {
+        if (height <= 0 || b <= a) return;
+        int s = nh[l];
+        if (s == kHoles) {
+          s = 0;
+          for (int h = 1; h < kHoles; ++h)
+            if (he[l][h] - hs[l][h] < he[l][s] - hs[l][s]) s = h;
+          if (he[l][s] - hs[l][s] >= b - a) return;
+        } else {
+          ++nh[l];
+        }
+        hs[l][s] = a;
+        he[l][s] = b;
+      };
+      pstart.assign(np, 0);
+      plane.assign(np, -1);
+      for (int q : porder) {
+        const int size = (int)P.parts[q].nodes.size();
+        const int release = q == 0 ? 0 : pstart[P.parts[q].parent_part] + P.row_of[P.parts[q].jnode] + 1;
+        int best = -1, bhole = -1, bstart = 0, bgap = 0;
+        auto consider = [&](int l, int h, int st, int gap) {
+          bool better = best < 0;
+          if (!better && pad_rule) {
+            const int cst = kHoleWeight * gap + st, cb = kHoleWeight * bgap + bstart;
+            better = cst < cb || (cst == cb && st < bstart);
+          } else if (!better) {
+            better = st < bstart || (st == bstart && gap < bgap);
+          }
+          if (better) {
+            best = l;
+            bhole = h;
+            bstart = st;
+            bgap = gap;
+          }
+        };
+        for (int l = 0; l < cn::kLanes; ++l) {
+          if (q == qsp && w.root[l]) continue;
+          if (!stack && own[l] != -1 && own[l] != c) continue;
+          const int st = std::max(lev[l], release);
+          if (st + size <= w.H) consider(l, -1, st, st - lev[l]);
+          for (int h = 0; h < nh[l]; ++h) {
+            const int sh = std::max(hs[l][h], release);
+            if (sh + size <= he[l][h]) consider(l, h, sh, sh - hs[l][h]);
+          }
+        }
+        if (best < 0) return q == porder[0] ? 1 : 2;
+        plane[q] = best;
+        pstart[q] = bstart;
+        if (bhole < 0) {
+          add_hole(best, lev[best], bstart);
+          lev[best] = bstart + size;
+        } else {  // the run splits into what is left below and above the part
+          const int a = hs[best][bhole], b = he[best][bhole];
+          --nh[best];
+          hs[best][bhole] = hs[best][nh[best]];
+          he[best][bhole] = he[best][nh[best]];
+          add_hole(best, a, bstart);
+          add_hole(best, bstart + size, b);
+        }
+        own[best] = (own[best] == -1 || own[best] == c) ? c : -2;
+      }
+      std::copy(lev, lev + cn::kLanes, w.lev);
+      std::copy(own, own + cn::kLanes, w.owner);
+      std::copy(nh, nh + cn::kLanes, w.nh);
+      std::copy(&hs[0][0], &hs[0][0] + cn::kLanes * kHoles, &w.hs[0][0]);
+      std::copy(&he[0][0], &he[0][0] + cn::kLanes * kHoles, &w.he[0][0]);
+      w.root[plane[qsp]] = true;
+      w.max_free = 0;
+      w.free_rows = 0;
+      w.min_lev = cn::kMailMask + (1 << 30);
+      for (int l = 0; l < cn::kLanes; ++l) {
+        w.max_free = std::max(w.max_free, w.H - w.lev[l]);
+        w.free_rows += w.H - w.lev[l];
+        int lo = w.lev[l];
+        for (int h = 0; h < w.nh[l]; ++h) {
+          w.max_free = std::max(w.max_free, w.he[l][h] - w.hs[l][h]);
+          w.free_rows += w.he[l][h] - w.hs[l][h];
+          lo = std::min(lo, w.hs[l][h]);
+        }
+        if (!w.root[l]) w.min_lev = std::min(w.min_lev, lo);  // where a spike-source part can go
+      }
+      return 0;
+    };
+    auto try_place = [&](int c, Warp& w, int wi) -> bool {
+      const int r = height > 0 ? place(c, w, true) : 2;
+      if (r == 1 || (r == 2 && place(c, w, false) != 0)) return false;
+      const int np = (int)L.plans[c].parts.size();
+      warp_mail0[c] = w.n_mail;
+      w.n_mail += np - 1;
+      cell_warp[c] = wi;
+      for (int q = 0; q < np; ++q) {
+        part_lane_of_cell[cell_part0[c] + q] = wi * cn::kLanes + plane[q];
+        part_start_of_cell[cell_part0[c] + q] = pstart[q];
+      }
+      return true;
+    };
+    auto set_order = [&](int c) {
+      porder.assign(cell_porder.begin() + cell_part0[c], cell_porder.begin() + cell_part0[c + 1]);
+    };
+    // a cell cannot fit a warp with fewer free rows than it has, or without a
+    // free run as long as its largest part (cheap tests before a placement try)
+    // (nor, when its first part holds the spike source and so starts no lower
+    // than the lowest lane free of one, if the cell's span does not fit above)
+    auto may_fit = [&](int c, const Warp& w) {
+      const CellPlan& P = L.plans[c];
+      const bool src0 = P.part_of[spike_node ? spike_node[c] : 0] == 0;
+      return cell_rows[c] <= w.free_rows && cell_maxpart[c] <= w.max_free && (!src0 || w.min_lev + P.span <= w.H);
+    };
+    // Fill one warp at a time: it opens with the largest remaining cell and
+    // takes, among the next kPackLookahead remaining cells of the same channel
+    // set, every cell that still fits; the rest wait for later warps.
+    std::vector<int32_t> next_of(n + 1);  // linked list of unplaced cells in order
+    for (int k = 0; k <= n; ++k) next_of[k] = k + 1;
+    int head = 0;  // position in order of the first unplaced cell
+    auto advance = [&](int k) { return next_of[k]; };
+      int tail = n;  // cells at positions >= tail are placed (or of another channel set)
+    while (head < n) {
+      const int c0 = ord[head];
+      const CellPlan& P0 = L.plans[c0];
+      Warp w;
+      std::fill(w.lev, w.lev + cn::kLanes, 0);
+      std::fill(w.owner, w.owner + cn::kLanes, -1);
+      std::fill(w.root, w.root + cn::kLanes, false);
+      std::fill(w.nh, w.nh + cn::kLanes, 0);
+      w.mask = mask(c0);
+      w.H = !tall ? P0.span : height > 0 ? std::max(height, P0.span) : tall * H / 2;
+      warps.push_back(w);
+      const int wi = (int)warps.size() - 1;
+      set_order(c0);
+      if (!try_place(c0, warps[wi], wi)) return false;
+      placed[c0] = 1;
+      int k = advance(head), seen = 0;
+      head = k;  // c0 leaves the list
+      int last_kept = -1;
+      while (k < n && seen < kPackLookahead) {
+        const int c = ord[k];
+        if (placed[c]) {  // taken by an earlier warp's gap filling: unlink
+          const int nk = advance(k);
+          if (last_kept < 0) head = nk;
+          else next_of[last_kept] = nk;
+          k = nk;
+          continue;
+        }
+        if (mask(c) != w.mask) break;
+        ++seen;
+        Warp& ww = warps[wi];
+        const CellPlan& P = L.plans[c];
+        const int size0 = (int)P.parts[P.part_of[spike_node ? spike_node[c] : 0]].nodes.size();
+        bool ok = false;
+        if (ww.min_lev + size0 <= ww.H && may_fit(c, ww)) {
+          set_order(c);
+          ok = try_place(c, ww, wi);
+        }
+        const int nk = advance(k);
+        if (ok) {
+          placed[c] = 1;
+          if (last_kept < 0) head = nk;  // unlink k
+          else next_of[last_kept] = nk;
+        } else {
+          last_kept = k;
+        }
+        k = nk;
+      }
+      // then the smallest remaining cells of the same channel set, to fill gaps
+      while (tail > 0 && placed[ord[tail - 1]]) --tail;
+      int tk = tail;
+      seen = 0;
+      while (tk > head && seen < kPackLookahead) {
+        const int c = ord[tk - 1];
+        --tk;
+        if (placed[c]) continue;
+        if (mask(c) != w.mask) break;
+        ++seen;
+        Warp& ww = warps[wi];
+        const CellPlan& P = L.plans[c];
+        const int size0 = (int)P.parts[P.part_of[spike_node ? spike_node[c] : 0]].nodes.size();
+        if (ww.min_lev + size0 > ww.H || !may_fit(c, ww)) continue;
+        set_order(c);
+        if (try_place(c, ww, wi)) placed[c] = 1;
+      }
+      while (head < n && placed[ord[head]]) head = advance(head);
+    }
+    return true;
+  };
+  // With a warp height the cells are dealt round robin (in their sorted
+  // order) into up to kPackChunks chunks of at least kPackChunkCells cells,
+  // packed in parallel; the count follows from the cell count only, so the
+  // layout does not depend on the host's cores.
+  std::vector<Warp> warps;
+  const int chunks = height > 0 ? std::max(1, std::min(kPackChunks, n_cells / kPackChunkCells)) : 1;
+  if (chunks == 1) {
+    if (!pack(order, warps)) {
       err = "internal: a cell does not fit an empty warp";
       return false;
     }
-    placed[c0] = 1;
-    int k = advance(head), seen = 0;
-    head = k;  // c0 leaves the list
-    int last_kept = -1;
-    while (k < n_cells && seen < kPackLookahead) {
-      const int c = order[k];
-      if (placed[c]) {  // taken by an earlier warp's gap filling: unlink
-        const int nk = advance(k);
-        if (last_kept < 0) head = nk;
-        else next_of[last_kept] = nk;
-        k = nk;
-        continue;
+  } else {
+    std::vector<std::vector<int32_t>> ords(chunks);
+    for (int i = 0; i < n_cells; ++i) ords[i % chunks].push_back(order[i]);
+    std::vector<std::vector<Warp>> cw(chunks);
+    std::vector<uint8_t> ok(chunks, 0);
+    parallel_ranges(chunks, 1, [&](int64_t j0, int64_t j1) {
+      for (int64_t j = j0; j < j1; ++j) ok[j] = pack(ords[j], cw[j]);
+    });
+    for (int j = 0; j < chunks; ++j) {
+      if (!ok[j]) {
+        err = "internal: a cell does not fit an empty warp";
+        return false;
       }
-      if (mask(c) != w.mask) break;
-      ++seen;
-      Warp& ww = warps[wi];
-      const CellPlan& P = L.plans[c];
-      const int size0 = (int)P.parts[P.part_of[spike_node ? spike_node[c] : 0]].nodes.size();
-      bool ok = false;
-      if (ww.min_lev + size0 <= ww.H && may_fit(c, ww)) {
-        set_order(c);
-        ok = try_place(c, ww, wi);
+      const int w0 = (int)warps.size();
+      for (int c : ords[j]) {  // chunk-local warp numbers to global ones
+        cell_warp[c] += w0;
+        for (int64_t q = cell_part0[c]; q < cell_part0[c + 1]; ++q) part_lane_of_cell[q] += w0 * cn::kLanes;
       }
-      const int nk = advance(k);
-      if (ok) {
-        placed[c] = 1;
-        if (last_kept < 0) head = nk;  // unlink k
-        else next_of[last_kept] = nk;
-      } else {
-        last_kept = k;
-      }
-      k = nk;
+      warps.insert(warps.end(), cw[j].begin(), cw[j].end());
     }
-    // then the smallest remaining cells of the same channel set, to fill gaps
-    while (tail > 0 && placed[order[tail - 1]]) --tail;
-    int tk = tail;
-    seen = 0;
-    while (tk > head && seen < kPackLookahead) {
-      const int c = order[tk - 1];
-      --tk;
-      if (placed[c]) continue;
-      if (mask(c) != w.mask) break;
-      ++seen;
-      Warp& ww = warps[wi];
-      const CellPlan& P = L.plans[c];
-      const int size0 = (int)P.parts[P.part_of[spike_node ? spike_node[c] : 0]].nodes.size();
-      if (ww.min_lev + size0 > ww.H || !may_fit(c, ww)) continue;
-      set_order(c);
-      if (try_place(c, ww, wi)) placed[c] = 1;
-    }
-    while (head < n_cells && placed[order[head]]) head = advance(head);
   }
   L.n_groups = (int)warps.size();
   L.n_mail = 1;
