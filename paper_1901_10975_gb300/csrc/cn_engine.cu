@@ -435,20 +435,16 @@ CellPlan plan_cell(const int32_t* parent, int n, int target) {
   P.parts.push_back(CellPart{});
   std::vector<int32_t> child_part_at(n, -1);  // junction node -> child part
   const int want = target > 0 ? std::min(32, std::max(1, (n + target - 1) / target)) : 1;
-  std::vector<int32_t> sub(n), dep(n);
+  // in-part subtree sizes, depths below the part root and part sizes, kept
+  // up to date as subtrees move to new parts
+  std::vector<int32_t> sub(n), dep(n), mv;
+  std::vector<int> psize{n};
+  for (int i = n - 1; i >= 0; --i) {
+    sub[i] = 1;
+    for (int c : ch(i)) sub[i] += sub[c];
+  }
+  for (int i = 0; i < n; ++i) dep[i] = i == 0 ? 0 : dep[parent[i]] + 1;
   while ((int)P.parts.size() < want) {
-    // in-part subtree sizes and depths
-    for (int i = n - 1; i >= 0; --i) {
-      sub[i] = 1;
-      for (int c : ch(i))
-        if (P.part_of[c] == P.part_of[i]) sub[i] += sub[c];
-    }
-    std::vector<int> psize(P.parts.size(), 0);
-    for (int i = 0; i < n; ++i) {
-      psize[P.part_of[i]]++;
-      const int q = P.part_of[i];
-      dep[i] = (i == P.parts[q].root) ? 0 : dep[parent[i]] + 1;
-    }
     // estimated bases: a child part starts at its junction depth + 1
     const std::vector<int> base = part_bases(P.parts, dep);
     int worst = 0;
@@ -472,15 +468,23 @@ CellPlan plan_cell(const int32_t* parent, int n, int target) {
     const int nq = (int)P.parts.size();
     P.parts.push_back(np_);
     child_part_at[parent[best_c]] = nq;
-    // move the in-part subtree of best_c (and re-parent child parts hanging inside it)
-    std::vector<int32_t> mv{best_c};
+    // move the in-part subtree of best_c (and re-parent child parts hanging
+    // inside it); its nodes keep their subtree sizes and rise by best_c's
+    // depth, and best_c's in-part ancestors lose its size
+    const int d0 = dep[best_c], s0 = sub[best_c];
+    mv.assign(1, best_c);
     while (!mv.empty()) {
       int u = mv.back();
       mv.pop_back();
       P.part_of[u] = nq;
+      dep[u] -= d0;
       for (int c : ch(u))
         if (P.part_of[c] == worst) mv.push_back(c);
     }
+    for (int a = parent[best_c]; a >= 0 && P.part_of[a] == worst; a = a == P.parts[worst].root ? -1 : parent[a])
+      sub[a] -= s0;
+    psize[worst] -= s0;
+    psize.push_back(s0);
     for (size_t q = 1; q < P.parts.size(); ++q)
       if (P.part_of[P.parts[q].jnode] == nq && (int)q != nq) P.parts[q].parent_part = nq;
   }
