@@ -67,3 +67,42 @@ def test_kernel_digest_ignores_comments_only():
     assert bench.code_only(a) == bench.code_only(b)
     assert bench.code_only(a) != bench.code_only(c)
     assert "//" not in bench.code_only(a) and "/*" not in bench.code_only(a)
+
+
+def test_profiled_traffic_only_for_its_layout():
+    """The DRAM traffic of the committed ncu summary is reported only for the
+    workload, precision and layout it was captured on, with the kernel source
+    it was captured from."""
+    import argparse
+    import re
+    sys.path.insert(0, ROOT)
+    import bench
+    txt = open(os.path.join(ROOT, "profiles", "k_interval_network16k.md")).read()
+    mp = int(re.search(r"layout_mapping:\s*([0-9]+)", txt).group(1))
+    digest = re.search(r"kernel_digest:\s*([0-9a-f]+)", txt).group(1)
+    args = argparse.Namespace(workload="network", cells=0, precision="fp64")
+    t = bench.profiled_traffic(args, mp)
+    if digest == bench.kernel_digest():
+        assert t is not None and t > 16.95e9  # at least the algorithmic bytes of a launch
+    else:
+        assert t is None
+    assert bench.profiled_traffic(args, mp + 1) is None
+    for other in (dict(workload="batched"), dict(cells=8192), dict(precision="gate_fp32")):
+        assert bench.profiled_traffic(argparse.Namespace(**{**vars(args), **other}), mp) is None
+
+
+def test_layout_description_names_the_warp_height():
+    sys.path.insert(0, ROOT)
+    import argparse
+    import bench
+
+    class Sc:
+        n_nodes = 100
+        cell_offset = [0, 50, 100]
+
+    args = argparse.Namespace(workload="network", cells=0, precision="fp64", mapping=2, cells_per_type=32)
+    d = bench.config_dict(args, Sc(), (32 | (1 << 20) | (112 << 22), 4, 2375, 6.5))
+    assert d["layout"]["mapping"] == "cells split to ~32 rows per lane, warps 112 rows tall"
+    assert d["layout"]["mapping_value"] == 32 | (1 << 20) | (112 << 22)
+    d = bench.config_dict(args, Sc(), (43 | (1 << 20), 4, 2272, 7.6))
+    assert d["layout"]["mapping"] == "cells split to ~43 rows per lane, tall warps"
