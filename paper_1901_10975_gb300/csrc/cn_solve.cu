@@ -80,7 +80,7 @@ __global__ void k_solve_trees(int32_t n_trees, const int32_t* __restrict__ off, 
 }
 
 // The two launches of a solve on one stream: the offset check, then the
-// trees (which read the check's verdict from the status word).
+// trees (which read the check's result from the status word).
 cudaError_t launch_solve(int32_t n_trees, int64_t n_nodes, const int32_t* off, const int32_t* parent,
                          const double* a, const double* b, const double* d, const double* rhs, double* x,
                          double* dd, int32_t* status, cudaStream_t st) {
