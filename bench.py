@@ -81,11 +81,16 @@ def profiled_traffic(args, mapping):
     except OSError:
         return None
     m = re.search(r"kernel_digest:\s*([0-9a-f]+)", txt)
+    if not m or m.group(1) != kernel_digest():
+        return None
     t = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
     lay = re.search(r"layout_mapping:\s*([0-9]+)", txt)
-    if not m or not t or not lay or m.group(1) != kernel_digest() or int(lay.group(1)) != mapping:
-        return None
-    return float(t.group(1))
+    if t and lay and int(lay.group(1)) == mapping:
+        return float(t.group(1))
+    for lm, tb in re.findall(r"layout_traffic:\s*([0-9]+)\s+([0-9.eE+]+)", txt):  # other layouts captured
+        if int(lm) == mapping:
+            return float(tb)
+    return None
 
 
 class Clocks:

@@ -87,6 +87,9 @@ def test_profiled_traffic_only_for_its_layout():
     else:
         assert t is None
     assert bench.profiled_traffic(args, mp + 1) is None
+    for lm, tb in re.findall(r"layout_traffic:\s*([0-9]+)\s+([0-9.eE+]+)", txt):
+        if digest == bench.kernel_digest():
+            assert bench.profiled_traffic(args, int(lm)) == float(tb)
     for other in (dict(workload="batched"), dict(cells=8192), dict(precision="gate_fp32")):
         assert bench.profiled_traffic(argparse.Namespace(**{**vars(args), **other}), mp) is None
 
