@@ -155,8 +155,11 @@ typedef enum {
  * targets (down to 4 rows per part) and open warps of their own span if
  * they still exceed it.  Parts then also fill the free runs of rows that a
  * part root's junction constraint leaves below a lane's top, and a part
- * goes where it leaves the least padding (four rows of padding weigh as one
- * row of delay), else at the earliest row that fits.                      */
+ * goes where 4 x (padding rows left below it) + (rows of delay past its
+ * earliest row) is least, else at the earliest row that fits.  Cells are
+ * packed in up to 16 chunks of at least 1,024 cells each, on host threads;
+ * the chunks follow from the cell count alone, so the layout does not
+ * depend on the host.                                                     */
 #define CN_MAP_HEIGHT_SHIFT 22
 #define CN_MAP_HEIGHT_MASK ((int32_t)0x1ff << CN_MAP_HEIGHT_SHIFT)
 #define CN_MAP_HEIGHT(h) ((int32_t)(h) << CN_MAP_HEIGHT_SHIFT)
