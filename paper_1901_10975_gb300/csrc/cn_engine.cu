@@ -606,14 +606,14 @@ bool valid_trees(int32_t n_cells, const int32_t* off, const int32_t* parent, std
 
 // Placement of every cell on the lanes of the warps.  Each warp is a grid
 // of 32 lanes x H rows: H is the span of the cell that opened the warp, or,
-// with "tall" warps, the largest span of all cells.  Cells are taken largest
-// span first and placed, part by part in part-tree order, into the first
-// warp where they fit (among the last few warps, or any warp when tall): the root part into a lane that holds no other spike
-// source, each child part into the lane whose free row is closest to (at or
-// below) the row after its junction, so that it starts there or, failing
-// that, as early as possible above it.  A child part may start anywhere
-// above its junction row: its eliminated (-a, x, b/d) and the junction's
-// back-substituted v pass through a per-warp mailbox in shared memory.
+// with "tall" warps, the largest span of all cells (or a given warp
+// height).  Warps are filled one at a time, cells largest span first; a
+// cell goes part by part in part-tree order: the root part into a lane that
+// holds no other spike source, each child part where it starts earliest at
+// or above the row after its junction (see place() for the rule with a
+// warp height).  A child part may start anywhere above its junction row:
+// its eliminated (-a, x, b/d) and the junction's back-substituted v pass
+// through a per-warp mailbox in shared memory.
 // With stacking on, a lane holds parts of several cells one above the
 // other; without it (channel kinetics are per lane; the adjoint sums per
 // lane) a lane holds parts of one cell only.  Channel sets never share a
@@ -653,11 +653,12 @@ void plan_cells(int32_t n_cells, const int32_t* off, const int32_t* parent, int 
   });
 }
 
-constexpr int kPackLookahead = 512;  // remaining cells tried per warp
-constexpr int kPackChunks = 16;      // chunks packed in parallel (warp height given), at most
-constexpr int kPackChunkCells = 1024;  // and at least this many cells each
-constexpr int kHoles = 4;            // free runs below a lane's top kept per lane (warp height given)
-constexpr int kHoleWeight = 4;       // rows of delay one row of padding is worth (warp height given)
+constexpr int kPackLookahead = 512;    // remaining cells tried per warp
+// with a warp height:
+constexpr int kPackChunks = 16;        // chunks packed in parallel, at most,
+constexpr int kPackChunkCells = 1024;  // of at least this many cells each
+constexpr int kHoles = 4;              // free runs below a lane's top kept per lane
+constexpr int kHoleWeight = 4;         // rows of delay one row of padding is worth
 
 // With a warp height (height > 0, tall warps): cells whose span exceeds it
 // are planned again with finer targets, warps are `height` rows tall (or
@@ -674,7 +675,6 @@ bool build_layout(int32_t n_cells, const int32_t* off, const int32_t* parent, co
     const int n = off[c + 1] - off[c];
     L.depth = std::max(L.depth, L.plans[c].depth);
     H = std::max(H, L.plans[c].span);
-    L.max_span = H;
     for (int32_t li = 0; li < n; ++li)
       if (L.plans[c].nfar[li] > (int)cn::kNFarMask) {
         err = "a node has more than 8 children";
@@ -685,6 +685,7 @@ bool build_layout(int32_t n_cells, const int32_t* off, const int32_t* parent, co
       return false;
     }
   }
+  L.max_span = H;
   std::vector<int32_t> order(n_cells);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
@@ -698,7 +699,7 @@ bool build_layout(int32_t n_cells, const int32_t* off, const int32_t* parent, co
     int n_mail = 0;
     int32_t mask = 0;
     int min_lev = 0;
-    int H = 0;               // rows of this warp: the span of the cell that opened it
+    int H = 0;               // rows of this warp
     int max_free = 1 << 30;  // longest free run of rows in any lane
     int64_t free_rows = 0;   // free rows over all lanes
     // with a warp height: free runs [hs, he) below a lane's top, left where
@@ -708,7 +709,7 @@ bool build_layout(int32_t n_cells, const int32_t* off, const int32_t* parent, co
   };
   // per cell: the placement found
   std::vector<std::vector<int>> kids;
-  std::vector<int> porder;
+  std::vector<int> po;
   std::vector<int32_t> part_lane_of_cell, part_start_of_cell;  // flattened by cell
   std::vector<int64_t> cell_part0(n_cells + 1, 0);
   for (int c = 0; c < n_cells; ++c) cell_part0[c + 1] = cell_part0[c] + (int64_t)L.plans[c].parts.size();
@@ -722,11 +723,10 @@ bool build_layout(int32_t n_cells, const int32_t* off, const int32_t* parent, co
     const int np = (int)P.parts.size();
     kids.assign(np, {});
     for (int q = 1; q < np; ++q) kids[P.parts[q].parent_part].push_back(q);
-    porder.clear();
-    porder.push_back(0);
-    for (size_t h = 0; h < porder.size(); ++h)
-      for (int k : kids[porder[h]]) porder.push_back(k);
-    std::copy(porder.begin(), porder.end(), cell_porder.begin() + cell_part0[c]);
+    po.assign(1, 0);
+    for (size_t h = 0; h < po.size(); ++h)
+      for (int k : kids[po[h]]) po.push_back(k);
+    std::copy(po.begin(), po.end(), cell_porder.begin() + cell_part0[c]);
     cell_rows[c] = off[c + 1] - off[c];
     cell_maxpart[c] = 0;
     for (const CellPart& pt : P.parts) cell_maxpart[c] = std::max(cell_maxpart[c], (int)pt.nodes.size());
